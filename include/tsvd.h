@@ -1,0 +1,184 @@
+/*
+ * tsvd.h -- C ABI of libtsvd: the randomized block Krylov truncated T-SVD
+ * (Kooshkghazi, Ahmadi-Asl, de Almeida, "Randomized block Krylov method for
+ * approximation of truncated tensor SVD", arXiv 2504.04989) and the t-product
+ * with its adjoints, as hand-written CUDA kernels for one GB300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - A real tensor X in R^{n1 x n2 x n3} is a dense row-major array of shape
+ *    (n3, n1, n2): frontal slice t (Sec. 2, "frontal slices X^(k)") is
+ *    contiguous, element X(i, j, t) sits at t*n1*n2 + i*n2 + j.
+ *  - Element type: double for TSVD_FP64, float for every other precision.
+ *  - Every pointer named "device" must point to memory of the current CUDA
+ *    device (cudaMalloc'd or torch-allocated); the caller owns all memory.
+ *    The library never allocates or frees memory on these paths: scratch space
+ *    is the caller's workspace `ws` of at least the size the matching
+ *    *_workspace_size call reports, aligned to 256 bytes.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous on it; argument errors are reported synchronously as a
+ *    negative return value and nothing is launched.
+ *  - Results are deterministic for fixed inputs, parameters and seed (no
+ *    atomics in reductions).
+ *  - No C++ exception crosses this interface.
+ */
+#ifndef TSVD_H
+#define TSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TSVD_API __attribute__((visibility("default")))
+#else
+#define TSVD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define TSVD_OK 0
+#define TSVD_ERR_INVALID_ARG (-1)   /* null pointer, bad size, bad parameter, misaligned */
+#define TSVD_ERR_WORKSPACE (-2)     /* ws_bytes smaller than required */
+#define TSVD_ERR_CUDA (-3)          /* a CUDA launch or API call failed */
+#define TSVD_ERR_UNSUPPORTED (-4)   /* size beyond a documented kernel limit */
+#define TSVD_ERR_NOT_CONVERGED (-5) /* device side: an eigen solve did not converge */
+
+/* ---- precision of the streaming contractions (FFT, Krylov, projection GEMMs) ---- */
+typedef enum {
+  TSVD_FP64 = 0,       /* everything in FP64 */
+  TSVD_FP32 = 1,       /* FFT and complex GEMMs in FP32 (FP32 accumulation); QR and small SVD in FP64 */
+  TSVD_MIXED_TF32 = 2, /* Krylov products on tcgen05 TF32, FP32 accumulation; rest as TSVD_FP32 */
+  TSVD_MIXED_BF16 = 3  /* Krylov products on tcgen05 BF16, FP32 accumulation; rest as TSVD_FP32 */
+} tsvd_precision;
+
+/* ---- parameters of Alg. 2 (Sec. 3): target tubal rank R, oversampling P,
+ *      power/Krylov depth q; seed of the Gaussian test tensor B = randn(n2, R+P, n3) ---- */
+typedef struct {
+  int R;
+  int P;
+  int q;
+  int precision;  /* tsvd_precision */
+  uint64_t seed;
+  int flags;      /* bit 0 (TSVD_FLAG_FP32_QR): orthonormalise the Krylov blocks in FP32 (non-FP64 precisions only) */
+} tsvd_params;
+
+#define TSVD_FLAG_FP32_QR 1
+
+/* ---- device-side outcome, read back only when requested ---- */
+typedef struct {
+  int status;          /* TSVD_OK or TSVD_ERR_NOT_CONVERGED */
+  int m_eff;           /* basis columns per slice: min((q+1)(R+P), n1, n2) */
+  int dead_columns;    /* Krylov columns found numerically dependent and replaced (all slices) */
+  int reserved;
+} tsvd_info;
+
+/*
+ * tsvd_rbk_workspace_size -- bytes of workspace tsvd_rbk needs for this shape.
+ * Returns TSVD_OK and writes *bytes, or TSVD_ERR_INVALID_ARG / TSVD_ERR_UNSUPPORTED.
+ */
+TSVD_API int tsvd_rbk_workspace_size(int n1, int n2, int n3, const tsvd_params* params, size_t* bytes);
+
+/*
+ * tsvd_rbk -- randomized block Krylov truncated T-SVD, Alg. 2 of the paper
+ * (Sec. 3), computed slice by slice in the Fourier domain (the remark opening
+ * Sec. 4; Alg. TP / Alg. TQR for the transform and the mirror).
+ *
+ *   A      device, (n3, n1, n2) real, the data tensor X.
+ *   params R >= 1, R <= min(n1, n2), P >= 0, q >= 0; precision; seed.
+ *   Omega  device, (n3, n2, R+P) real test tensor B of Alg. 2, or NULL to draw
+ *          it on the device: element e is output e%4 of Philox4x32-10 call e/4
+ *          with counter (e/4 low, e/4 high, 0, 0) and key (seed low, seed high);
+ *          words (x0,x1) and (x2,x3) become normals by Box-Muller with
+ *          uniforms (x+1)/2^32: r = sqrt(-2 ln u1), (r cos 2 pi u2, r sin 2 pi u2).
+ *   U      device out, (n3, n1, R): U_R of Alg. 2 (last line).
+ *   S      device out, (n3, R): the diagonal tubes of the f-diagonal S_R.
+ *   V      device out, (n3, n2, R): V_R.
+ *   sigma_hat  device out (double), (floor(n3/2)+1, R): Fourier-domain singular
+ *          values per slice, descending; may be NULL.
+ *   ws, ws_bytes  device workspace (see tsvd_rbk_workspace_size).
+ *   info   host out, may be NULL.  When non-NULL the call synchronises `stream`
+ *          and fills it; otherwise the call is fully asynchronous.
+ * Limits: R + P <= 128, min((q+1)(R+P), n1, n2) <= 512 (TSVD_ERR_UNSUPPORTED).
+ * The Krylov block is built in its block-orthonormalised form (same span as
+ * K = [K_0..K_q] in exact arithmetic): Q_0 = orth(A B), Q_i = orth(A A^H Q_{i-1}
+ * minus its part in Q_0..Q_{i-1}); the last block keeps its leading columns.
+ */
+TSVD_API int tsvd_rbk(const void* A, int n1, int n2, int n3, const tsvd_params* params, const void* Omega,
+             void* U, void* S, void* V, double* sigma_hat, void* ws, size_t ws_bytes, void* stream,
+             tsvd_info* info);
+
+/*
+ * tprod -- t-product C = A * B (Definition of the T-product, Sec. 2, computed
+ * by Alg. TP: mode-3 FFT, one complex product per non-redundant Fourier slice,
+ * conjugate mirror, inverse FFT).
+ *   A device (n3, n1, n2), B device (n3, n2, n4), C device out (n3, n1, n4).
+ *   precision: TSVD_FP64 (double arrays) or TSVD_FP32 / TSVD_MIXED_TF32 /
+ *   TSVD_MIXED_BF16 (float arrays; the slice products on FP32 SIMT or tcgen05).
+ */
+TSVD_API int tprod_workspace_size(int n1, int n2, int n4, int n3, int precision, size_t* bytes);
+TSVD_API int tprod(const void* A, const void* B, void* C, int n1, int n2, int n4, int n3, int precision, void* ws,
+          size_t ws_bytes, void* stream);
+
+/*
+ * tproj -- projection Y = Q * Q^T * A onto the range of Q (the projector of
+ * Lemma mn38), per Fourier slice Y_k = Q_k (Q_k^H A_k).
+ *   Q device (n3, n1, m), A device (n3, n1, n2), Y device out (n3, n1, n2).
+ */
+TSVD_API int tproj_workspace_size(int n1, int m, int n2, int n3, int precision, size_t* bytes);
+TSVD_API int tproj(const void* Q, const void* A, void* Y, int n1, int m, int n2, int n3, int precision, void* ws,
+                   size_t ws_bytes, void* stream);
+
+/*
+ * tprod_backward -- adjoint of the t-product for L = <dC, A*B> (inner product
+ * of Sec. 2): dA = dC * B^T and dB = A^T * dC, with the tensor transpose of
+ * Sec. 2 (bcirc(X^T) = bcirc(X)^T).  In the Fourier domain these are
+ * dA_k = dC_k B_k^H and dB_k = A_k^H dC_k.  Either output may be NULL.
+ *   A (n3,n1,n2), B (n3,n2,n4), dC (n3,n1,n4); dA (n3,n1,n2), dB (n3,n2,n4).
+ */
+TSVD_API int tprod_backward_workspace_size(int n1, int n2, int n4, int n3, int precision, size_t* bytes);
+TSVD_API int tprod_backward(const void* A, const void* B, const void* dC, void* dA, void* dB, int n1, int n2, int n4,
+                   int n3, int precision, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * tproj_backward -- adjoint of the projection Y = Q * Q^T * A (the projector
+ * of Lemma mn38): dA = Q * (Q^T * dY) and dQ = dY * (A^T * Q) + A * (dY^T * Q).
+ *   Q (n3,n1,m), A (n3,n1,n2), dY (n3,n1,n2); dQ (n3,n1,m), dA (n3,n1,n2).
+ *   Either output may be NULL.
+ */
+TSVD_API int tproj_backward_workspace_size(int n1, int m, int n2, int n3, int precision, size_t* bytes);
+TSVD_API int tproj_backward(const void* Q, const void* A, const void* dY, void* dQ, void* dA, int n1, int m, int n2, int n3,
+                   int precision, void* ws, size_t ws_bytes, void* stream);
+
+/* Philox4x32-10 Gaussian draw of the test tensor on the device (the same
+ * definition as tsvd_rbk uses when Omega is NULL), for inspection and tests:
+ * out (device, double) receives n normals of (seed, stream, tensor_id). */
+TSVD_API int tsvd_gaussian(uint64_t seed, uint32_t stream_id, uint32_t tensor_id, long n, double* out, void* stream);
+/* raw Philox words for counters ctr0..ctr0+n-1 (ctr1..3 fixed), 4 words each */
+TSVD_API int tsvd_philox_words(const uint32_t key[2], uint32_t ctr1, uint32_t ctr2, uint32_t ctr3, long n, uint32_t* out,
+                      void* stream);
+
+/* ---- optional stage timing (diagnostic, process-global, not thread safe) ----
+ * Between tsvd_profile_begin() and tsvd_profile_end() every pipeline stage of
+ * the calls above records a CUDA event pair on its stream.  tsvd_profile_end()
+ * synchronises those events and writes up to max_out per-stage totals
+ * (summed milliseconds and the number of recorded stage executions); *n_out
+ * receives the number written. */
+typedef struct {
+  char name[32];
+  double ms;
+  int count;
+} tsvd_stage_time;
+TSVD_API int tsvd_profile_begin(void);
+TSVD_API int tsvd_profile_end(tsvd_stage_time* out, int max_out, int* n_out);
+
+TSVD_API const char* tsvd_strerror(int code);
+/* library version (major*10000 + minor*100 + patch) */
+TSVD_API int tsvd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,267 @@
+"""Torch-facing API of the randomized block Krylov truncated T-SVD
+(arXiv 2504.04989) on one GB300.
+
+PyTorch supplies device memory, the current stream and autograd; every step
+of the computation runs in libtsvd's CUDA kernels (see include/tsvd.h).  A
+real n1 x n2 x n3 tensor is a torch tensor of shape (n3, n1, n2) (frontal
+slices contiguous), float64 for precision "fp64" and float32 otherwise.
+"""
+import ctypes as C
+
+import torch
+
+from . import _lib
+
+_DT = {"fp64": torch.float64, "fp32": torch.float32, "tf32": torch.float32, "bf16": torch.float32}
+
+
+def _prec(precision):
+    if precision not in _lib.PRECISIONS:
+        raise ValueError("precision must be one of %s" % sorted(_lib.PRECISIONS))
+    return _lib.PRECISIONS[precision]
+
+
+def _stream(device):
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _need_cuda(*ts, dtype=None):
+    for t in ts:
+        if t is None:
+            continue
+        if not t.is_cuda:
+            raise ValueError("libtsvd operates on CUDA tensors only (got a %s tensor)" % t.device)
+        if dtype is not None and t.dtype != dtype:
+            raise ValueError("expected dtype %s, got %s" % (dtype, t.dtype))
+
+
+def _workspace(nbytes, device):
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def rbk(A, R, P=10, q=2, seed=0, precision="fp32", omega=None, return_info=False):
+    """Randomized block Krylov truncated T-SVD (Alg. 2): A ~ U * S * V^T.
+
+    A: (n3, n1, n2) CUDA tensor.  Returns U (n3, n1, R), S (n3, R) singular
+    tubes, V (n3, n2, R) and sigma_hat (n3 // 2 + 1, R) float64 Fourier-domain
+    singular values (descending per slice).  omega (n3, n2, R + P) replaces the
+    Philox-drawn test tensor when given.
+    """
+    lib = _lib.load()
+    pr = _prec(precision)
+    dt = _DT[precision]
+    A = A.contiguous()
+    _need_cuda(A, omega, dtype=dt)
+    n3, n1, n2 = A.shape
+    p = _lib.TsvdParams(R=int(R), P=int(P), q=int(q), precision=pr, seed=int(seed), flags=0)
+    nbytes = C.c_size_t()
+    _lib.check(lib.tsvd_rbk_workspace_size(n1, n2, n3, C.byref(p), C.byref(nbytes)), "tsvd_rbk_workspace_size")
+    dev = A.device
+    ws = _workspace(nbytes.value, dev)
+    h = n3 // 2 + 1
+    U = torch.empty((n3, n1, R), dtype=dt, device=dev)
+    S = torch.empty((n3, R), dtype=dt, device=dev)
+    V = torch.empty((n3, n2, R), dtype=dt, device=dev)
+    sig = torch.empty((h, R), dtype=torch.float64, device=dev)
+    if omega is not None:
+        omega = omega.contiguous()
+        if tuple(omega.shape) != (n3, n2, R + P):
+            raise ValueError("omega must have shape (n3, n2, R+P)")
+    info = _lib.TsvdInfo()
+    with torch.cuda.device(dev):
+        rc = lib.tsvd_rbk(_ptr(A), n1, n2, n3, C.byref(p), _ptr(omega), _ptr(U), _ptr(S), _ptr(V), _ptr(sig),
+                          _ptr(ws), nbytes.value, _stream(dev), C.byref(info) if return_info else None)
+    _lib.check(rc, "tsvd_rbk")
+    if return_info:
+        return U, S, V, sig, {"status": info.status, "m_eff": info.m_eff, "dead_columns": info.dead_columns}
+    return U, S, V, sig
+
+
+class RbkPlan:
+    """Pre-allocated outputs and workspace for repeated T-SVDs of one shape
+    (no allocation per call, so a loop of calls can be captured in a CUDA graph)."""
+
+    def __init__(self, n1, n2, n3, R, P=10, q=2, seed=0, precision="fp32", device="cuda"):
+        self.lib = _lib.load()
+        self.dt = _DT[precision]
+        self.p = _lib.TsvdParams(R=int(R), P=int(P), q=int(q), precision=_prec(precision), seed=int(seed), flags=0)
+        self.shape = (n1, n2, n3)
+        nbytes = C.c_size_t()
+        _lib.check(self.lib.tsvd_rbk_workspace_size(n1, n2, n3, C.byref(self.p), C.byref(nbytes)), "workspace")
+        self.nbytes = nbytes.value
+        self.device = torch.device(device)
+        self.ws = _workspace(self.nbytes, self.device)
+        self.U = torch.empty((n3, n1, R), dtype=self.dt, device=self.device)
+        self.S = torch.empty((n3, R), dtype=self.dt, device=self.device)
+        self.V = torch.empty((n3, n2, R), dtype=self.dt, device=self.device)
+        self.sig = torch.empty((n3 // 2 + 1, R), dtype=torch.float64, device=self.device)
+
+    def __call__(self, A, omega=None, stream=None):
+        n1, n2, n3 = self.shape
+        s = C.c_void_p(stream.cuda_stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream)
+        rc = self.lib.tsvd_rbk(_ptr(A), n1, n2, n3, C.byref(self.p), _ptr(omega), _ptr(self.U), _ptr(self.S),
+                               _ptr(self.V), _ptr(self.sig), _ptr(self.ws), self.nbytes, s, None)
+        _lib.check(rc, "tsvd_rbk")
+        return self.U, self.S, self.V, self.sig
+
+
+def _tprod_raw(A, B, precision):
+    lib = _lib.load()
+    pr = _prec(precision)
+    A, B = A.contiguous(), B.contiguous()
+    _need_cuda(A, B, dtype=_DT[precision])
+    n3, n1, n2 = A.shape
+    n3b, n2b, n4 = B.shape
+    if n3b != n3 or n2b != n2:
+        raise ValueError("tprod: shapes (n3,n1,n2) and (n3,n2,n4) required")
+    nbytes = C.c_size_t()
+    _lib.check(lib.tprod_workspace_size(n1, n2, n4, n3, pr, C.byref(nbytes)), "tprod_workspace_size")
+    ws = _workspace(nbytes.value, A.device)
+    out = torch.empty((n3, n1, n4), dtype=A.dtype, device=A.device)
+    with torch.cuda.device(A.device):
+        _lib.check(lib.tprod(_ptr(A), _ptr(B), _ptr(out), n1, n2, n4, n3, pr, _ptr(ws), nbytes.value,
+                             _stream(A.device)), "tprod")
+    return out
+
+
+def tprod_backward(A, B, dC, precision="fp32", need_dA=True, need_dB=True):
+    """dA = dC * B^T, dB = A^T * dC (adjoint of the t-product)."""
+    lib = _lib.load()
+    pr = _prec(precision)
+    A, B, dC = A.contiguous(), B.contiguous(), dC.contiguous()
+    _need_cuda(A, B, dC, dtype=_DT[precision])
+    n3, n1, n2 = A.shape
+    n4 = B.shape[2]
+    nbytes = C.c_size_t()
+    _lib.check(lib.tprod_backward_workspace_size(n1, n2, n4, n3, pr, C.byref(nbytes)), "workspace")
+    ws = _workspace(nbytes.value, A.device)
+    dA = torch.empty_like(A) if need_dA else None
+    dB = torch.empty_like(B) if need_dB else None
+    with torch.cuda.device(A.device):
+        _lib.check(lib.tprod_backward(_ptr(A), _ptr(B), _ptr(dC), _ptr(dA), _ptr(dB), n1, n2, n4, n3, pr, _ptr(ws),
+                                      nbytes.value, _stream(A.device)), "tprod_backward")
+    return dA, dB
+
+
+def _tproj_raw(Q, A, precision):
+    lib = _lib.load()
+    pr = _prec(precision)
+    Q, A = Q.contiguous(), A.contiguous()
+    _need_cuda(Q, A, dtype=_DT[precision])
+    n3, n1, m = Q.shape
+    n2 = A.shape[2]
+    nbytes = C.c_size_t()
+    _lib.check(lib.tproj_workspace_size(n1, m, n2, n3, pr, C.byref(nbytes)), "workspace")
+    ws = _workspace(nbytes.value, Q.device)
+    Y = torch.empty_like(A)
+    with torch.cuda.device(Q.device):
+        _lib.check(lib.tproj(_ptr(Q), _ptr(A), _ptr(Y), n1, m, n2, n3, pr, _ptr(ws), nbytes.value,
+                             _stream(Q.device)), "tproj")
+    return Y
+
+
+def tproj_backward(Q, A, dY, precision="fp32", need_dQ=True, need_dA=True):
+    """dA = Q * (Q^T * dY), dQ = dY * (A^T * Q) + A * (dY^T * Q) for Y = Q * Q^T * A."""
+    lib = _lib.load()
+    pr = _prec(precision)
+    Q, A, dY = Q.contiguous(), A.contiguous(), dY.contiguous()
+    _need_cuda(Q, A, dY, dtype=_DT[precision])
+    n3, n1, m = Q.shape
+    n2 = A.shape[2]
+    nbytes = C.c_size_t()
+    _lib.check(lib.tproj_backward_workspace_size(n1, m, n2, n3, pr, C.byref(nbytes)), "workspace")
+    ws = _workspace(nbytes.value, Q.device)
+    dQ = torch.empty_like(Q) if need_dQ else None
+    dA = torch.empty_like(A) if need_dA else None
+    with torch.cuda.device(Q.device):
+        _lib.check(lib.tproj_backward(_ptr(Q), _ptr(A), _ptr(dY), _ptr(dQ), _ptr(dA), n1, m, n2, n3, pr, _ptr(ws),
+                                      nbytes.value, _stream(Q.device)), "tproj_backward")
+    return dQ, dA
+
+
+def _precision_of(t, precision):
+    if precision is not None:
+        return precision
+    return "fp64" if t.dtype == torch.float64 else "fp32"
+
+
+class TProd(torch.autograd.Function):
+    """C = A * B with the hand-written adjoint as backward."""
+
+    @staticmethod
+    def forward(ctx, A, B, precision):
+        ctx.save_for_backward(A, B)
+        ctx.precision = precision
+        return _tprod_raw(A, B, precision)
+
+    @staticmethod
+    def backward(ctx, dC):
+        A, B = ctx.saved_tensors
+        dA, dB = tprod_backward(A, B, dC, ctx.precision, ctx.needs_input_grad[0], ctx.needs_input_grad[1])
+        return dA, dB, None
+
+
+class TProj(torch.autograd.Function):
+    """Y = Q * Q^T * A with the hand-written adjoint as backward."""
+
+    @staticmethod
+    def forward(ctx, Q, A, precision):
+        ctx.save_for_backward(Q, A)
+        ctx.precision = precision
+        return _tproj_raw(Q, A, precision)
+
+    @staticmethod
+    def backward(ctx, dY):
+        Q, A = ctx.saved_tensors
+        dQ, dA = tproj_backward(Q, A, dY, ctx.precision, ctx.needs_input_grad[0], ctx.needs_input_grad[1])
+        return dQ, dA, None
+
+
+def tprod(A, B, precision=None):
+    """t-product C = A * B (Alg. TP); differentiable."""
+    return TProd.apply(A, B, _precision_of(A, precision))
+
+
+def tproj(Q, A, precision=None):
+    """Projection Y = Q * Q^T * A (Lemma mn38); differentiable."""
+    return TProj.apply(Q, A, _precision_of(Q, precision))
+
+
+def gaussian(seed, n, stream_id=0, tensor_id=0, device="cuda"):
+    """Device draw of the Philox4x32-10 / Box-Muller Gaussian stream (float64)."""
+    lib = _lib.load()
+    out = torch.empty(int(n), dtype=torch.float64, device=device)
+    _lib.check(lib.tsvd_gaussian(int(seed), stream_id, tensor_id, int(n), _ptr(out), _stream(out.device)), "gaussian")
+    return out
+
+
+def philox_words(key, ctr1, ctr2, ctr3, n, device="cuda"):
+    """Raw Philox4x32-10 words for counters (i, ctr1, ctr2, ctr3), i < n: int64 (n, 4)."""
+    lib = _lib.load()
+    out = torch.empty((int(n), 4), dtype=torch.int32, device=device)
+    k = (C.c_uint32 * 2)(int(key[0]) & 0xFFFFFFFF, int(key[1]) & 0xFFFFFFFF)
+    _lib.check(lib.tsvd_philox_words(k, ctr1, ctr2, ctr3, int(n), _ptr(out), _stream(out.device)), "philox_words")
+    return out.to(torch.int64) & 0xFFFFFFFF
+
+
+class profile:
+    """Context manager collecting per-stage GPU times (CUDA events recorded by
+    the library around each pipeline stage).  After exit, `.stages` maps a
+    stage name to (total milliseconds, executions)."""
+
+    def __enter__(self):
+        self.lib = _lib.load()
+        _lib.check(self.lib.tsvd_profile_begin(), "tsvd_profile_begin")
+        self.stages = {}
+        return self
+
+    def __exit__(self, *exc):
+        buf = (_lib.TsvdStageTime * 64)()
+        n = C.c_int()
+        _lib.check(self.lib.tsvd_profile_end(buf, 64, C.byref(n)), "tsvd_profile_end")
+        self.stages = {buf[i].name.decode(): (buf[i].ms, buf[i].count) for i in range(n.value)}
+        return False

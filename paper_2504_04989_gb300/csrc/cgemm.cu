@@ -1,0 +1,203 @@
+// cgemm.cu -- batched complex GEMM on the SIMT FP64 / FP32 pipes.
+//
+// One CTA computes a 64 x 64 tile of one slice's product with 256 threads,
+// each holding a 4 x 4 complex register tile (rows ty + 16 i, columns
+// tx + 16 j, so a warp's shared-memory reads are contiguous).  op(A) and op(B)
+// tiles are staged in shared memory k-major; the conjugate transpose is taken
+// while staging, reading the stored matrix along its contiguous dimension.
+// Thin products (long K, small M x N) split K across CTAs and reduce the
+// partial tiles in a fixed order (deterministic, no atomics).
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace tsvd {
+
+template <typename C>
+struct GemmCfg;
+template <>
+struct GemmCfg<double2> {
+  static constexpr int BK = 8;
+  using R = double;
+};
+template <>
+struct GemmCfg<float2> {
+  static constexpr int BK = 16;
+  using R = float;
+};
+
+constexpr int GBM = 64, GBN = 64;
+
+template <typename C, bool AH, bool BH>
+__global__ void __launch_bounds__(256) k_cgemm(GemmArgs g, C* __restrict__ ws, int ksplit, int kchunk, int tiles_m) {
+  constexpr int BK = GemmCfg<C>::BK;
+  using R = typename GemmCfg<C>::R;
+  __shared__ __align__(16) C As[BK][GBM];
+  __shared__ __align__(16) C Bs[BK][GBN];
+  const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+  const int bi = blockIdx.z / ksplit, kz = blockIdx.z % ksplit;
+  const int m0 = tm * GBM, n0 = tn * GBN;
+  const C* __restrict__ A = (const C*)g.A + (long)bi * g.sA;
+  const C* __restrict__ B = (const C*)g.B + (long)bi * g.sB;
+  const int kb = kz * kchunk, ke = min(g.K, kb + kchunk);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  C acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = mkc(R(0), R(0));
+
+  for (int k0 = kb; k0 < ke; k0 += BK) {
+    for (int idx = tid; idx < GBM * BK; idx += 256) {
+      int mm, kk;
+      if (!AH) { kk = idx % BK; mm = idx / BK; }
+      else { mm = idx % GBM; kk = idx / GBM; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      C v = mkc(R(0), R(0));
+      if (gm < g.M && gk < ke) v = AH ? cconj(A[(long)gk * g.lda + gm]) : A[(long)gm * g.lda + gk];
+      As[kk][mm] = v;
+    }
+    for (int idx = tid; idx < GBN * BK; idx += 256) {
+      int nn, kk;
+      if (!BH) { nn = idx % GBN; kk = idx / GBN; }
+      else { kk = idx % BK; nn = idx / BK; }
+      const int gn = n0 + nn, gk = k0 + kk;
+      C v = mkc(R(0), R(0));
+      if (gn < g.N && gk < ke) v = BH ? cconj(B[(long)gn * g.ldb + gk]) : B[(long)gk * g.ldb + gn];
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      C a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+  C* __restrict__ Cm = (C*)g.C + (long)bi * g.sC;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty + 16 * i;
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn >= g.N) continue;
+      if (ksplit > 1) {
+        ws[(((long)kz * g.batch + bi) * g.M + gm) * g.N + gn] = acc[i][j];
+      } else {
+        C r = cscale(acc[i][j], (R)g.alpha);
+        if (g.beta != 0.0) r = cadd(r, cscale(Cm[(long)gm * g.ldc + gn], (R)g.beta));
+        Cm[(long)gm * g.ldc + gn] = r;
+      }
+    }
+  }
+}
+
+template <typename C>
+__global__ void k_splitk_reduce(const C* __restrict__ ws, int ksplit, GemmArgs g) {
+  using R = typename GemmCfg<C>::R;
+  const long total = (long)g.batch * g.M * g.N;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int n = idx % g.N;
+    const long r = idx / g.N;
+    const int m = r % g.M;
+    const int bi = r / g.M;
+    C s = mkc(R(0), R(0));
+    for (int kz = 0; kz < ksplit; ++kz) s = cadd(s, ws[(long)kz * total + idx]);
+    C* Cm = (C*)g.C + (long)bi * g.sC + (long)m * g.ldc + n;
+    C out = cscale(s, (R)g.alpha);
+    if (g.beta != 0.0) out = cadd(out, cscale(*Cm, (R)g.beta));
+    *Cm = out;
+  }
+}
+
+int choose_ksplit(int M, int N, int K, int batch, size_t splitk_elems) {
+  const long tiles = (long)cdiv(M, GBM) * cdiv(N, GBN) * batch;
+  const long target = 2 * 152;
+  int ks = (int)std::max(1L, std::min(16L, target / std::max(1L, tiles)));
+  ks = std::min(ks, std::max(1, K / 64));
+  while (ks > 1 && (size_t)ks * batch * M * N > splitk_elems) --ks;
+  while (ks > 1 && (long)ks * batch > 65535) --ks;
+  return ks;
+}
+
+template <typename C>
+int cgemm(const GemmArgs& g, void* splitk_ws, size_t splitk_elems, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return TSVD_OK;
+  if (g.batch > 65535) return TSVD_ERR_UNSUPPORTED;
+  if (g.beta != 0.0 && g.beta != 1.0) return TSVD_ERR_INVALID_ARG;
+  int ks = (g.K > 0) ? choose_ksplit(g.M, g.N, g.K, g.batch, splitk_ws ? splitk_elems : 0) : 1;
+  constexpr int BK = GemmCfg<C>::BK;
+  int kchunk = (g.K + ks - 1) / ks;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  if (kchunk == 0) kchunk = BK;
+  ks = (g.K + kchunk - 1) / kchunk;
+  if (ks < 1) ks = 1;
+  const int tiles_m = cdiv(g.M, GBM), tiles_n = cdiv(g.N, GBN);
+  dim3 grid(tiles_m * tiles_n, 1, g.batch * ks);
+  const bool ah = (g.opA == 'H'), bh = (g.opB == 'H');
+  C* ws = (C*)splitk_ws;
+  if (!ah && !bh) k_cgemm<C, false, false><<<grid, 256, 0, s>>>(g, ws, ks, kchunk, tiles_m);
+  else if (ah && !bh) k_cgemm<C, true, false><<<grid, 256, 0, s>>>(g, ws, ks, kchunk, tiles_m);
+  else if (!ah && bh) k_cgemm<C, false, true><<<grid, 256, 0, s>>>(g, ws, ks, kchunk, tiles_m);
+  else k_cgemm<C, true, true><<<grid, 256, 0, s>>>(g, ws, ks, kchunk, tiles_m);
+  TSVD_LAUNCHED();
+  if (ks > 1) {
+    const long total = (long)g.batch * g.M * g.N;
+    k_splitk_reduce<C><<<std::min<long>(cdiv(total, 256), 4096), 256, 0, s>>>(ws, ks, g);
+    TSVD_LAUNCHED();
+  }
+  return TSVD_OK;
+}
+template int cgemm<double2>(const GemmArgs&, void*, size_t, cudaStream_t);
+template int cgemm<float2>(const GemmArgs&, void*, size_t, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+template <typename S, typename D>
+__global__ void k_convert(const S* __restrict__ src, long lds, long ss, D* __restrict__ dst, long ldd, long sd,
+                          int rows, int cols, int batch) {
+  const long total = (long)batch * rows * cols;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int c = idx % cols;
+    const long r = idx / cols;
+    const int row = r % rows;
+    const int b = r / rows;
+    const S v = src[(long)b * ss + (long)row * lds + c];
+    D o;
+    o.x = v.x;
+    o.y = v.y;
+    dst[(long)b * sd + (long)row * ldd + c] = o;
+  }
+}
+
+template <typename S, typename D>
+static int convert(const S* src, long lds, long ss, D* dst, long ldd, long sd, int rows, int cols, int batch,
+                   cudaStream_t s) {
+  const long total = (long)batch * rows * cols;
+  if (total <= 0) return TSVD_OK;
+  k_convert<S, D><<<std::min<long>(cdiv(total, 256), 8192), 256, 0, s>>>(src, lds, ss, dst, ldd, sd, rows, cols, batch);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
+int convert_c64_to_c32(const double2* src, long lds, long ss, float2* dst, long ldd, long sd, int rows, int cols,
+                       int batch, cudaStream_t s) {
+  return convert(src, lds, ss, dst, ldd, sd, rows, cols, batch, s);
+}
+int convert_c32_to_c64(const float2* src, long lds, long ss, double2* dst, long ldd, long sd, int rows, int cols,
+                       int batch, cudaStream_t s) {
+  return convert(src, lds, ss, dst, ldd, sd, rows, cols, batch, s);
+}
+int copy_c64(const double2* src, long lds, long ss, double2* dst, long ldd, long sd, int rows, int cols, int batch,
+             cudaStream_t s) {
+  return convert(src, lds, ss, dst, ldd, sd, rows, cols, batch, s);
+}
+
+}  // namespace tsvd

@@ -1,0 +1,93 @@
+// kernels.cuh -- host launchers shared between the translation units of libtsvd.
+#pragma once
+
+#include "common.cuh"
+
+namespace tsvd {
+
+// RAII stage timer: records a CUDA event pair around a pipeline stage when
+// stage profiling is enabled (profile.cu); no-op otherwise.
+class StageTimer {
+ public:
+  StageTimer(const char* name, cudaStream_t s);
+  ~StageTimer();
+
+ private:
+  const char* name_;
+  cudaStream_t s_;
+  void* a_;
+};
+#define TSVD_CAT2(a, b) a##b
+#define TSVD_CAT(a, b) TSVD_CAT2(a, b)
+#define TSVD_STAGE(name, s) ::tsvd::StageTimer TSVD_CAT(_stage_timer_, __LINE__)(name, s)
+
+// fft.cu
+template <typename T>
+int launch_rfft3(const T* X, cx_t<T>* Xh, long plane, int n3, cudaStream_t s);
+template <typename T>
+int launch_irfft3(const cx_t<T>* Xh, T* X, long plane, int n3, cudaStream_t s);
+template <typename T>
+int launch_gaussian(uint64_t seed, uint32_t stream_id, uint32_t tensor_id, long n, T* out, cudaStream_t s);
+
+// cgemm.cu -- batched complex GEMM on the SIMT pipes,
+//   C_b = alpha * op(A_b) * op(B_b) + beta * C_b   for b < batch,
+// op = 'N' (as stored) or 'H' (conjugate transpose); all row-major.
+// op(A) is M x K, op(B) is K x N; C is M x N with leading dimension ldc.
+// beta must be 0 or 1 (C is not read when beta == 0).  When ksplit > 1 the K
+// range is split over CTAs; `splitk_ws` must hold ksplit*batch*M*N elements.
+struct GemmArgs {
+  char opA, opB;
+  int M, N, K;
+  double alpha, beta;
+  const void* A;
+  long lda, sA;
+  const void* B;
+  long ldb, sB;
+  void* C;
+  long ldc, sC;
+  int batch;
+};
+template <typename C>
+int cgemm(const GemmArgs& g, void* splitk_ws, size_t splitk_elems, cudaStream_t s);
+// pick a split of K that fills the GPU (bounded by the scratch it needs)
+int choose_ksplit(int M, int N, int K, int batch, size_t splitk_elems);
+
+// element-wise conversions of batched complex matrices (rows x cols, leading dims)
+int convert_c64_to_c32(const double2* src, long lds, long ss, float2* dst, long ldd, long sd, int rows, int cols,
+                       int batch, cudaStream_t s);
+int convert_c32_to_c64(const float2* src, long lds, long ss, double2* dst, long ldd, long sd, int rows, int cols,
+                       int batch, cudaStream_t s);
+int copy_c64(const double2* src, long lds, long ss, double2* dst, long ldd, long sd, int rows, int cols, int batch,
+             cudaStream_t s);
+
+// linalg.cu -- small dense FP64 kernels, one problem per Fourier slice
+// Cholesky R^H R = G + s I of the nb x nb Hermitian G (s = shift * trace(G)
+// when shift > 0).  R is written dense upper triangular (zeros below).
+// Columns whose pivot falls below the dependence threshold (plain pass:
+// d_j <= 1e-12 G_jj; shifted pass: d_j <= 0) are marked in `dead` (4 words
+// per slice) and get R_jj = 1, R_jk = 0.
+int chol_upper(const double2* G, long ldg, long sG, double2* Rm, long ldr, long sR, int nb, int batch, double shift,
+               uint32_t* dead, cudaStream_t s);
+// W <- W R^{-1} in place for the n1 x nb blocks W (leading dim ldw) of every
+// slice; dead columns come out zero.
+int trsm_right_upper(double2* W, long ldw, long sW, const double2* Rm, long ldr, long sR, int n1, int nb, int batch,
+                     const uint32_t* dead, cudaStream_t s);
+// Replace dead columns [c, c+nb) of Q (n1 x ldq per slice) by unit vectors
+// orthogonal to columns [0, c+nb): Philox directions projected twice.
+int repair_dead(double2* Q, long ldq, long sQ, int n1, int c, int nb, const uint32_t* dead, int batch,
+                uint64_t seed, int block_id, int* dead_count, cudaStream_t s);
+// Eigen-decomposition of the m x m Hermitian G per slice (G is overwritten):
+// top-R eigenvalues (descending) in lam (batch x R) and eigenvectors in
+// U (batch x m x R, row-major, leading dim ldu).  scratch: eig_scratch_bytes.
+size_t eig_scratch_bytes(int m, int R, int batch);
+int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double* lam, double2* U, long ldu, long sU,
+                  void* scratch, int* status, cudaStream_t s);
+// sigma = sqrt(max(lam, 0)) -> sig (batch x R, may be null) and the complex
+// tube slices Sh of S; a non-finite eigenvalue sets *status.
+template <typename T>
+int sigma_from_lambda(const double* lam, int R, int batch, double* sig, cx_t<T>* Sh, cudaStream_t s, int* status);
+// columns r of V (rows x R per slice) scaled by 1 / sqrt(lam_r) (zero where lam_r <= 0)
+template <typename T>
+int scale_columns_inv(cx_t<T>* V, long ldv, long sV, int rows, int R, const double* lam, int batch, cudaStream_t s);
+
+}  // namespace tsvd

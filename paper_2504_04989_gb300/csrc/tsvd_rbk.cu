@@ -1,0 +1,335 @@
+// tsvd_rbk.cu -- the randomized block Krylov truncated T-SVD (Alg. 2, Sec. 3)
+// as one stream of kernels, and its C-ABI entry points.
+//
+// Per non-redundant Fourier slice k (all slices batched in every launch):
+//   Omega_k          rFFT of the real Gaussian test tensor B (Alg. 2, line 1)
+//   A_k              rFFT of the data tensor (Alg. TP, first line)
+//   W_0 = A_k Om_k   K_0 = X * B                               (Alg. 2, line 2)
+//   Q_0 = orth(W_0)
+//   Y_i = A_k^H Q_{i-1},  W_i = A_k Y_i   K_i = X * X^T * K_{i-1} (Alg. 2, line 4)
+//   Q_i = orth(W_i - Q_{<i} Q_{<i}^H W_i)  T-QR of K = [K_0..K_q] (Alg. 2, lines 5-6)
+//   C^H = A_k^H Q = [Y_1, .., Y_q, A_k^H Q_q]  (C = Q^T * X, Alg. 2 line 7; the
+//         first q blocks are the Y_i already formed by the Krylov steps)
+//   G = C C^H = U_c S_c^2 U_c^H           T-SVD(C)                  (Alg. 2, line 8)
+//   Uhat = Q U_c(:, 1:R),  Vhat = C^H U_c(:, 1:R) S_R^{-1}          (Alg. 2, lines 9-10)
+//   inverse rFFT of Uhat, Vhat and the singular tubes.
+// orth = three passes of [classical Gram-Schmidt against Q_{<i}, CholeskyQR]
+// (shifted CholeskyQR3): the first Cholesky is shifted so that it cannot break
+// down; columns found dependent afterwards are replaced by fresh orthonormal
+// directions.
+#include <type_traits>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace tsvd {
+
+struct RbkDims {
+  int n1, n2, n3, h, R, P, q, b, m;
+};
+
+static int rbk_dims(int n1, int n2, int n3, const tsvd_params* p, RbkDims* d) {
+  if (!p || n1 < 1 || n2 < 1 || n3 < 1) return TSVD_ERR_INVALID_ARG;
+  if (p->R < 1 || p->P < 0 || p->q < 0 || p->R > n1 || p->R > n2) return TSVD_ERR_INVALID_ARG;
+  if (p->precision < TSVD_FP64 || p->precision > TSVD_MIXED_BF16) return TSVD_ERR_INVALID_ARG;
+  d->n1 = n1;
+  d->n2 = n2;
+  d->n3 = n3;
+  d->h = n3 / 2 + 1;
+  d->R = p->R;
+  d->P = p->P;
+  d->q = p->q;
+  d->b = p->R + p->P;
+  long m = (long)(p->q + 1) * d->b;
+  m = std::min<long>(m, std::min(n1, n2));
+  d->m = (int)m;
+  if (d->b > 128 || d->m > 512) return TSVD_ERR_UNSUPPORTED;
+  if ((long)d->h * n1 * n2 > (1L << 40)) return TSVD_ERR_UNSUPPORTED;
+  return TSVD_OK;
+}
+
+template <typename T>
+struct RbkWs {
+  using C = cx_t<T>;
+  C* Ah;
+  T* Om;
+  C* Omh;
+  double2* Q64;
+  C* Qt;
+  C* Wt;
+  double2* W64;
+  C* CHt;
+  double2* CH64;
+  double2* P64;
+  double2* Gs;
+  double2* Rs;
+  uint32_t* dead;
+  int* counters;  // [0] status, [1] dead columns
+  double2* G;
+  double* lam;
+  double2* Uc64;
+  C* Uct;
+  C* Uh;
+  C* Vh;
+  C* Sh;
+  void* eig;
+  double2* splitk;
+  size_t splitk_elems;
+  size_t bytes;
+};
+
+template <typename T>
+static RbkWs<T> carve_rbk(void* base, const RbkDims& d) {
+  using C = cx_t<T>;
+  constexpr bool dbl = std::is_same<T, double>::value;
+  Carver cv(base);
+  RbkWs<T> w;
+  const size_t h = d.h;
+  w.Ah = cv.take<C>(h * d.n1 * d.n2);
+  w.Om = cv.take<T>((size_t)d.n3 * d.n2 * d.b);
+  w.Omh = cv.take<C>(h * d.n2 * d.b);
+  w.Q64 = cv.take<double2>(h * d.n1 * d.m);
+  w.Qt = dbl ? (C*)w.Q64 : cv.take<C>(h * d.n1 * d.m);
+  w.W64 = cv.take<double2>(h * d.n1 * d.b);
+  w.Wt = dbl ? (C*)w.W64 : cv.take<C>(h * d.n1 * d.b);
+  w.CHt = cv.take<C>(h * d.n2 * d.m);
+  w.CH64 = dbl ? (double2*)w.CHt : cv.take<double2>(h * d.n2 * d.m);
+  w.P64 = cv.take<double2>(h * d.m * d.b);
+  w.Gs = cv.take<double2>(h * d.b * d.b);
+  w.Rs = cv.take<double2>(h * d.b * d.b);
+  w.dead = cv.take<uint32_t>(h * 4);
+  w.counters = cv.take<int>(8);
+  w.G = cv.take<double2>(h * d.m * d.m);
+  w.lam = cv.take<double>(h * d.R);
+  w.Uc64 = cv.take<double2>(h * d.m * d.R);
+  w.Uct = dbl ? (C*)w.Uc64 : cv.take<C>(h * d.m * d.R);
+  w.Uh = cv.take<C>(h * d.n1 * d.R);
+  w.Vh = cv.take<C>(h * d.n2 * d.R);
+  w.Sh = cv.take<C>(h * d.R);
+  w.eig = cv.take<char>(eig_scratch_bytes(d.m, d.R, d.h));
+  w.splitk_elems = 8 * h * (size_t)d.m * std::max(d.b, 64);
+  w.splitk = cv.take<double2>(w.splitk_elems);
+  w.bytes = cv.bytes();
+  return w;
+}
+
+static GemmArgs gemm(char opA, char opB, int M, int N, int K, double alpha, const void* A, long lda, long sA,
+                     const void* B, long ldb, long sB, double beta, void* Cm, long ldc, long sC, int batch) {
+  GemmArgs g;
+  g.opA = opA;
+  g.opB = opB;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.alpha = alpha;
+  g.beta = beta;
+  g.A = A;
+  g.lda = lda;
+  g.sA = sA;
+  g.B = B;
+  g.ldb = ldb;
+  g.sB = sB;
+  g.C = Cm;
+  g.ldc = ldc;
+  g.sC = sC;
+  g.batch = batch;
+  return g;
+}
+
+// Orthonormalise the nb leading columns of W64 (n1 x b per slice) against the
+// c finished columns of Q64 and write them to Q64 columns [c, c+nb).
+template <typename T>
+static int orth_block(const RbkDims& d, RbkWs<T>& w, int c, int nb, int block_id, uint64_t seed, cudaStream_t s) {
+  const int n1 = d.n1, b = d.b, m = d.m, h = d.h;
+  const long sQ = (long)n1 * m, sW = (long)n1 * b, sP = (long)m * b, sG = (long)b * b;
+  const double u = 1.1102230246251565e-16;
+  const double shift = 11.0 * ((double)n1 * nb + (double)nb * (nb + 1)) * u;
+  // shifted CholeskyQR3 (the shift makes the first Cholesky succeed for any
+  // W; the next two passes restore orthogonality to rounding level), each
+  // pass preceded by a classical Gram-Schmidt projection against Q_{<i}
+  for (int pass = 0; pass < 3; ++pass) {
+    if (c > 0) {
+      TSVD_STAGE("orth_cgs", s);
+      TSVD_TRY(cgemm<double2>(gemm('H', 'N', c, nb, n1, 1.0, w.Q64, m, sQ, w.W64, b, sW, 0.0, w.P64, nb, sP, h),
+                              w.splitk, w.splitk_elems, s));
+      TSVD_TRY(cgemm<double2>(gemm('N', 'N', n1, nb, c, -1.0, w.Q64, m, sQ, w.P64, nb, sP, 1.0, w.W64, b, sW, h),
+                              w.splitk, w.splitk_elems, s));
+    }
+    {
+      TSVD_STAGE("orth_gram", s);
+      TSVD_TRY(cgemm<double2>(gemm('H', 'N', nb, nb, n1, 1.0, w.W64, b, sW, w.W64, b, sW, 0.0, w.Gs, b, sG, h),
+                              w.splitk, w.splitk_elems, s));
+    }
+    {
+      TSVD_STAGE("orth_chol", s);
+      TSVD_TRY(chol_upper(w.Gs, b, sG, w.Rs, b, sG, nb, h, pass == 0 ? shift : 0.0, w.dead, s));
+    }
+    {
+      TSVD_STAGE("orth_trsm", s);
+      TSVD_TRY(trsm_right_upper(w.W64, b, sW, w.Rs, b, sG, n1, nb, h, w.dead, s));
+    }
+  }
+  {
+    TSVD_STAGE("orth_repair", s);
+    TSVD_TRY(copy_c64(w.W64, b, sW, w.Q64 + c, m, sQ, n1, nb, h, s));
+    TSVD_TRY(repair_dead(w.Q64, m, sQ, n1, c, nb, w.dead, h, seed, block_id, w.counters + 1, s));
+  }
+  if (!std::is_same<T, double>::value) {
+    TSVD_STAGE("convert", s);
+    TSVD_TRY(convert_c64_to_c32(w.Q64 + c, m, sQ, (float2*)w.Qt + c, m, sQ, n1, nb, h, s));
+  }
+  return TSVD_OK;
+}
+
+// to FP64 for the orthonormalisation (no-op when T is double)
+template <typename T>
+static int to64(const cx_t<T>* src, long lds, long ss, double2* dst, long ldd, long sd, int rows, int cols, int batch,
+                cudaStream_t s) {
+  if (std::is_same<T, double>::value) return TSVD_OK;
+  TSVD_STAGE("convert", s);
+  return convert_c32_to_c64((const float2*)src, lds, ss, dst, ldd, sd, rows, cols, batch, s);
+}
+
+template <typename T>
+static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* Omega, T* U, T* S, T* V,
+                   double* sig, void* ws, cudaStream_t s, tsvd_info* info) {
+  using C = cx_t<T>;
+  RbkWs<T> w = carve_rbk<T>(ws, d);
+  const int n1 = d.n1, n2 = d.n2, n3 = d.n3, h = d.h, b = d.b, m = d.m, R = d.R;
+  const long sA = (long)n1 * n2, sQ = (long)n1 * m, sW = (long)n1 * b, sCH = (long)n2 * m, sO = (long)n2 * b;
+  if (cudaMemsetAsync(w.counters, 0, 8 * sizeof(int), s) != cudaSuccess) return TSVD_ERR_CUDA;
+
+  // test tensor and data in the Fourier domain
+  const T* Om = Omega;
+  if (!Om) {
+    TSVD_STAGE("omega", s);
+    TSVD_TRY(launch_gaussian<T>(p.seed, 0, 0, (long)n3 * n2 * b, w.Om, s));
+    Om = w.Om;
+  }
+  {
+    TSVD_STAGE("rfft", s);
+    TSVD_TRY(launch_rfft3<T>(Om, w.Omh, (long)n2 * b, n3, s));
+    TSVD_TRY(launch_rfft3<T>(A, w.Ah, (long)n1 * n2, n3, s));
+  }
+
+  // block 0: W_0 = A Omega
+  const int b0 = std::min(b, m);
+  {
+    TSVD_STAGE("krylov_gemm", s);
+    TSVD_TRY(cgemm<C>(gemm('N', 'N', n1, b0, n2, 1.0, w.Ah, n2, sA, w.Omh, b, sO, 0.0, w.Wt, b, sW, h), w.splitk,
+                      w.splitk_elems * 2, s));
+  }
+  TSVD_TRY(to64<T>(w.Wt, b, sW, w.W64, b, sW, n1, b0, h, s));
+  TSVD_TRY(orth_block<T>(d, w, 0, b0, 0, p.seed, s));
+  int c = b0, pw = b0;
+  for (int i = 1; i <= d.q && c < m; ++i) {
+    const int bi = std::min(b, m - c);
+    {
+    TSVD_STAGE("krylov_gemm", s);
+    // Y_i = A^H Q_{i-1}: the block of C^H that belongs to Q_{i-1}
+    TSVD_TRY(cgemm<C>(gemm('H', 'N', n2, pw, n1, 1.0, w.Ah, n2, sA, w.Qt + (c - pw), m, sQ, 0.0, w.CHt + (c - pw), m,
+                           sCH, h),
+                      w.splitk, w.splitk_elems * 2, s));
+    // W_i = A Y_i (leading bi columns)
+    TSVD_TRY(cgemm<C>(gemm('N', 'N', n1, bi, n2, 1.0, w.Ah, n2, sA, w.CHt + (c - pw), m, sCH, 0.0, w.Wt, b, sW, h),
+                      w.splitk, w.splitk_elems * 2, s));
+    }
+    TSVD_TRY(to64<T>(w.Wt, b, sW, w.W64, b, sW, n1, bi, h, s));
+    TSVD_TRY(orth_block<T>(d, w, c, bi, i, p.seed, s));
+    c += bi;
+    pw = bi;
+  }
+  // last block of C^H = A^H Q_last
+  {
+  TSVD_STAGE("krylov_gemm", s);
+  TSVD_TRY(cgemm<C>(gemm('H', 'N', n2, pw, n1, 1.0, w.Ah, n2, sA, w.Qt + (c - pw), m, sQ, 0.0, w.CHt + (c - pw), m,
+                         sCH, h),
+                    w.splitk, w.splitk_elems * 2, s));
+  }
+
+  // G = C C^H (FP64) and its top-R eigenpairs
+  TSVD_TRY(to64<T>(w.CHt, m, sCH, w.CH64, m, sCH, n2, m, h, s));
+  {
+  TSVD_STAGE("gram_c", s);
+  TSVD_TRY(cgemm<double2>(gemm('H', 'N', m, m, n2, 1.0, w.CH64, m, sCH, w.CH64, m, sCH, 0.0, w.G, m, (long)m * m, h),
+                          w.splitk, w.splitk_elems, s));
+  }
+  TSVD_TRY(herm_eig_topR(w.G, m, (long)m * m, m, R, h, w.lam, w.Uc64, R, (long)m * R, w.eig, w.counters, s));
+  {
+  TSVD_STAGE("outputs", s);
+  TSVD_TRY(sigma_from_lambda<T>(w.lam, R, h, sig, w.Sh, s, w.counters));
+  if (!std::is_same<T, double>::value)
+    TSVD_TRY(convert_c64_to_c32(w.Uc64, R, (long)m * R, (float2*)w.Uct, R, (long)m * R, m, R, h, s));
+
+  // Uhat = Q U_c,  Vhat = C^H U_c S^{-1}
+  TSVD_TRY(cgemm<C>(gemm('N', 'N', n1, R, m, 1.0, w.Qt, m, sQ, w.Uct, R, (long)m * R, 0.0, w.Uh, R, (long)n1 * R, h),
+                    w.splitk, w.splitk_elems * 2, s));
+  TSVD_TRY(cgemm<C>(gemm('N', 'N', n2, R, m, 1.0, w.CHt, m, sCH, w.Uct, R, (long)m * R, 0.0, w.Vh, R, (long)n2 * R, h),
+                    w.splitk, w.splitk_elems * 2, s));
+  TSVD_TRY(scale_columns_inv<T>(w.Vh, R, (long)n2 * R, n2, R, w.lam, h, s));
+  }
+  {
+  // back to the spatial domain
+  TSVD_STAGE("irfft", s);
+  TSVD_TRY(launch_irfft3<T>(w.Uh, U, (long)n1 * R, n3, s));
+  TSVD_TRY(launch_irfft3<T>(w.Vh, V, (long)n2 * R, n3, s));
+  TSVD_TRY(launch_irfft3<T>(w.Sh, S, (long)R, n3, s));
+  }
+
+  if (info) {
+    int host[8];
+    if (cudaMemcpyAsync(host, w.counters, sizeof(host), cudaMemcpyDeviceToHost, s) != cudaSuccess) return TSVD_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TSVD_ERR_CUDA;
+    info->status = host[0];
+    info->dead_columns = host[1];
+    info->m_eff = m;
+    info->reserved = 0;
+  }
+  return TSVD_OK;
+}
+
+}  // namespace tsvd
+
+using namespace tsvd;
+
+extern "C" int tsvd_rbk_workspace_size(int n1, int n2, int n3, const tsvd_params* params, size_t* bytes) {
+  if (!bytes) return TSVD_ERR_INVALID_ARG;
+  RbkDims d;
+  TSVD_TRY(rbk_dims(n1, n2, n3, params, &d));
+  if (params->precision == TSVD_MIXED_TF32 || params->precision == TSVD_MIXED_BF16) return TSVD_ERR_UNSUPPORTED;
+  *bytes = (params->precision == TSVD_FP64) ? carve_rbk<double>(nullptr, d).bytes : carve_rbk<float>(nullptr, d).bytes;
+  return TSVD_OK;
+}
+
+extern "C" int tsvd_rbk(const void* A, int n1, int n2, int n3, const tsvd_params* params, const void* Omega, void* U,
+                        void* S, void* V, double* sigma_hat, void* ws, size_t ws_bytes, void* stream,
+                        tsvd_info* info) {
+  RbkDims d;
+  TSVD_TRY(rbk_dims(n1, n2, n3, params, &d));
+  if (!A || !U || !S || !V || !ws) return TSVD_ERR_INVALID_ARG;
+  if (((uintptr_t)ws & 255) != 0) return TSVD_ERR_INVALID_ARG;
+  if (params->precision == TSVD_MIXED_TF32 || params->precision == TSVD_MIXED_BF16) return TSVD_ERR_UNSUPPORTED;
+  const bool dbl = params->precision == TSVD_FP64;
+  const size_t need = dbl ? carve_rbk<double>(nullptr, d).bytes : carve_rbk<float>(nullptr, d).bytes;
+  if (ws_bytes < need) return TSVD_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dbl)
+    return rbk_run<double>((const double*)A, d, *params, (const double*)Omega, (double*)U, (double*)S, (double*)V,
+                           sigma_hat, ws, s, info);
+  return rbk_run<float>((const float*)A, d, *params, (const float*)Omega, (float*)U, (float*)S, (float*)V, sigma_hat,
+                        ws, s, info);
+}
+
+extern "C" const char* tsvd_strerror(int code) {
+  switch (code) {
+    case TSVD_OK: return "ok";
+    case TSVD_ERR_INVALID_ARG: return "invalid argument";
+    case TSVD_ERR_WORKSPACE: return "workspace too small";
+    case TSVD_ERR_CUDA: return "CUDA launch or API failure";
+    case TSVD_ERR_UNSUPPORTED: return "size or mode beyond a kernel limit";
+    case TSVD_ERR_NOT_CONVERGED: return "eigen solve produced a non-finite value";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int tsvd_version(void) { return 100; }
