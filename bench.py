@@ -1,0 +1,291 @@
+"""Benchmark of the randomized block Krylov truncated T-SVD (arXiv 2504.04989).
+
+Workload (one step = one whole T-SVD, every stage of Alg. 2): the image-like
+512 x 512 x 64 float32 tensor with per-Fourier-slice singular values
+sigma_i = i^-1.5 (full rank), R = 50, P = 10, q = 4, synthetic (seeded), the
+input resident in HBM.  Metric: rank-R T-SVD approximations per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
+
+Under torchrun every rank runs its own independent tensor (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="image-like 512x512x64 fp32, sigma_i=i^-1.5 full rank, R=50 P=10 q=4",
+                n1=512, n2=512, n3=64, R=50, P=10, q=4)
+METRIC = "rank-R T-SVD approximations/s"
+FP64_PEAK_TFLOPS = 1.20   # FMA-chain probe on this GB300 (nominal 1.25)
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "fallback": True}
+
+
+def algorithmic(stage, d, precision):
+    """Algorithmic work of one stage for one T-SVD (flops; bytes for transforms)."""
+    n1, n2, n3, R, b, m = d["n1"], d["n2"], d["n3"], d["R"], d["R"] + d["P"], d["m"]
+    h = n3 // 2 + 1
+    q = d["q"]
+    cm = 8.0  # real flops per complex multiply-add
+    blocks = [min(b, m - i * b) for i in range(q + 1) if i * b < m]
+    c_before = np.cumsum([0] + blocks[:-1])
+    if stage == "eig_hetrd":      # Householder tridiagonalisation of the m x m Hermitian Gram
+        return {"flops": 16.0 / 3.0 * m ** 3 * h}
+    if stage == "gram_c":         # G = C C^H (Hermitian: half of the m x m outputs)
+        return {"flops": cm * n2 * m * (m + 1) / 2 * h}
+    if stage == "orth_cgs":       # two classical Gram-Schmidt sweeps per block
+        return {"flops": sum(2 * 2 * cm * n1 * c * nb for c, nb in zip(c_before, blocks)) * h}
+    if stage == "orth_gram":
+        return {"flops": sum(2 * cm * n1 * nb * (nb + 1) / 2 for nb in blocks) * h}
+    if stage == "orth_trsm":
+        return {"flops": sum(2 * cm * n1 * nb * nb / 2 for nb in blocks) * h}
+    if stage == "krylov_gemm":    # A Omega, then A^H Q and A Y per Krylov step, and the last A^H Q
+        return {"flops": cm * n1 * n2 * (sum(blocks) + sum(blocks[:-1]) + blocks[-1]) * h}
+    if stage in ("rfft", "irfft"):
+        s = 8 if precision == "fp64" else 4
+        if stage == "rfft":
+            return {"bytes": s * (n1 * n2 * n3 + 2 * n1 * n2 * h)}
+        return {"bytes": s * (2 * (n1 + n2) * R * h + (n1 + n2) * R * n3)}
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+ORACLE_SLICES = 16  # bounded sample: this many of the workload's Fourier slices per oracle run
+
+
+def oracle_sample(X, d, nslices=ORACLE_SLICES):
+    """The FP64 CPU oracle, as it stands, on `nslices` of the workload's
+    h = n3/2 + 1 independent Fourier slices (OpenMP across slices); the time
+    of a whole T-SVD is that of the sample scaled by h / nslices."""
+    import oracle
+    h = d["n3"] // 2 + 1
+    om = oracle.gaussian(0, d["n3"] * d["n2"] * (d["R"] + d["P"])).reshape(d["n3"], d["n2"], d["R"] + d["P"])
+    t0 = time.perf_counter()
+    oracle.rtsvd_fourier(X, d["R"], d["P"], d["q"], omega=om, slices=list(range(nslices)))
+    dt = time.perf_counter() - t0
+    return dt * h / nslices, dt, oracle.num_threads()
+
+
+def cpu_baseline(X, d):
+    per_tsvd, dt, cores = oracle_sample(X.astype(np.float64), d)
+    return {"value": 1.0 / per_tsvd, "unit": "T-SVD/s", "cores": cores, "kind": "oracle",
+            "sample": "%d of the %d Fourier slices of one T-SVD of the workload (FP64, %.1f s), scaled to the whole "
+                      "T-SVD" % (ORACLE_SLICES, d["n3"] // 2 + 1, dt)}
+
+
+def run_reference(args, d, rank, world):
+    if rank != 0:
+        return
+    from paper_2504_04989_gb300 import workloads as wl
+    X = wl.make_c2(0).astype(np.float32).astype(np.float64)
+    steps = []
+    for i in range(args.warmup + args.steps):
+        per, dt, cores = oracle_sample(X, d)
+        if i >= args.warmup:
+            steps.append(per)
+    t = sum(steps)
+    val = args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "T-SVD/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": d["name"], "precision": "fp64 CPU oracle"},
+            "cpu_baseline": {"value": val, "unit": "T-SVD/s", "cores": cores, "kind": "oracle",
+                             "sample": "each step: %d of the %d Fourier slices of one T-SVD, scaled to the whole "
+                                       "T-SVD" % (ORACLE_SLICES, d["n3"] // 2 + 1)},
+            "e2e": {"value": val, "unit": "T-SVD/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    d = dict(WORKLOAD)
+    d["m"] = min((d["q"] + 1) * (d["R"] + d["P"]), d["n1"], d["n2"])
+    if args.impl == "reference":
+        return run_reference(args, d, rank, world)
+
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2504_04989_gb300 import api
+    from paper_2504_04989_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    X = wl.make_c2(seed=rank).astype(np.float32 if args.precision == "fp32" else np.float64)
+    Xd = torch.from_numpy(X).to(dev)
+    plan = api.RbkPlan(d["n1"], d["n2"], d["n3"], d["R"], d["P"], d["q"], seed=0, precision=args.precision,
+                       device=dev)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        plan(Xd)
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        l0 = api.launch_count()
+        for a, b in ev:
+            flush.zero_()          # evict the previous step's working set from L2
+            a.record(stream)
+            plan(Xd)
+            b.record(stream)
+        barrier()
+        launches_timed = api.launch_count() - l0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1000.0
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * args.steps / total_s
+
+    # end to end through the public API: pinned host input -> device -> T-SVD -> host outputs
+    Xh = torch.from_numpy(X).pin_memory()
+    outs_h = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (plan.U, plan.S, plan.V, plan.sig)]
+    Xe = torch.empty_like(Xd)
+    h2d = Xh.numel() * Xh.element_size()
+    d2h = sum(t.numel() * t.element_size() for t in outs_h)
+    barrier()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in e2e_ev:
+        flush.zero_()
+        a.record(stream)
+        Xe.copy_(Xh, non_blocking=True)
+        U, S, V, sg = plan(Xe)
+        for src, dst in zip((U, S, V, sg), outs_h):
+            dst.copy_(src, non_blocking=True)
+        b.record(stream)
+    barrier()
+    e2e_s = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1000.0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * args.steps / e2e_s
+
+    # per-stage times (CUDA events recorded by the library on this stream)
+    with api.profile() as pr:
+        for _ in range(3):
+            flush.zero_()
+            plan(Xd)
+    stages = {k: v[0] / 3 for k, v in pr.stages.items()}
+    launches = {k: v[1] // 3 for k, v in pr.stages.items()}
+    dom = max(stages, key=stages.get)
+    work = algorithmic(dom, d, args.precision)
+    pk = peaks()
+    if "flops" in work:
+        achieved = work["flops"] / (stages[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 FMA-chain probe on this GB300 (not in MEASURED_PEAKS.json)"}
+    else:
+        achieved = work.get("bytes", 0) / (stages[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    roof["stage_ms"] = {k: round(v, 3) for k, v in sorted(stages.items(), key=lambda kv: -kv[1])}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "T-SVD/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32" else "f64",
+                "data": "synthetic",
+                "config": {"workload": d["name"], "precision": args.precision, "m_eff": d["m"],
+                           "l2": "flushed between steps (256 MB write)", "parallelism": "dp%d" % world},
+                "e2e": {"value": e2e_value, "unit": "T-SVD/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches_timed, "roofline": roof, "clocks": clk.summary()}
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(X, d)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -174,6 +174,9 @@ typedef struct {
 TSVD_API int tsvd_profile_begin(void);
 TSVD_API int tsvd_profile_end(tsvd_stage_time* out, int max_out, int* n_out);
 
+/* number of kernels the library has launched in this process (all threads) */
+TSVD_API unsigned long long tsvd_launch_count(void);
+
 TSVD_API const char* tsvd_strerror(int code);
 /* library version (major*10000 + minor*100 + patch) */
 TSVD_API int tsvd_version(void);

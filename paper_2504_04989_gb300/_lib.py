@@ -48,6 +48,7 @@ SIGNATURES = {
     "tsvd_philox_words": (_i, [C.POINTER(_u32), _u32, _u32, _u32, _l, _vp, _vp]),
     "tsvd_profile_begin": (_i, []),
     "tsvd_profile_end": (_i, [C.POINTER(TsvdStageTime), _i, C.POINTER(_i)]),
+    "tsvd_launch_count": (C.c_ulonglong, []),
     "tsvd_strerror": (C.c_char_p, [_i]),
     "tsvd_version": (_i, []),
 }

@@ -265,3 +265,8 @@ class profile:
         _lib.check(self.lib.tsvd_profile_end(buf, 64, C.byref(n)), "tsvd_profile_end")
         self.stages = {buf[i].name.decode(): (buf[i].ms, buf[i].count) for i in range(n.value)}
         return False
+
+
+def launch_count():
+    """Kernels launched by libtsvd so far in this process."""
+    return int(_lib.load().tsvd_launch_count())

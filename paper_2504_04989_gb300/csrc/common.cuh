@@ -169,8 +169,12 @@ inline int launch_status() { return cudaGetLastError() == cudaSuccess ? TSVD_OK 
     if (_rc != TSVD_OK) return _rc; \
   } while (0)
 
+// counts every kernel launch of the library (profile.cu)
+void count_launch();
+
 #define TSVD_LAUNCHED()                                          \
   do {                                                           \
+    ::tsvd::count_launch();                                      \
     if (cudaPeekAtLastError() != cudaSuccess) {                  \
       cudaGetLastError();                                        \
       return TSVD_ERR_CUDA;                                      \

@@ -18,6 +18,9 @@ struct Rec {
   cudaEvent_t a, b;
 };
 static bool g_on = false;
+static unsigned long long g_launches = 0;
+
+void count_launch() { __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED); }
 static std::vector<Rec> g_recs;
 static std::vector<cudaEvent_t> g_pool;
 
@@ -90,3 +93,5 @@ extern "C" int tsvd_profile_end(tsvd_stage_time* out, int max_out, int* n_out) {
   if (n_out) *n_out = out ? n : (int)names.size();
   return TSVD_OK;
 }
+
+extern "C" unsigned long long tsvd_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
