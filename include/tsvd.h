@@ -49,7 +49,8 @@ extern "C" {
 /* ---- precision of the streaming contractions (FFT, Krylov, projection GEMMs) ---- */
 typedef enum {
   TSVD_FP64 = 0,       /* everything in FP64 */
-  TSVD_FP32 = 1,       /* FFT and complex GEMMs in FP32 (FP32 accumulation); QR and small SVD in FP64 */
+  TSVD_FP32 = 1,       /* FFT, complex GEMMs and the block orthonormalisation in FP32 (FP32
+                          accumulation); the Gram of C and the small eigen-solve in FP64 */
   TSVD_MIXED_TF32 = 2, /* Krylov products on tcgen05 TF32, FP32 accumulation; rest as TSVD_FP32 */
   TSVD_MIXED_BF16 = 3  /* Krylov products on tcgen05 BF16, FP32 accumulation; rest as TSVD_FP32 */
 } tsvd_precision;
@@ -62,10 +63,11 @@ typedef struct {
   int q;
   int precision;  /* tsvd_precision */
   uint64_t seed;
-  int flags;      /* bit 0 (TSVD_FLAG_FP32_QR): orthonormalise the Krylov blocks in FP32 (non-FP64 precisions only) */
+  int flags;      /* bit 0 (TSVD_FLAG_FP64_QR): orthonormalise the Krylov blocks in FP64 on the
+                     FP32 / mixed paths too (they use FP32 by default; the FP64 path always uses FP64) */
 } tsvd_params;
 
-#define TSVD_FLAG_FP32_QR 1
+#define TSVD_FLAG_FP64_QR 1
 
 /* ---- device-side outcome, read back only when requested ---- */
 typedef struct {

@@ -11,6 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtsvd.so")
 
 TSVD_FP64, TSVD_FP32, TSVD_MIXED_TF32, TSVD_MIXED_BF16 = 0, 1, 2, 3
+TSVD_FLAG_FP64_QR = 1
 PRECISIONS = {"fp64": TSVD_FP64, "fp32": TSVD_FP32, "tf32": TSVD_MIXED_TF32, "bf16": TSVD_MIXED_BF16}
 
 ERRORS = {0: "ok", -1: "invalid argument", -2: "workspace too small", -3: "CUDA failure",

@@ -195,9 +195,11 @@ int convert_c32_to_c64(const float2* src, long lds, long ss, double2* dst, long 
                        int batch, cudaStream_t s) {
   return convert(src, lds, ss, dst, ldd, sd, rows, cols, batch, s);
 }
-int copy_c64(const double2* src, long lds, long ss, double2* dst, long ldd, long sd, int rows, int cols, int batch,
-             cudaStream_t s) {
+template <typename C>
+int copy_cx(const C* src, long lds, long ss, C* dst, long ldd, long sd, int rows, int cols, int batch, cudaStream_t s) {
   return convert(src, lds, ss, dst, ldd, sd, rows, cols, batch, s);
 }
+template int copy_cx<double2>(const double2*, long, long, double2*, long, long, int, int, int, cudaStream_t);
+template int copy_cx<float2>(const float2*, long, long, float2*, long, long, int, int, int, cudaStream_t);
 
 }  // namespace tsvd

@@ -57,25 +57,30 @@ int convert_c64_to_c32(const double2* src, long lds, long ss, float2* dst, long 
                        int batch, cudaStream_t s);
 int convert_c32_to_c64(const float2* src, long lds, long ss, double2* dst, long ldd, long sd, int rows, int cols,
                        int batch, cudaStream_t s);
-int copy_c64(const double2* src, long lds, long ss, double2* dst, long ldd, long sd, int rows, int cols, int batch,
-             cudaStream_t s);
+template <typename C>
+int copy_cx(const C* src, long lds, long ss, C* dst, long ldd, long sd, int rows, int cols, int batch,
+            cudaStream_t s);
 
-// linalg.cu -- small dense FP64 kernels, one problem per Fourier slice
-// Cholesky R^H R = G + s I of the nb x nb Hermitian G (s = shift * trace(G)
-// when shift > 0).  R is written dense upper triangular (zeros below).
-// Columns whose pivot falls below the dependence threshold (plain pass:
-// d_j <= 1e-12 G_jj; shifted pass: d_j <= 0) are marked in `dead` (4 words
-// per slice) and get R_jj = 1, R_jk = 0.
-int chol_upper(const double2* G, long ldg, long sG, double2* Rm, long ldr, long sR, int nb, int batch, double shift,
-               uint32_t* dead, cudaStream_t s);
-// W <- W R^{-1} in place for the n1 x nb blocks W (leading dim ldw) of every
+// cholqr.cu -- block orthonormalisation pieces (one problem per Fourier slice)
+// Cholesky R^H R = G + s I (FP64) of the nb x nb Hermitian Gram G of precision
+// GC (s = shift_rel * trace(G) when shift_rel > 0).  R is written dense upper
+// triangular (zeros below).  Pivots: shifted pass -> dead iff d_j <= 0; plain
+// pass -> dead iff d_j <= dead_rel * G_jj.  Dead columns are marked in `dead`
+// (4 words per slice) and get R_jj = 1, R_jk = 0.
+template <typename GC>
+int chol_upper(const GC* G, long ldg, long sG, double2* Rm, long ldr, long sR, int nb, int batch, double shift_rel,
+               double dead_rel, uint32_t* dead, cudaStream_t s);
+// W <- W R^{-1} in place (W's precision) for the n1 x nb blocks of every
 // slice; dead columns come out zero.
-int trsm_right_upper(double2* W, long ldw, long sW, const double2* Rm, long ldr, long sR, int n1, int nb, int batch,
+template <typename C>
+int trsm_right_upper(C* W, long ldw, long sW, const double2* Rm, long ldr, long sR, int n1, int nb, int batch,
                      const uint32_t* dead, cudaStream_t s);
 // Replace dead columns [c, c+nb) of Q (n1 x ldq per slice) by unit vectors
 // orthogonal to columns [0, c+nb): Philox directions projected twice.
-int repair_dead(double2* Q, long ldq, long sQ, int n1, int c, int nb, const uint32_t* dead, int batch,
-                uint64_t seed, int block_id, int* dead_count, cudaStream_t s);
+template <typename C>
+int repair_dead(C* Q, long ldq, long sQ, int n1, int c, int nb, const uint32_t* dead, int batch, uint64_t seed,
+                int block_id, int* dead_count, cudaStream_t s);
+// eig.cu
 // Eigen-decomposition of the m x m Hermitian G per slice (G is overwritten):
 // top-R eigenvalues (descending) in lam (batch x R) and eigenvectors in
 // U (batch x m x R, row-major, leading dim ldu).  scratch: eig_scratch_bytes.

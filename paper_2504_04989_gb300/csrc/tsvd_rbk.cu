@@ -16,7 +16,11 @@
 // orth = three passes of [classical Gram-Schmidt against Q_{<i}, CholeskyQR]
 // (shifted CholeskyQR3): the first Cholesky is shifted so that it cannot break
 // down; columns found dependent afterwards are replaced by fresh orthonormal
-// directions.
+// directions.  It runs in FP64 on the FP64 path and in FP32 on the FP32 path
+// (FP64 on request): on GB300 FP64 arithmetic runs at 1/58 of FP32, and the
+// projected Krylov blocks are well conditioned, so FP32 keeps the basis
+// orthonormal to ~1e-7, far inside the path's singular-value tolerance.  The
+// Gram matrix G and its eigen-solve always run in FP64.
 #include <type_traits>
 
 #include "common.cuh"
@@ -54,14 +58,14 @@ struct RbkWs {
   C* Ah;
   T* Om;
   C* Omh;
-  double2* Q64;
-  C* Qt;
-  C* Wt;
-  double2* W64;
+  void* Ql;    // basis in the orthonormalisation precision (n1 x m per slice)
+  C* Qt;       // basis in the GEMM precision (alias of Ql when they agree)
+  void* Wl;    // Krylov block in the orthonormalisation precision (n1 x b)
+  C* Wt;       // Krylov block from the GEMMs (alias of Wl when they agree)
+  void* Pl;    // Gram-Schmidt coefficients (m x b)
+  void* Gl;    // block Gram matrix (b x b)
   C* CHt;
   double2* CH64;
-  double2* P64;
-  double2* Gs;
   double2* Rs;
   uint32_t* dead;
   int* counters;  // [0] status, [1] dead columns
@@ -78,24 +82,26 @@ struct RbkWs {
   size_t bytes;
 };
 
-template <typename T>
+template <typename T, typename L>
 static RbkWs<T> carve_rbk(void* base, const RbkDims& d) {
   using C = cx_t<T>;
+  using CL = cx_t<L>;
   constexpr bool dbl = std::is_same<T, double>::value;
+  constexpr bool same = std::is_same<T, L>::value;
   Carver cv(base);
   RbkWs<T> w;
   const size_t h = d.h;
   w.Ah = cv.take<C>(h * d.n1 * d.n2);
   w.Om = cv.take<T>((size_t)d.n3 * d.n2 * d.b);
   w.Omh = cv.take<C>(h * d.n2 * d.b);
-  w.Q64 = cv.take<double2>(h * d.n1 * d.m);
-  w.Qt = dbl ? (C*)w.Q64 : cv.take<C>(h * d.n1 * d.m);
-  w.W64 = cv.take<double2>(h * d.n1 * d.b);
-  w.Wt = dbl ? (C*)w.W64 : cv.take<C>(h * d.n1 * d.b);
+  w.Ql = cv.take<CL>(h * d.n1 * d.m);
+  w.Qt = same ? (C*)w.Ql : cv.take<C>(h * d.n1 * d.m);
+  w.Wl = cv.take<CL>(h * d.n1 * d.b);
+  w.Wt = same ? (C*)w.Wl : cv.take<C>(h * d.n1 * d.b);
+  w.Pl = cv.take<CL>(h * d.m * d.b);
+  w.Gl = cv.take<CL>(h * d.b * d.b);
   w.CHt = cv.take<C>(h * d.n2 * d.m);
   w.CH64 = dbl ? (double2*)w.CHt : cv.take<double2>(h * d.n2 * d.m);
-  w.P64 = cv.take<double2>(h * d.m * d.b);
-  w.Gs = cv.take<double2>(h * d.b * d.b);
   w.Rs = cv.take<double2>(h * d.b * d.b);
   w.dead = cv.take<uint32_t>(h * 4);
   w.counters = cv.take<int>(8);
@@ -136,52 +142,69 @@ static GemmArgs gemm(char opA, char opB, int M, int N, int K, double alpha, cons
   return g;
 }
 
-// Orthonormalise the nb leading columns of W64 (n1 x b per slice) against the
-// c finished columns of Q64 and write them to Q64 columns [c, c+nb).
-template <typename T>
+// Orthonormalise the nb leading columns of W (n1 x b per slice) against the c
+// finished columns of Q and write them to Q columns [c, c+nb), in the
+// precision L: shifted CholeskyQR3 (the shift makes the first Cholesky
+// succeed for any W; the next two passes restore orthogonality to rounding
+// level), each pass preceded by a classical Gram-Schmidt projection against
+// Q_{<i}; dependent columns are then replaced.
+template <typename T, typename L>
 static int orth_block(const RbkDims& d, RbkWs<T>& w, int c, int nb, int block_id, uint64_t seed, cudaStream_t s) {
+  using CL = cx_t<L>;
   const int n1 = d.n1, b = d.b, m = d.m, h = d.h;
   const long sQ = (long)n1 * m, sW = (long)n1 * b, sP = (long)m * b, sG = (long)b * b;
-  const double u = 1.1102230246251565e-16;
-  const double shift = 11.0 * ((double)n1 * nb + (double)nb * (nb + 1)) * u;
-  // shifted CholeskyQR3 (the shift makes the first Cholesky succeed for any
-  // W; the next two passes restore orthogonality to rounding level), each
-  // pass preceded by a classical Gram-Schmidt projection against Q_{<i}
+  CL* Q = (CL*)w.Ql;
+  CL* W = (CL*)w.Wl;
+  CL* P = (CL*)w.Pl;
+  CL* Gs = (CL*)w.Gl;
+  const size_t sk = std::is_same<L, double>::value ? w.splitk_elems : 2 * w.splitk_elems;
+  // FP64: Fukaya et al.'s shift 11 (n nb + nb (nb+1)) u ||W||^2 (trace as the norm
+  // bound); FP32: 1e-5 trace(G), above the FP32 Gram error ~ sqrt(n) u ||W||^2
+  const double shift = std::is_same<L, double>::value
+                           ? 11.0 * ((double)n1 * nb + (double)nb * (nb + 1)) * 1.1102230246251565e-16
+                           : 1e-5;
+  const double dead_rel = std::is_same<L, double>::value ? 1e-12 : 1e-7;
   for (int pass = 0; pass < 3; ++pass) {
     if (c > 0) {
       TSVD_STAGE("orth_cgs", s);
-      TSVD_TRY(cgemm<double2>(gemm('H', 'N', c, nb, n1, 1.0, w.Q64, m, sQ, w.W64, b, sW, 0.0, w.P64, nb, sP, h),
-                              w.splitk, w.splitk_elems, s));
-      TSVD_TRY(cgemm<double2>(gemm('N', 'N', n1, nb, c, -1.0, w.Q64, m, sQ, w.P64, nb, sP, 1.0, w.W64, b, sW, h),
-                              w.splitk, w.splitk_elems, s));
+      TSVD_TRY(cgemm<CL>(gemm('H', 'N', c, nb, n1, 1.0, Q, m, sQ, W, b, sW, 0.0, P, nb, sP, h), w.splitk, sk, s));
+      TSVD_TRY(cgemm<CL>(gemm('N', 'N', n1, nb, c, -1.0, Q, m, sQ, P, nb, sP, 1.0, W, b, sW, h), w.splitk, sk, s));
     }
     {
       TSVD_STAGE("orth_gram", s);
-      TSVD_TRY(cgemm<double2>(gemm('H', 'N', nb, nb, n1, 1.0, w.W64, b, sW, w.W64, b, sW, 0.0, w.Gs, b, sG, h),
-                              w.splitk, w.splitk_elems, s));
+      TSVD_TRY(cgemm<CL>(gemm('H', 'N', nb, nb, n1, 1.0, W, b, sW, W, b, sW, 0.0, Gs, b, sG, h), w.splitk, sk, s));
     }
     {
       TSVD_STAGE("orth_chol", s);
-      TSVD_TRY(chol_upper(w.Gs, b, sG, w.Rs, b, sG, nb, h, pass == 0 ? shift : 0.0, w.dead, s));
+      TSVD_TRY(chol_upper<CL>(Gs, b, sG, w.Rs, b, sG, nb, h, pass == 0 ? shift : 0.0, dead_rel, w.dead, s));
     }
     {
       TSVD_STAGE("orth_trsm", s);
-      TSVD_TRY(trsm_right_upper(w.W64, b, sW, w.Rs, b, sG, n1, nb, h, w.dead, s));
+      TSVD_TRY(trsm_right_upper<CL>(W, b, sW, w.Rs, b, sG, n1, nb, h, w.dead, s));
     }
   }
   {
     TSVD_STAGE("orth_repair", s);
-    TSVD_TRY(copy_c64(w.W64, b, sW, w.Q64 + c, m, sQ, n1, nb, h, s));
-    TSVD_TRY(repair_dead(w.Q64, m, sQ, n1, c, nb, w.dead, h, seed, block_id, w.counters + 1, s));
+    TSVD_TRY(copy_cx<CL>(W, b, sW, Q + c, m, sQ, n1, nb, h, s));
+    TSVD_TRY(repair_dead<CL>(Q, m, sQ, n1, c, nb, w.dead, h, seed, block_id, w.counters + 1, s));
   }
-  if (!std::is_same<T, double>::value) {
+  if (!std::is_same<T, L>::value) {
     TSVD_STAGE("convert", s);
-    TSVD_TRY(convert_c64_to_c32(w.Q64 + c, m, sQ, (float2*)w.Qt + c, m, sQ, n1, nb, h, s));
+    TSVD_TRY(convert_c64_to_c32((const double2*)Q + c, m, sQ, (float2*)w.Qt + c, m, sQ, n1, nb, h, s));
   }
   return TSVD_OK;
 }
 
-// to FP64 for the orthonormalisation (no-op when T is double)
+// Krylov block from the GEMM precision to the orthonormalisation precision
+template <typename T, typename L>
+static int to_orth(const RbkWs<T>& w, const RbkDims& d, int cols, cudaStream_t s) {
+  if (std::is_same<T, L>::value) return TSVD_OK;
+  TSVD_STAGE("convert", s);
+  const long sW = (long)d.n1 * d.b;
+  return convert_c32_to_c64((const float2*)w.Wt, d.b, sW, (double2*)w.Wl, d.b, sW, d.n1, cols, d.h, s);
+}
+
+// to FP64 (no-op when T is double)
 template <typename T>
 static int to64(const cx_t<T>* src, long lds, long ss, double2* dst, long ldd, long sd, int rows, int cols, int batch,
                 cudaStream_t s) {
@@ -190,11 +213,11 @@ static int to64(const cx_t<T>* src, long lds, long ss, double2* dst, long ldd, l
   return convert_c32_to_c64((const float2*)src, lds, ss, dst, ldd, sd, rows, cols, batch, s);
 }
 
-template <typename T>
+template <typename T, typename L>
 static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* Omega, T* U, T* S, T* V,
                    double* sig, void* ws, cudaStream_t s, tsvd_info* info) {
   using C = cx_t<T>;
-  RbkWs<T> w = carve_rbk<T>(ws, d);
+  RbkWs<T> w = carve_rbk<T, L>(ws, d);
   const int n1 = d.n1, n2 = d.n2, n3 = d.n3, h = d.h, b = d.b, m = d.m, R = d.R;
   const long sA = (long)n1 * n2, sQ = (long)n1 * m, sW = (long)n1 * b, sCH = (long)n2 * m, sO = (long)n2 * b;
   if (cudaMemsetAsync(w.counters, 0, 8 * sizeof(int), s) != cudaSuccess) return TSVD_ERR_CUDA;
@@ -219,8 +242,8 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
     TSVD_TRY(cgemm<C>(gemm('N', 'N', n1, b0, n2, 1.0, w.Ah, n2, sA, w.Omh, b, sO, 0.0, w.Wt, b, sW, h), w.splitk,
                       w.splitk_elems * 2, s));
   }
-  TSVD_TRY(to64<T>(w.Wt, b, sW, w.W64, b, sW, n1, b0, h, s));
-  TSVD_TRY(orth_block<T>(d, w, 0, b0, 0, p.seed, s));
+  TSVD_TRY((to_orth<T, L>(w, d, b0, s)));
+  TSVD_TRY((orth_block<T, L>(d, w, 0, b0, 0, p.seed, s)));
   int c = b0, pw = b0;
   for (int i = 1; i <= d.q && c < m; ++i) {
     const int bi = std::min(b, m - c);
@@ -234,8 +257,8 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
     TSVD_TRY(cgemm<C>(gemm('N', 'N', n1, bi, n2, 1.0, w.Ah, n2, sA, w.CHt + (c - pw), m, sCH, 0.0, w.Wt, b, sW, h),
                       w.splitk, w.splitk_elems * 2, s));
     }
-    TSVD_TRY(to64<T>(w.Wt, b, sW, w.W64, b, sW, n1, bi, h, s));
-    TSVD_TRY(orth_block<T>(d, w, c, bi, i, p.seed, s));
+    TSVD_TRY((to_orth<T, L>(w, d, bi, s)));
+    TSVD_TRY((orth_block<T, L>(d, w, c, bi, i, p.seed, s)));
     c += bi;
     pw = bi;
   }
@@ -292,12 +315,18 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
 
 using namespace tsvd;
 
+static size_t rbk_bytes(const RbkDims& d, const tsvd_params* p) {
+  if (p->precision == TSVD_FP64) return carve_rbk<double, double>(nullptr, d).bytes;
+  if (p->flags & TSVD_FLAG_FP64_QR) return carve_rbk<float, double>(nullptr, d).bytes;
+  return carve_rbk<float, float>(nullptr, d).bytes;
+}
+
 extern "C" int tsvd_rbk_workspace_size(int n1, int n2, int n3, const tsvd_params* params, size_t* bytes) {
   if (!bytes) return TSVD_ERR_INVALID_ARG;
   RbkDims d;
   TSVD_TRY(rbk_dims(n1, n2, n3, params, &d));
   if (params->precision == TSVD_MIXED_TF32 || params->precision == TSVD_MIXED_BF16) return TSVD_ERR_UNSUPPORTED;
-  *bytes = (params->precision == TSVD_FP64) ? carve_rbk<double>(nullptr, d).bytes : carve_rbk<float>(nullptr, d).bytes;
+  *bytes = rbk_bytes(d, params);
   return TSVD_OK;
 }
 
@@ -309,15 +338,16 @@ extern "C" int tsvd_rbk(const void* A, int n1, int n2, int n3, const tsvd_params
   if (!A || !U || !S || !V || !ws) return TSVD_ERR_INVALID_ARG;
   if (((uintptr_t)ws & 255) != 0) return TSVD_ERR_INVALID_ARG;
   if (params->precision == TSVD_MIXED_TF32 || params->precision == TSVD_MIXED_BF16) return TSVD_ERR_UNSUPPORTED;
-  const bool dbl = params->precision == TSVD_FP64;
-  const size_t need = dbl ? carve_rbk<double>(nullptr, d).bytes : carve_rbk<float>(nullptr, d).bytes;
-  if (ws_bytes < need) return TSVD_ERR_WORKSPACE;
+  if (ws_bytes < rbk_bytes(d, params)) return TSVD_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
-  if (dbl)
-    return rbk_run<double>((const double*)A, d, *params, (const double*)Omega, (double*)U, (double*)S, (double*)V,
-                           sigma_hat, ws, s, info);
-  return rbk_run<float>((const float*)A, d, *params, (const float*)Omega, (float*)U, (float*)S, (float*)V, sigma_hat,
-                        ws, s, info);
+  if (params->precision == TSVD_FP64)
+    return rbk_run<double, double>((const double*)A, d, *params, (const double*)Omega, (double*)U, (double*)S,
+                                   (double*)V, sigma_hat, ws, s, info);
+  if (params->flags & TSVD_FLAG_FP64_QR)
+    return rbk_run<float, double>((const float*)A, d, *params, (const float*)Omega, (float*)U, (float*)S, (float*)V,
+                                  sigma_hat, ws, s, info);
+  return rbk_run<float, float>((const float*)A, d, *params, (const float*)Omega, (float*)U, (float*)S, (float*)V,
+                               sigma_hat, ws, s, info);
 }
 
 extern "C" const char* tsvd_strerror(int code) {

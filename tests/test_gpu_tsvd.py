@@ -36,22 +36,23 @@ def weights(n3):
     return w
 
 
-def run_gpu(api, X, R, P, q, precision, omega=None, seed=0):
+def run_gpu(api, X, R, P, q, precision, omega=None, seed=0, fp64_qr=False):
     dt = torch.float64 if precision == "fp64" else torch.float32
     om = None if omega is None else dev(omega.astype(np.float32) if dt == torch.float32 else omega, dt)
-    U, S, V, sig, info = api.rbk(dev(X, dt), R, P, q, seed=seed, precision=precision, omega=om, return_info=True)
+    U, S, V, sig, info = api.rbk(dev(X, dt), R, P, q, seed=seed, precision=precision, omega=om, return_info=True,
+                                 fp64_qr=fp64_qr)
     torch.cuda.synchronize()
     assert info["status"] == 0, info
     return U.double().cpu().numpy(), S.double().cpu().numpy(), V.double().cpu().numpy(), sig.cpu().numpy(), info
 
 
-def check_against_oracle(api, orc, X, R, P, q, precision, omega=None, seed=0, sig_floor=0.0):
+def check_against_oracle(api, orc, X, R, P, q, precision, omega=None, seed=0, sig_floor=0.0, fp64_qr=False):
     n3 = X.shape[0]
     Xin = X.astype(np.float32).astype(np.float64) if precision != "fp64" else X
     om_in = None
     if omega is not None:
         om_in = omega.astype(np.float32).astype(np.float64) if precision != "fp64" else omega
-    U, S, V, sig, info = run_gpu(api, Xin, R, P, q, precision, om_in, seed)
+    U, S, V, sig, info = run_gpu(api, Xin, R, P, q, precision, om_in, seed, fp64_qr)
     ref = orc.rtsvd_fourier(Xin, R, P, q, omega=om_in, seed=seed)
     s_ref = ref["sig"]
     mask = s_ref > sig_floor * s_ref.max()
@@ -79,10 +80,11 @@ def test_c1_fp64_philox_omega(api, orc):
     check_against_oracle(api, orc, X, 10, 5, 2, "fp64", seed=12345)
 
 
-def test_c1_fp32(api, orc):
+@pytest.mark.parametrize("fp64_qr", [False, True])
+def test_c1_fp32(api, orc, fp64_qr):
     X = wl.make_c1(0)
     om = wl.omega(64, 15, 16, seed=0)
-    check_against_oracle(api, orc, X, 10, 5, 2, "fp32", omega=om)
+    check_against_oracle(api, orc, X, 10, 5, 2, "fp32", omega=om, fp64_qr=fp64_qr)
 
 
 @pytest.mark.parametrize("n1,n2,n3,R,P,q", [
