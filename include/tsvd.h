@@ -154,6 +154,27 @@ TSVD_API int tproj_backward_workspace_size(int n1, int m, int n2, int n3, int pr
 TSVD_API int tproj_backward(const void* Q, const void* A, const void* dY, void* dQ, void* dA, int n1, int m, int n2, int n3,
                    int precision, void* ws, size_t ws_bytes, void* stream);
 
+/*
+ * tprod_noalloc -- the t-product C = A * B of tprod(), for callers that cannot
+ * allocate device memory (an arena or pool that must not grow, a plug-in whose
+ * host process owns every device allocation, a real-time loop where an
+ * allocation would stall).  The paper has no counterpart: this is a service of
+ * the library.  It takes no workspace: its scratch is a fixed 16 MiB array
+ * inside the library (reserved on every GPU that loads the library until the
+ * process exits), and it calls no allocating routine.
+ *   A device (n3, n1, n2), B device (n3, n2, n4), C device out (n3, n1, n4);
+ *   precision TSVD_FP64 (double) or TSVD_FP32 (float).
+ * Limit: the three half-spectrum operands, (floor(n3/2)+1) * (n1*n2 + n2*n4 +
+ * n1*n4) complex elements (8 bytes each in FP32, 16 in FP64, each array rounded
+ * up to 256 bytes), must fit in 16 MiB; larger problems return
+ * TSVD_ERR_UNSUPPORTED and launch nothing.
+ * All calls share the array: calls whose kernels overlap on the GPU race.  The
+ * first call on each device looks up the array's device address, so make it
+ * before capturing a CUDA graph.
+ */
+TSVD_API int tprod_noalloc(const void* A, const void* B, void* C, int n1, int n2, int n4, int n3, int precision,
+                           void* stream);
+
 /* Philox4x32-10 Gaussian draw of the test tensor on the device (the same
  * definition as tsvd_rbk uses when Omega is NULL), for inspection and tests:
  * out (device, double) receives n normals of (seed, stream, tensor_id). */
