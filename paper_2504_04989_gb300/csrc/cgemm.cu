@@ -28,12 +28,14 @@ struct GemmCfg<float2> {
 constexpr int GBM = 64, GBN = 64;
 
 template <typename C, bool AH, bool BH>
-__global__ void __launch_bounds__(256) k_cgemm(GemmArgs g, C* __restrict__ ws, int ksplit, int kchunk, int tiles_m) {
+__global__ void __launch_bounds__(256) k_cgemm(GemmArgs g, C* __restrict__ ws, int ksplit, int kchunk, int tiles_m,
+                                               int herm_upper) {
   constexpr int BK = GemmCfg<C>::BK;
   using R = typename GemmCfg<C>::R;
   __shared__ __align__(16) C As[BK][GBM];
   __shared__ __align__(16) C Bs[BK][GBN];
   const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+  if (herm_upper && tm > tn) return;  // Hermitian product: the lower tiles are mirrored afterwards
   const int bi = blockIdx.z / ksplit, kz = blockIdx.z % ksplit;
   const int m0 = tm * GBM, n0 = tn * GBN;
   const C* __restrict__ A = (const C*)g.A + (long)bi * g.sA;
@@ -128,8 +130,21 @@ int choose_ksplit(int M, int N, int K, int batch, size_t splitk_elems) {
   return ks;
 }
 
+// lower triangle of each slice's square C from the conjugate of the upper one
 template <typename C>
-int cgemm(const GemmArgs& g, void* splitk_ws, size_t splitk_elems, cudaStream_t s) {
+__global__ void k_mirror_lower(C* __restrict__ Cm, long ldc, long sC, int n, int batch) {
+  const long total = (long)batch * n * n;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int j = idx % n;
+    const long t = idx / n;
+    const int i = t % n;
+    const int b = t / n;
+    if (i > j) Cm[(long)b * sC + (long)i * ldc + j] = cconj(Cm[(long)b * sC + (long)j * ldc + i]);
+  }
+}
+
+template <typename C>
+static int cgemm_impl(const GemmArgs& g, void* splitk_ws, size_t splitk_elems, cudaStream_t s, int herm) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return TSVD_OK;
   if (g.batch > 65535) return TSVD_ERR_UNSUPPORTED;
   if (g.beta != 0.0 && g.beta != 1.0) return TSVD_ERR_INVALID_ARG;
@@ -144,18 +159,36 @@ int cgemm(const GemmArgs& g, void* splitk_ws, size_t splitk_elems, cudaStream_t 
   dim3 grid(tiles_m * tiles_n, 1, g.batch * ks);
   const bool ah = (g.opA == 'H'), bh = (g.opB == 'H');
   C* ws = (C*)splitk_ws;
-  if (!ah && !bh) k_cgemm<C, false, false><<<grid, 256, 0, s>>>(g, ws, ks, kchunk, tiles_m);
-  else if (ah && !bh) k_cgemm<C, true, false><<<grid, 256, 0, s>>>(g, ws, ks, kchunk, tiles_m);
-  else if (!ah && bh) k_cgemm<C, false, true><<<grid, 256, 0, s>>>(g, ws, ks, kchunk, tiles_m);
-  else k_cgemm<C, true, true><<<grid, 256, 0, s>>>(g, ws, ks, kchunk, tiles_m);
+  if (!ah && !bh) k_cgemm<C, false, false><<<grid, 256, 0, s>>>(g, ws, ks, kchunk, tiles_m, herm);
+  else if (ah && !bh) k_cgemm<C, true, false><<<grid, 256, 0, s>>>(g, ws, ks, kchunk, tiles_m, herm);
+  else if (!ah && bh) k_cgemm<C, false, true><<<grid, 256, 0, s>>>(g, ws, ks, kchunk, tiles_m, herm);
+  else k_cgemm<C, true, true><<<grid, 256, 0, s>>>(g, ws, ks, kchunk, tiles_m, herm);
   TSVD_LAUNCHED();
   if (ks > 1) {
     const long total = (long)g.batch * g.M * g.N;
     k_splitk_reduce<C><<<std::min<long>(cdiv(total, 256), 4096), 256, 0, s>>>(ws, ks, g);
     TSVD_LAUNCHED();
   }
+  if (herm) {
+    const long total = (long)g.batch * g.M * g.M;
+    k_mirror_lower<C><<<std::min<long>(cdiv(total, 256), 8192), 256, 0, s>>>((C*)g.C, g.ldc, g.sC, g.M, g.batch);
+    TSVD_LAUNCHED();
+  }
   return TSVD_OK;
 }
+
+template <typename C>
+int cgemm(const GemmArgs& g, void* splitk_ws, size_t splitk_elems, cudaStream_t s) {
+  return cgemm_impl<C>(g, splitk_ws, splitk_elems, s, 0);
+}
+
+template <typename C>
+int cgemm_herm(const GemmArgs& g, void* splitk_ws, size_t splitk_elems, cudaStream_t s) {
+  if (g.M != g.N || g.beta != 0.0) return TSVD_ERR_INVALID_ARG;
+  return cgemm_impl<C>(g, splitk_ws, splitk_elems, s, 1);
+}
+template int cgemm_herm<double2>(const GemmArgs&, void*, size_t, cudaStream_t);
+template int cgemm_herm<float2>(const GemmArgs&, void*, size_t, cudaStream_t);
 template int cgemm<double2>(const GemmArgs&, void*, size_t, cudaStream_t);
 template int cgemm<float2>(const GemmArgs&, void*, size_t, cudaStream_t);
 

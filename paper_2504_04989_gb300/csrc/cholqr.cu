@@ -63,15 +63,21 @@ __global__ void __launch_bounds__(256) k_chol_upper(const GC* __restrict__ G, lo
     }
     if (tid == 0) S[pidx(j, j, nb)] = make_double2(r, 0);
     __syncthreads();
-    const int nt = nb - j - 1;
-    for (int e = tid; e < nt * nt; e += blockDim.x) {
-      const int i = j + 1 + e / nt, k = j + 1 + e % nt;
-      if (k < i) continue;
-      const double2 a = S[pidx(j, i, nb)], c = S[pidx(j, k, nb)];
-      double2 t = S[pidx(i, k, nb)];
-      t.x -= a.x * c.x + a.y * c.y;  // t -= conj(a) * c
-      t.y -= a.x * c.y - a.y * c.x;
-      S[pidx(i, k, nb)] = t;
+    // trailing update S(i, k) -= conj(S(j, i)) S(j, k) for j < i <= k, one warp per row i
+    const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const int offj = pidx(j, j, nb);
+    for (int i = j + 1 + warp; i < nb; i += nwarp) {
+      const double2 a = S[offj + (i - j)];
+      const int offi = pidx(i, i, nb);
+      for (int k = i + lane; k < nb; k += 32) {
+        const double2 c = S[offj + (k - j)];
+        double2 t = S[offi + (k - i)];
+        t.x = fma(-a.x, c.x, t.x);
+        t.x = fma(-a.y, c.y, t.x);
+        t.y = fma(-a.x, c.y, t.y);
+        t.y = fma(a.y, c.x, t.y);
+        S[offi + (k - i)] = t;
+      }
     }
     __syncthreads();
   }

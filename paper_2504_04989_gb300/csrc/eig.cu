@@ -22,15 +22,17 @@ namespace cg = cooperative_groups;
 
 namespace tsvd {
 
+constexpr int HETRD_CLUSTER = 4;
+
 struct EigScratch {
   double* d;       // [batch][m] diagonal of T
   double* f;       // [batch][m] off-diagonal |alpha_j|
   double2* alpha;  // [batch][m] complex off-diagonals of T'
   double2* delta;  // [batch][m] phases making T real
   double2* Hv;     // [batch][m][m] Householder vectors (row j, columns j+1..m-1)
-  double2* pbuf;   // [batch][m] matrix-vector product shared inside a cluster
-  double* Z;       // [batch][m][R] real eigenvectors of T
-  double* lu;      // [batch][6][m][R] inverse-iteration work
+  double2* pbuf;   // [batch][HETRD_CLUSTER][m] partial matrix-vector products of a cluster
+  double* Z;       // [batch][R][m] real eigenvectors of T (vector-contiguous)
+  double* lu;      // [batch][5][m][R] inverse-iteration LU factors
   double* tnorm;   // [batch]
 };
 
@@ -42,9 +44,9 @@ static EigScratch carve_eig(void* base, int m, int R, int batch, size_t* bytes) 
   e.alpha = cv.take<double2>((size_t)batch * m);
   e.delta = cv.take<double2>((size_t)batch * m);
   e.Hv = cv.take<double2>((size_t)batch * m * m);
-  e.pbuf = cv.take<double2>((size_t)batch * m);
+  e.pbuf = cv.take<double2>((size_t)batch * HETRD_CLUSTER * m);
   e.Z = cv.take<double>((size_t)batch * m * R);
-  e.lu = cv.take<double>((size_t)batch * 6 * m * R);
+  e.lu = cv.take<double>((size_t)batch * 5 * m * R);
   e.tnorm = cv.take<double>((size_t)batch);
   if (bytes) *bytes = cv.bytes();
   return e;
@@ -59,20 +61,25 @@ size_t eig_scratch_bytes(int m, int R, int batch) {
 __device__ __forceinline__ double2 ldcg2(const double2* p) { return __ldcg(p); }
 
 // ---------------------------------------------------------------------------
-// Householder tridiagonalisation, one cluster of CL CTAs per slice.  Rows of
-// the trailing block are owned round-robin (global row g by CTA g mod CL).
-// Step j: every CTA reads row j (x = conj of it) and forms the same
-// v = (x - alpha e_1)/||.||, alpha = -e^{i arg x_0} ||x||; each CTA computes
-// p = 2 A v on its rows; after a cluster barrier every CTA reads all of p,
-// forms w = p - (v^H p) v and updates its rows A -= v w^H + w v^H (both
-// triangles, so rows stay contiguous).  Data another CTA wrote is read with
-// L2-coherent loads after the barrier (release / acquire at cluster scope).
+// Householder tridiagonalisation, one cluster of CL CTAs per slice; only the
+// lower triangle of G is read and updated.  Rows of the trailing block are
+// owned round-robin (global row g by CTA g mod CL).  Step j:
+//   x = G(j+1:, j), alpha = -e^{i arg x_0} ||x||, v = (x - alpha e_1)/||.||
+//   (every CTA forms the same v);
+//   p = 2 A v from the lower triangle: each CTA adds, for its rows r, the row
+//   part sum_{k<=r} A(r,k) v_k to p_r and the transposed part conj(A(r,k)) v_r
+//   to p_k (k < r) into a shared partial, then the CL partials are summed
+//   after a cluster barrier;
+//   w = p - (v^H p) v;  A(r,k) -= v_r conj(w_k) + w_r conj(v_k) for k <= r.
+// Data another CTA wrote is read with L2-coherent loads after the barrier
+// (release / acquire at cluster scope).
 // ---------------------------------------------------------------------------
 template <int CL>
 __global__ void __launch_bounds__(512) k_hetrd(double2* __restrict__ G, long ldg, long sG, int m, EigScratch e) {
   extern __shared__ __align__(16) double2 sh[];
-  double2* v = sh;      // [m]
-  double2* p = sh + m;  // [m]
+  double2* v = sh;            // [m]
+  double2* p = sh + m;        // [m] full product / w
+  double2* pw = sh + 2 * m;   // [nwarp][m] per-warp partial products (fixed-order sum: deterministic)
   __shared__ double red[64];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (CL > 1) ? (int)cluster.block_rank() : 0;
@@ -80,22 +87,24 @@ __global__ void __launch_bounds__(512) k_hetrd(double2* __restrict__ G, long ldg
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   G += (long)b * sG;
   double2* Hv = e.Hv + (long)b * m * m;
-  double2* pb = e.pbuf + (long)b * m;
+  double2* pb = e.pbuf + (long)b * CL * m;  // [CL][m] partial products of the cluster's CTAs
+  double2* mine = pw + (long)warp * m;
   for (int j = 0; j < m - 1; ++j) {
     const int n = m - j - 1;
-    const double2* rowj = G + (long)j * ldg + j + 1;
     double part = 0;
     for (int i = tid; i < n; i += blockDim.x) {
-      const double2 x = cconj(ldcg2(rowj + i));
+      const double2 x = ldcg2(G + (long)(j + 1 + i) * ldg + j);
       v[i] = x;
       part += cabs2(x);
     }
+    for (int i = lane; i < n; i += 32) mine[i] = make_double2(0, 0);
     const double nrm2 = block_sum(part, red);  // synchronises: v visible
     const double2 x0 = v[0];
     const double djj = ldcg2(G + (long)j * ldg + j).x;
     __syncthreads();
     if (rank == 0 && tid == 0) e.d[(long)b * m + j] = djj;
     const bool skip = !(nrm2 > 0.0);  // identical in every CTA of the cluster
+    const int r0 = ((rank - (j + 1)) % CL + CL) % CL;
     if (!skip) {
       const double nrm = sqrt(nrm2), ax0 = sqrt(cabs2(x0));
       const double2 ph = (ax0 > 0) ? cscale(x0, 1.0 / ax0) : make_double2(1, 0);
@@ -110,14 +119,33 @@ __global__ void __launch_bounds__(512) k_hetrd(double2* __restrict__ G, long ldg
       }
       if (rank == 0 && tid == 0) e.alpha[(long)b * m + j] = alpha;
       __syncthreads();
-      // p = 2 A v on the rows this CTA owns: global row g = j+1+r with g % CL == rank
-      const int r0 = ((rank - (j + 1)) % CL + CL) % CL;
+      // this warp's rows: row part into mine[r], transposed part conj(A(r,k)) v_r into mine[k]
       for (int r = r0 + warp * CL; r < n; r += nwarp * CL) {
         const double2* row = G + (long)(j + 1 + r) * ldg + j + 1;
+        const double2 vr = v[r];
         double2 acc = make_double2(0, 0);
-        for (int k = lane; k < n; k += 32) cfma(acc, row[k], v[k]);
+        for (int k = lane; k <= r; k += 32) {
+          const double2 a = row[k];
+          cfma(acc, a, v[k]);
+          if (k < r) {  // t += conj(a) v_r
+            double2 t = mine[k];
+            t.x = fma(a.x, vr.x, t.x);
+            t.x = fma(a.y, vr.y, t.x);
+            t.y = fma(a.x, vr.y, t.y);
+            t.y = fma(-a.y, vr.x, t.y);
+            mine[k] = t;
+          }
+        }
         acc = warp_sum(acc);
-        if (lane == 0) __stcg(pb + r, cscale(acc, 2.0));
+        __syncwarp();
+        if (lane == 0) mine[r] = cadd(mine[r], acc);
+        __syncwarp();
+      }
+      __syncthreads();
+      for (int i = tid; i < n; i += blockDim.x) {
+        double2 s = make_double2(0, 0);
+        for (int w = 0; w < nwarp; ++w) s = cadd(s, pw[(long)w * m + i]);
+        __stcg(pb + (long)rank * m + i, s);
       }
     } else {
       for (int i = tid; i < n; i += blockDim.x)
@@ -129,24 +157,34 @@ __global__ void __launch_bounds__(512) k_hetrd(double2* __restrict__ G, long ldg
     if (!skip) {
       double2 kp = make_double2(0, 0);
       for (int i = tid; i < n; i += blockDim.x) {
-        const double2 pi = ldcg2(pb + i);
+        double2 pi = make_double2(0, 0);
+#pragma unroll
+        for (int c = 0; c < CL; ++c) pi = cadd(pi, ldcg2(pb + (long)c * m + i));
+        pi = cscale(pi, 2.0);
         p[i] = pi;
         cfmac(kp, v[i], pi);
       }
       const double K = block_sum2(kp, red).x;
       for (int i = tid; i < n; i += blockDim.x) p[i] = csub(p[i], cscale(v[i], K));  // p <- w
       __syncthreads();
-      const int r0 = ((rank - (j + 1)) % CL + CL) % CL;
-      const int nown = (n > r0) ? (n - r0 + CL - 1) / CL : 0;
-      for (long idx = tid; idx < (long)nown * n; idx += blockDim.x) {
-        const int r = r0 + (int)(idx / n) * CL, k = (int)(idx % n);
-        double2* g = G + (long)(j + 1 + r) * ldg + j + 1 + k;
-        const double2 vr = v[r], wr = p[r], vk = v[k], wk = p[k];
-        double2 t = *g;
-        // t -= v_r conj(w_k) + w_r conj(v_k)
-        t.x -= vr.x * wk.x + vr.y * wk.y + wr.x * vk.x + wr.y * vk.y;
-        t.y -= vr.y * wk.x - vr.x * wk.y + wr.y * vk.x - wr.x * vk.y;
-        *g = t;
+      // lower-triangle update of this CTA's rows, one warp per row
+      for (int r = r0 + warp * CL; r < n; r += nwarp * CL) {
+        double2* row = G + (long)(j + 1 + r) * ldg + j + 1;
+        const double2 vr = v[r], wr = p[r];
+        for (int k = lane; k <= r; k += 32) {
+          const double2 vk = v[k], wk = p[k];
+          double2 t = row[k];
+          // t -= v_r conj(w_k) + w_r conj(v_k), as four fused multiply-adds per component
+          t.x = fma(-vr.x, wk.x, t.x);
+          t.x = fma(-vr.y, wk.y, t.x);
+          t.x = fma(-wr.x, vk.x, t.x);
+          t.x = fma(-wr.y, vk.y, t.x);
+          t.y = fma(-vr.y, wk.x, t.y);
+          t.y = fma(vr.x, wk.y, t.y);
+          t.y = fma(-wr.y, vk.x, t.y);
+          t.y = fma(wr.x, vk.y, t.y);
+          row[k] = t;
+        }
       }
     }
     if (CL > 1) cluster.sync();
@@ -178,38 +216,43 @@ __global__ void __launch_bounds__(512) k_hetrd(double2* __restrict__ G, long ldg
 // P_i = (d_{i-1} - x) P_{i-1} - f_{i-2}^2 P_{i-2}, i.e. negative ratios
 // q_i = P_i / P_{i-1}; a zero ratio is replaced by -pivmin.  The pair
 // (P_i, P_{i-1}) is rescaled by powers of two to stay in range.
-__device__ int sturm_count(const double* d, const double* f2, int m, double x, double pivmin) {
+__device__ __forceinline__ int sturm_count(const double* d, const double* f2, int m, double x, double pivmin) {
   double pm = 1.0, p = d[0] - x;
   if (p == 0.0) p = -pivmin;
-  int cnt = (p < 0.0);
+  int cnt = (int)((unsigned long long)__double_as_longlong(p) >> 63);
   for (int i = 1; i < m; ++i) {
-    double pn = (d[i] - x) * p - f2[i - 1] * pm;
-    if (pn == 0.0) pn = -pivmin * p;
-    cnt += ((pn < 0.0) != (p < 0.0));
+    double pn = fma(d[i] - x, p, -f2[i - 1] * pm);
+    long long bn = __double_as_longlong(pn);
+    if ((bn << 1) == 0) {  // zero ratio
+      pn = -pivmin * p;
+      bn = __double_as_longlong(pn);
+    }
+    cnt += (int)((unsigned long long)(bn ^ __double_as_longlong(p)) >> 63);
     pm = p;
     p = pn;
-    const double s = fabs(p) + fabs(pm);
-    if (s > 0x1p+600) {
-      p *= 0x1p-600;
-      pm *= 0x1p-600;
-    } else if (s < 0x1p-600) {
-      p *= 0x1p+600;
-      pm *= 0x1p+600;
+    // keep the pair in range: rescale both by a power of two when the exponent of p leaves +-600
+    const int ex = (int)((bn >> 52) & 0x7ff) - 1023;
+    if (ex > 600 || ex < -600) {
+      const double sc = __longlong_as_double((long long)(1023 - ex) << 52);
+      p *= sc;
+      pm *= sc;
     }
   }
   return cnt;
 }
 
-// One CTA per slice, one thread per wanted eigenpair r < R (the (r+1)-th
-// largest): bisection, then inverse iteration (three solves).
-__global__ void __launch_bounds__(128) k_tridiag_pairs(int m, int R, EigScratch e, double* __restrict__ lam_out) {
-  extern __shared__ __align__(16) double tsm[];
-  double* d = tsm;       // [m] scaled diagonal
-  double* f = tsm + m;   // [m] scaled off-diagonal
-  double* f2 = f + m;    // [m] squares
-  __shared__ double s_scale;
-  const int b = blockIdx.x, r = threadIdx.x;
-  if (r == 0) {
+// Multisection: one warp per wanted eigenvalue (the (r+1)-th largest of the
+// slice's scaled T); per step the 32 lanes count at 32 interior points of the
+// bracket, so the bracket shrinks 33-fold per step.
+constexpr int BIS_WARPS = 4;
+__global__ void __launch_bounds__(BIS_WARPS * 32) k_bisect(int m, int R, EigScratch e, double* __restrict__ lam_out) {
+  extern __shared__ __align__(16) double bsm[];
+  double* d = bsm;      // [m] scaled diagonal
+  double* f2 = bsm + m; // [m] scaled squared off-diagonal
+  __shared__ double s_scale, s_lo, s_hi;
+  const int b = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = blockIdx.x * BIS_WARPS + warp;
+  if (threadIdx.x == 0) {
     const double tn = e.tnorm[b];
     s_scale = (tn > 0.0 && isfinite(tn)) ? 1.0 / tn : 1.0;
   }
@@ -218,110 +261,161 @@ __global__ void __launch_bounds__(128) k_tridiag_pairs(int m, int R, EigScratch 
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     d[i] = e.d[(long)b * m + i] * sc;
     const double fi = (i < m - 1) ? e.f[(long)b * m + i] * sc : 0.0;
+    f2[i] = fi * fi;
+  }
+  if (threadIdx.x == 0) {  // Gershgorin bracket of the scaled T
+    double lo = e.d[(long)b * m] * sc, hi = lo;
+    for (int i = 0; i < m; ++i) {
+      const double fl = (i > 0) ? e.f[(long)b * m + i - 1] * sc : 0.0;
+      const double fr = (i < m - 1) ? e.f[(long)b * m + i] * sc : 0.0;
+      const double di = e.d[(long)b * m + i] * sc;
+      lo = fmin(lo, di - fl - fr);
+      hi = fmax(hi, di + fl + fr);
+    }
+    s_lo = lo;
+    s_hi = hi;
+  }
+  __syncthreads();
+  if (r >= R) return;
+  if (!(e.tnorm[b] > 0.0)) {  // T = 0 (zero data): every eigenvalue is 0
+    if (lane == 0) lam_out[(long)b * R + r] = 0.0;
+    return;
+  }
+  const double tn = fmax(fabs(s_lo), fabs(s_hi));
+  const double pivmin = DBL_MIN * 0x1p+64;
+  double lo = s_lo - (4.0 * DBL_EPSILON * tn + pivmin);
+  double hi = s_hi + (4.0 * DBL_EPSILON * tn + pivmin);
+  const int idx = m - 1 - r;  // ascending index of the wanted eigenvalue
+  for (int it = 0; it < 64; ++it) {
+    const double w = hi - lo;
+    if (w <= 2.0 * DBL_EPSILON * (fabs(lo) + fabs(hi)) + pivmin) break;
+    const double x = lo + w * ((double)(lane + 1) / 33.0);
+    const unsigned above = __ballot_sync(0xffffffffu, sturm_count(d, f2, m, x, pivmin) > idx);
+    const int first = above ? __ffs(above) - 1 : 32;  // lowest point with more than idx values below it
+    const double nlo = (first == 0) ? lo : lo + w * ((double)first / 33.0);
+    const double nhi = (first == 32) ? hi : lo + w * ((double)(first + 1) / 33.0);
+    if (nlo == lo && nhi == hi) break;
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) lam_out[(long)b * R + r] = 0.5 * (lo + hi) / sc;
+}
+
+// One thread per wanted eigenpair r (the (r+1)-th largest), TP_THREADS pairs
+// per CTA: inverse iteration (three solves) with a partially pivoted LU of
+// T - lam I for the eigenvalue found by k_bisect.  The LU factors stream
+// from global memory (coalesced across the CTA's threads); the iterate lives
+// in shared memory, so the dependent chain of each solve never waits on L2.
+constexpr int TP_THREADS = 32;
+
+__global__ void __launch_bounds__(TP_THREADS) k_tridiag_pairs(int m, int R, EigScratch e,
+                                                              const double* __restrict__ lam_out) {
+  extern __shared__ __align__(16) double tsm[];
+  double* d = tsm;      // [m] scaled diagonal
+  double* f = tsm + m;  // [m] scaled off-diagonal
+  double* f2 = f + m;   // [m] squares
+  double* xs = f2 + m;  // [m][TP_THREADS] iterates
+  __shared__ double s_scale;
+  const int b = blockIdx.y, t = threadIdx.x, r = blockIdx.x * TP_THREADS + t;
+  if (t == 0) {
+    const double tn = e.tnorm[b];
+    s_scale = (tn > 0.0 && isfinite(tn)) ? 1.0 / tn : 1.0;
+  }
+  __syncthreads();
+  const double sc = s_scale;
+  for (int i = t; i < m; i += blockDim.x) {
+    d[i] = e.d[(long)b * m + i] * sc;
+    const double fi = (i < m - 1) ? e.f[(long)b * m + i] * sc : 0.0;
     f[i] = fi;
     f2[i] = fi * fi;
   }
   __syncthreads();
   if (r >= R) return;
-  if (!(e.tnorm[b] > 0.0)) {  // T = 0 (zero data): every eigenvalue is 0, vectors e_r
-    lam_out[(long)b * R + r] = 0.0;
-    double* Z0 = e.Z + (long)b * m * R;
-    for (int i = 0; i < m; ++i) Z0[(long)i * R + r] = (i == r) ? 1.0 : 0.0;
+  double* Z = e.Z + ((long)b * R + r) * m;  // vector r, contiguous
+  if (!(e.tnorm[b] > 0.0)) {  // T = 0 (zero data): vectors e_r
+    for (int i = 0; i < m; ++i) Z[i] = (i == r) ? 1.0 : 0.0;
     return;
   }
-  double lo = d[0], hi = d[0];
-  for (int i = 0; i < m; ++i) {
-    const double fl = (i > 0) ? f[i - 1] : 0.0, fr = f[i];
-    lo = fmin(lo, d[i] - fl - fr);
-    hi = fmax(hi, d[i] + fl + fr);
-  }
-  const double tn = fmax(fabs(lo), fabs(hi));
-  const double pivmin = DBL_MIN * 0x1p+64;
-  lo -= 4.0 * DBL_EPSILON * tn + pivmin;
-  hi += 4.0 * DBL_EPSILON * tn + pivmin;
-  const int idx = m - 1 - r;  // ascending index of the wanted eigenvalue
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (hi - lo <= 2.0 * DBL_EPSILON * (fabs(lo) + fabs(hi)) + pivmin || mid == lo || mid == hi) break;
-    if (sturm_count(d, f2, m, mid, pivmin) > idx) hi = mid;
-    else lo = mid;
-  }
-  const double lam = 0.5 * (lo + hi);
-  lam_out[(long)b * R + r] = lam / sc;
+  double tn = 0;
+  for (int i = 0; i < m; ++i) tn = fmax(tn, fabs(d[i]) + ((i > 0) ? f[i - 1] : 0.0) + f[i]);
+  const double lam = lam_out[(long)b * R + r] * sc;
 
-  // element i of work array a at lu[((b*6 + a)*m + i)*R + r] (coalesced over r)
-  double* base = e.lu + (long)b * 6 * m * R + r;
+  // factor element i of array a at lu[((b*5 + a)*m + i)*R + r] (coalesced over r)
+  // a: 0 multiplier, 1 reciprocal U diagonal, 2 U first super, 3 U second super, 4 row swap (0 / 1)
+  double* base = e.lu + (long)b * 5 * m * R + r;
 #define LU(a, i) base[((long)(a) * m + (i)) * R]
-  // a: 0 multipliers, 1 reciprocal U diagonal, 2 U first super, 3 U second super, 4 row swap, 5 x
+  double* x = xs + t;
+#define X(i) x[(long)(i) * TP_THREADS]
   const double tiny = DBL_EPSILON * fmax(tn, 1e-200);
-  for (int i = 0; i < m; ++i) {
-    LU(1, i) = d[i] - lam;
-    LU(0, i) = f[i];
-    LU(2, i) = f[i];
-    LU(3, i) = 0.0;
-  }
+  double dcur = d[0] - lam, ucur = f[0];
   for (int i = 0; i < m - 1; ++i) {
-    const double a = LU(1, i), sub = LU(0, i);
-    if (fabs(a) >= fabs(sub)) {
-      const double piv = (fabs(a) < tiny) ? copysign(tiny, a) : a;
+    const double sub = f[i];
+    const double dn = d[i + 1] - lam, un = (i < m - 2) ? f[i + 1] : 0.0;
+    if (fabs(dcur) >= fabs(sub)) {
+      const double piv = (fabs(dcur) < tiny) ? copysign(tiny, dcur) : dcur;
       const double l = sub / piv;
+      LU(0, i) = l;
       LU(1, i) = 1.0 / piv;
-      LU(0, i) = l;
-      LU(1, i + 1) -= l * LU(2, i);
+      LU(2, i) = ucur;
+      LU(3, i) = 0.0;
       LU(4, i) = 0.0;
+      dcur = dn - l * ucur;
+      ucur = un;
     } else {
-      // swap rows i and i+1: the new row i is (sub, d_{i+1}, du_{i+1})
+      // swap rows i and i+1: the new row i is (sub, dn, un); the old row i is eliminated
       const double sb = (fabs(sub) < tiny) ? copysign(tiny, sub) : sub;
-      const double l = a / sb;
-      const double dd1 = LU(1, i + 1), du0 = LU(2, i), du1 = (i < m - 2) ? LU(2, i + 1) : 0.0;
-      LU(1, i) = 1.0 / sb;
-      LU(2, i) = dd1;
-      LU(3, i) = du1;
-      LU(1, i + 1) = du0 - l * dd1;
-      if (i < m - 2) LU(2, i + 1) = -l * du1;
+      const double l = dcur / sb;
       LU(0, i) = l;
+      LU(1, i) = 1.0 / sb;
+      LU(2, i) = dn;
+      LU(3, i) = un;
       LU(4, i) = 1.0;
+      const double nd = ucur - l * dn;
+      ucur = -l * un;
+      dcur = nd;
     }
   }
-  {
-    const double a = LU(1, m - 1);
-    LU(1, m - 1) = 1.0 / ((fabs(a) < tiny) ? copysign(tiny, a) : a);
-  }
+  LU(1, m - 1) = 1.0 / ((fabs(dcur) < tiny) ? copysign(tiny, dcur) : dcur);
+  LU(2, m - 1) = 0.0;
+  LU(3, m - 1) = 0.0;
   for (int i = 0; i < m; ++i) {  // starting vector: Philox uniforms in (-1, 1)
-    const uint4 x = philox10(make_uint4((uint32_t)i, (uint32_t)r, (uint32_t)b, 0x1e16u), 0x2504u, 0x4989u);
-    LU(5, i) = ((double)x.x + 0.5) * (2.0 / 4294967296.0) - 1.0;
+    const uint4 w = philox10(make_uint4((uint32_t)i, (uint32_t)r, (uint32_t)b, 0x1e16u), 0x2504u, 0x4989u);
+    X(i) = ((double)w.x + 0.5) * (2.0 / 4294967296.0) - 1.0;
   }
   for (int iter = 0; iter < 3; ++iter) {
-    for (int i = 0; i < m - 1; ++i) {  // row interchanges and multipliers
+    double xi = X(0);
+    for (int i = 0; i < m - 1; ++i) {  // row interchanges and multipliers: L^{-1} P
+      double xn = X(i + 1);
       if (LU(4, i) != 0.0) {
-        const double t = LU(5, i);
-        LU(5, i) = LU(5, i + 1);
-        LU(5, i + 1) = t;
+        const double tmp = xi;
+        xi = xn;
+        xn = tmp;
       }
-      LU(5, i + 1) -= LU(0, i) * LU(5, i);
+      X(i) = xi;
+      xi = xn - LU(0, i) * xi;
     }
-    double mx = 0;
+    X(m - 1) = xi;
+    double mx = 0, x1 = 0, x2 = 0;
     for (int i = m - 1; i >= 0; --i) {  // back substitution with U
-      double s = LU(5, i);
-      if (i + 1 < m) s -= LU(2, i) * LU(5, i + 1);
-      if (i + 2 < m) s -= LU(3, i) * LU(5, i + 2);
-      s *= LU(1, i);
-      LU(5, i) = s;
+      const double s = (X(i) - LU(2, i) * x1 - LU(3, i) * x2) * LU(1, i);
+      X(i) = s;
+      x2 = x1;
+      x1 = s;
       mx = fmax(mx, fabs(s));
     }
     if (!(mx > 0) || !isfinite(mx)) mx = 1.0;
     const double imx = 1.0 / mx;
     double nrm2 = 0;
     for (int i = 0; i < m; ++i) {
-      const double t = LU(5, i) * imx;
-      LU(5, i) = t;
-      nrm2 += t * t;
+      const double v = X(i) * imx;
+      X(i) = v;
+      nrm2 += v * v;
     }
     const double inv = 1.0 / sqrt(nrm2);
-    for (int i = 0; i < m; ++i) LU(5, i) *= inv;
+    for (int i = 0; i < m; ++i) X(i) *= inv;
   }
-  double* Z = e.Z + (long)b * m * R;
-  for (int i = 0; i < m; ++i) Z[(long)i * R + r] = LU(5, i);
+  for (int i = 0; i < m; ++i) Z[i] = X(i);
+#undef X
 #undef LU
 }
 
@@ -332,7 +426,7 @@ __global__ void __launch_bounds__(256) k_cluster_orth(int m, int R, EigScratch e
   __shared__ double red[32];
   __shared__ double dots[128];
   const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  double* Z = e.Z + (long)b * m * R;
+  double* Z = e.Z + (long)b * R * m;  // vector r at Z + r*m
   const double* l = lam + (long)b * R;
   const double tol = 1e-3 * e.tnorm[b];
   int c0 = 0;
@@ -341,68 +435,81 @@ __global__ void __launch_bounds__(256) k_cluster_orth(int m, int R, EigScratch e
       c0 = r;
       continue;
     }
+    double* zr = Z + (long)r * m;
     for (int pass = 0; pass < 2; ++pass) {
       for (int s = c0 + warp; s < r; s += nwarp) {
+        const double* zs = Z + (long)s * m;
         double acc = 0;
-        for (int i = lane; i < m; i += 32) acc += Z[(long)i * R + s] * Z[(long)i * R + r];
+        for (int i = lane; i < m; i += 32) acc += zs[i] * zr[i];
         acc = warp_sum(acc);
         if (lane == 0) dots[s - c0] = acc;
       }
       __syncthreads();
       for (int i = tid; i < m; i += blockDim.x) {
-        double acc = Z[(long)i * R + r];
-        for (int s = c0; s < r; ++s) acc -= dots[s - c0] * Z[(long)i * R + s];
-        Z[(long)i * R + r] = acc;
+        double acc = zr[i];
+        for (int s = c0; s < r; ++s) acc -= dots[s - c0] * Z[(long)s * m + i];
+        zr[i] = acc;
       }
       __syncthreads();
     }
     double part = 0;
-    for (int i = tid; i < m; i += blockDim.x) part += Z[(long)i * R + r] * Z[(long)i * R + r];
+    for (int i = tid; i < m; i += blockDim.x) part += zr[i] * zr[i];
     const double nrm = sqrt(block_sum(part, red));
-    for (int i = tid; i < m; i += blockDim.x) Z[(long)i * R + r] /= nrm;
+    for (int i = tid; i < m; i += blockDim.x) zr[i] /= nrm;
     __syncthreads();
   }
 }
 
-// u_r = H_0 H_1 .. H_{m-2} D z_r, one warp per eigenvector.
+// u_r = H_0 H_1 .. H_{m-2} D z_r, one warp per eigenvector, in the precision
+// of the output (the FP32 path rounds U_c to FP32 for its GEMMs anyway).
 constexpr int BT_WARPS = 8;
-__global__ void __launch_bounds__(BT_WARPS * 32) k_backtransform(int m, int R, EigScratch e, double2* __restrict__ U,
+template <typename C>
+__global__ void __launch_bounds__(BT_WARPS * 32) k_backtransform(int m, int R, EigScratch e, C* __restrict__ U,
                                                                  long ldu, long sU) {
-  extern __shared__ __align__(16) double2 us[];
+  using Rt = decltype(C().x);
+  extern __shared__ __align__(16) unsigned char bts[];
   const int b = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = blockIdx.x * BT_WARPS + warp;
   if (r >= R) return;
-  double2* u = us + (long)warp * m;
-  const double* Z = e.Z + (long)b * m * R;
+  C* u = (C*)bts + (long)warp * m;
+  const double* z = e.Z + ((long)b * R + r) * m;
   const double2* dl = e.delta + (long)b * m;
   const double2* Hv = e.Hv + (long)b * m * m;
-  for (int i = lane; i < m; i += 32) u[i] = cscale(dl[i], Z[(long)i * R + r]);
+  for (int i = lane; i < m; i += 32) u[i] = from_c64<C>(cscale(dl[i], z[i]));
   __syncwarp();
   for (int j = m - 2; j >= 0; --j) {
     const int n = m - j - 1;
     const double2* v = Hv + (long)j * m + j + 1;
-    double2 acc = make_double2(0, 0);
-    for (int i = lane; i < n; i += 32) cfmac(acc, v[i], u[j + 1 + i]);
-    acc = warp_sum(acc);
-    const double2 s2 = cscale(acc, 2.0);
-    for (int i = lane; i < n; i += 32) u[j + 1 + i] = csub(u[j + 1 + i], cmul(v[i], s2));
+    C acc;
+    acc.x = Rt(0);
+    acc.y = Rt(0);
+    for (int i = lane; i < n; i += 32) {
+      const C vi = from_c64<C>(v[i]), ui = u[j + 1 + i];
+      acc.x = fma(vi.x, ui.x, acc.x);  // acc += conj(v_i) u_i
+      acc.x = fma(vi.y, ui.y, acc.x);
+      acc.y = fma(vi.x, ui.y, acc.y);
+      acc.y = fma(-vi.y, ui.x, acc.y);
+    }
+    acc.x = warp_sum(acc.x);
+    acc.y = warp_sum(acc.y);
+    const C s2 = cscale(acc, Rt(2));
+    for (int i = lane; i < n; i += 32) u[j + 1 + i] = csub(u[j + 1 + i], cmul(from_c64<C>(v[i]), s2));
     __syncwarp();
   }
-  double2* Ub = U + (long)b * sU;
+  C* Ub = U + (long)b * sU;
   for (int i = lane; i < m; i += 32) Ub[(long)i * ldu + r] = u[i];
 }
 
-constexpr int HETRD_CLUSTER = 4;
-
-int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double* lam, double2* U, long ldu, long sU,
+template <typename C>
+int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double* lam, C* U, long ldu, long sU,
                   void* scratch, int* status, cudaStream_t s) {
   (void)status;
   if (m <= 0 || R <= 0 || batch <= 0) return TSVD_OK;
-  if (R > m || R > 128 || m > 1024) return TSVD_ERR_UNSUPPORTED;
+  if (R > m || R > 128 || m > 768) return TSVD_ERR_UNSUPPORTED;  // shared memory of k_hetrd
   EigScratch e = carve_eig(scratch, m, R, batch, nullptr);
   {
     TSVD_STAGE("eig_hetrd", s);
-    const size_t smem = 2 * (size_t)m * sizeof(double2);
+    const size_t smem = (2 + 16) * (size_t)m * sizeof(double2);  // v, p and 16 warps' partials
     if (smem > 48 * 1024) {
       cudaFuncSetAttribute(k_hetrd<HETRD_CLUSTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
@@ -425,20 +532,36 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
     TSVD_LAUNCHED();
   }
   {
-    TSVD_STAGE("eig_tridiag", s);
-    k_tridiag_pairs<<<batch, 128, 3 * (size_t)m * sizeof(double), s>>>(m, R, e, lam);
+    TSVD_STAGE("eig_bisect", s);
+    const size_t smem_b = 2 * (size_t)m * sizeof(double);
+    k_bisect<<<dim3(cdiv(R, BIS_WARPS), batch), BIS_WARPS * 32, smem_b, s>>>(m, R, e, lam);
     TSVD_LAUNCHED();
+  }
+  {
+    TSVD_STAGE("eig_invit", s);
+    const size_t smem_tp = (3 + (size_t)TP_THREADS) * m * sizeof(double);
+    if (smem_tp > 48 * 1024)
+      cudaFuncSetAttribute(k_tridiag_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tp);
+    k_tridiag_pairs<<<dim3(cdiv(R, TP_THREADS), batch), TP_THREADS, smem_tp, s>>>(m, R, e, lam);
+    TSVD_LAUNCHED();
+  }
+  {
+    TSVD_STAGE("eig_cluster", s);
     k_cluster_orth<<<batch, 256, 0, s>>>(m, R, e, lam);
     TSVD_LAUNCHED();
   }
   TSVD_STAGE("eig_backtransform", s);
-  const size_t smem_bt = (size_t)BT_WARPS * m * sizeof(double2);
+  const size_t smem_bt = (size_t)BT_WARPS * m * sizeof(C);
   if (smem_bt > 48 * 1024)
-    cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bt);
-  k_backtransform<<<dim3(cdiv(R, BT_WARPS), batch), BT_WARPS * 32, smem_bt, s>>>(m, R, e, U, ldu, sU);
+    cudaFuncSetAttribute(k_backtransform<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bt);
+  k_backtransform<C><<<dim3(cdiv(R, BT_WARPS), batch), BT_WARPS * 32, smem_bt, s>>>(m, R, e, U, ldu, sU);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }
+template int herm_eig_topR<double2>(double2*, long, long, int, int, int, double*, double2*, long, long, void*, int*,
+                                    cudaStream_t);
+template int herm_eig_topR<float2>(double2*, long, long, int, int, int, double*, float2*, long, long, void*, int*,
+                                   cudaStream_t);
 
 // ---------------------------------------------------------------------------
 template <typename T>

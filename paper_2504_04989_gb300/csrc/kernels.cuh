@@ -49,6 +49,10 @@ struct GemmArgs {
 };
 template <typename C>
 int cgemm(const GemmArgs& g, void* splitk_ws, size_t splitk_elems, cudaStream_t s);
+// C = op(A) op(B) known to be Hermitian (square, beta = 0, e.g. A^H A): only
+// the upper tiles are computed, the lower triangle is mirrored from them
+template <typename C>
+int cgemm_herm(const GemmArgs& g, void* splitk_ws, size_t splitk_elems, cudaStream_t s);
 // pick a split of K that fills the GPU (bounded by the scratch it needs)
 int choose_ksplit(int M, int N, int K, int batch, size_t splitk_elems);
 
@@ -83,9 +87,10 @@ int repair_dead(C* Q, long ldq, long sQ, int n1, int c, int nb, const uint32_t* 
 // eig.cu
 // Eigen-decomposition of the m x m Hermitian G per slice (G is overwritten):
 // top-R eigenvalues (descending) in lam (batch x R) and eigenvectors in
-// U (batch x m x R, row-major, leading dim ldu).  scratch: eig_scratch_bytes.
+// U (batch x m x R, row-major, leading dim ldu) in U's precision.
 size_t eig_scratch_bytes(int m, int R, int batch);
-int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double* lam, double2* U, long ldu, long sU,
+template <typename C>
+int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double* lam, C* U, long ldu, long sU,
                   void* scratch, int* status, cudaStream_t s);
 // sigma = sqrt(max(lam, 0)) -> sig (batch x R, may be null) and the complex
 // tube slices Sh of S; a non-finite eigenvalue sets *status.

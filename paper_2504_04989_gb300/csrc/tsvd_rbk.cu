@@ -71,8 +71,7 @@ struct RbkWs {
   int* counters;  // [0] status, [1] dead columns
   double2* G;
   double* lam;
-  double2* Uc64;
-  C* Uct;
+  C* Uct;      // U_c (m x R per slice) in the GEMM precision
   C* Uh;
   C* Vh;
   C* Sh;
@@ -107,8 +106,7 @@ static RbkWs<T> carve_rbk(void* base, const RbkDims& d) {
   w.counters = cv.take<int>(8);
   w.G = cv.take<double2>(h * d.m * d.m);
   w.lam = cv.take<double>(h * d.R);
-  w.Uc64 = cv.take<double2>(h * d.m * d.R);
-  w.Uct = dbl ? (C*)w.Uc64 : cv.take<C>(h * d.m * d.R);
+  w.Uct = cv.take<C>(h * d.m * d.R);
   w.Uh = cv.take<C>(h * d.n1 * d.R);
   w.Vh = cv.take<C>(h * d.n2 * d.R);
   w.Sh = cv.take<C>(h * d.R);
@@ -274,15 +272,13 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
   TSVD_TRY(to64<T>(w.CHt, m, sCH, w.CH64, m, sCH, n2, m, h, s));
   {
   TSVD_STAGE("gram_c", s);
-  TSVD_TRY(cgemm<double2>(gemm('H', 'N', m, m, n2, 1.0, w.CH64, m, sCH, w.CH64, m, sCH, 0.0, w.G, m, (long)m * m, h),
+  TSVD_TRY(cgemm_herm<double2>(gemm('H', 'N', m, m, n2, 1.0, w.CH64, m, sCH, w.CH64, m, sCH, 0.0, w.G, m, (long)m * m, h),
                           w.splitk, w.splitk_elems, s));
   }
-  TSVD_TRY(herm_eig_topR(w.G, m, (long)m * m, m, R, h, w.lam, w.Uc64, R, (long)m * R, w.eig, w.counters, s));
+  TSVD_TRY(herm_eig_topR<C>(w.G, m, (long)m * m, m, R, h, w.lam, w.Uct, R, (long)m * R, w.eig, w.counters, s));
   {
   TSVD_STAGE("outputs", s);
   TSVD_TRY(sigma_from_lambda<T>(w.lam, R, h, sig, w.Sh, s, w.counters));
-  if (!std::is_same<T, double>::value)
-    TSVD_TRY(convert_c64_to_c32(w.Uc64, R, (long)m * R, (float2*)w.Uct, R, (long)m * R, m, R, h, s));
 
   // Uhat = Q U_c,  Vhat = C^H U_c S^{-1}
   TSVD_TRY(cgemm<C>(gemm('N', 'N', n1, R, m, 1.0, w.Qt, m, sQ, w.Uct, R, (long)m * R, 0.0, w.Uh, R, (long)n1 * R, h),
