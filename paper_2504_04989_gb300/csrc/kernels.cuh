@@ -84,6 +84,19 @@ int trsm_right_upper(C* W, long ldw, long sW, const double2* Rm, long ldr, long 
 template <typename C>
 int repair_dead(C* Q, long ldq, long sQ, int n1, int c, int nb, const uint32_t* dead, int batch, uint64_t seed,
                 int block_id, int* dead_count, cudaStream_t s);
+// tc_gemm.cu -- tcgen05 tensor-core GEMM C_b (M x N, FP32) = A_b (M x K) B_b^T
+// with A (M x K) and B (N x K) K-major, TF32 (FP32 storage) or BF16.  Needs
+// 16-byte aligned bases, row strides and batch strides (tc_gemm_supported);
+// *err is set if a pipeline wait timed out.
+bool tc_gemm_supported(const void* A, long lda, long sA, const void* B, long ldb, long sB, int batch, bool bf16);
+int tc_gemm(const void* A, long lda, long sA, int M, const void* B, long ldb, long sB, int N, int K, float* C, long ldc,
+            long sC, int batch, bool bf16, int* err, cudaStream_t s);
+// expanded real form E (2N x 2K, leading dim lde) of a thin interleaved complex
+// Y (K x N): real(X) E^T = X Y (mode 0) or conj(X) Y (mode 1)
+int expand_thin(const float2* Y, long ldy, long sy, int K, int N, void* E, long lde, long se, int batch, int mode,
+                bool bf16, cudaStream_t s);
+// rows x cols FP32 rows (leading dim ldx) copied to BF16 or FP32 rows of leading dim ldy (zero padded)
+int copy_rows(const float* x, long ldx, void* y, long ldy, int cols, long rows, bool bf16, cudaStream_t s);
 // eig.cu
 // Eigen-decomposition of the m x m Hermitian G per slice (G is overwritten):
 // top-R eigenvalues (descending) in lam (batch x R) and eigenvectors in

@@ -1,0 +1,356 @@
+// tc_gemm.cu -- batched real GEMM on the 5th-generation tensor cores:
+//   C_b (M x N, FP32) = A_b (M x K) * B_b^T,   B_b stored N x K,
+// A and B K-major (K contiguous), TF32 (FP32 storage) or BF16 operands, FP32
+// accumulation in tensor memory.
+//
+// One CTA computes a 128 x 128 tile.  Operand tiles of 128 rows x 128 bytes
+// of K are staged by TMA (128-byte swizzle) through a 4-stage ring of shared
+// buffers guarded by mbarriers; one thread issues tcgen05.mma (4 per stage,
+// 32 bytes of K each) into a 128-column TMEM accumulator and commits each
+// stage back to the producer; all four warps then read the accumulator with
+// tcgen05.ld and store it.  Every wait is bounded: on a timeout the kernel
+// records an error flag instead of hanging.
+//
+// Complex products use it without moving the big operand: an interleaved
+// complex matrix X (rows x cols) is the real matrix [Re Im Re Im ...] of
+// rows x 2cols, so X * Y = real(X) * E(Y)^T with a small expanded real form
+// E(Y) of the thin factor (see expand_* below).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace tsvd {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BN = 128;
+constexpr int TC_STAGES = 4;
+constexpr int TC_TILE_BYTES = 128 * 128;  // 128 rows x 128 bytes of K
+constexpr int TC_SMEM = 2 * TC_STAGES * TC_TILE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// true once the phase of the given parity has completed; false after ~1 s
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (2LL << 30)) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(dst),
+      "l"((unsigned long long)tm), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major operand tile, 128-byte swizzle,
+// 8-row groups 1024 bytes apart (SBO), descriptor version 1
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // version
+  d |= (uint64_t)2 << 61;            // swizzle 128B
+  return d;
+}
+
+// instruction descriptor: D FP32, A/B TF32 (kind::tf32) or BF16 (kind::f16),
+// both K-major, M = 128, N = TC_BN
+template <bool BF16>
+__device__ __forceinline__ uint32_t instr_desc() {
+  const uint32_t fmt = BF16 ? 1u : 2u;
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+template <bool BF16>
+__device__ __forceinline__ void mma_issue(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  if (BF16) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
+                                                    const __grid_constant__ CUtensorMap tmB, float* __restrict__ C,
+                                                    long ldc, long sC, int M, int N, int nk, int* __restrict__ err) {
+  extern __shared__ unsigned char tc_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* As = base;
+  unsigned char* Bs = base + TC_STAGES * TC_TILE_BYTES;
+  uint64_t* bars = (uint64_t*)(Bs + TC_STAGES * TC_TILE_BYTES);  // full[S], empty[S], done
+  uint32_t* tslot = (uint32_t*)(bars + 2 * TC_STAGES + 1);
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n0 = blockIdx.x * TC_BN, m0 = blockIdx.y * TC_BM, bz = blockIdx.z;
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_STAGES), done = smem_u32(bars + 2 * TC_STAGES);
+  constexpr int KE = BF16 ? 64 : 32;  // elements per 128 bytes of K
+
+  if (tid == 0) {
+    s_fail = 0;
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(TC_BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+
+  int issued = 0;  // stages the producer loaded
+  if (tid == 0) {  // TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % TC_STAGES, round = kb / TC_STAGES;
+      if (round > 0 && !mbar_wait(empty0 + 8 * s, (round - 1) & 1)) {
+        s_fail = 1;
+        break;
+      }
+      mbar_expect_tx(full0 + 8 * s, 2 * TC_TILE_BYTES);
+      tma_load_3d(smem_u32(As + s * TC_TILE_BYTES), &tmA, kb * KE, m0, bz, full0 + 8 * s);
+      tma_load_3d(smem_u32(Bs + s * TC_TILE_BYTES), &tmB, kb * KE, n0, bz, full0 + 8 * s);
+      issued = kb + 1;
+    }
+  } else if (tid == 32) {  // MMA issuer
+    const uint32_t idesc = instr_desc<BF16>();
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % TC_STAGES, round = kb / TC_STAGES;
+      if (!mbar_wait(full0 + 8 * s, round & 1)) {
+        s_fail = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint64_t ad = smem_desc_sw128(smem_u32(As + s * TC_TILE_BYTES));
+      const uint64_t bd = smem_desc_sw128(smem_u32(Bs + s * TC_TILE_BYTES));
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)  // 32 bytes of K per instruction: advance the start address by 2 x 16 B
+        mma_issue<BF16>(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0);
+      mma_commit(empty0 + 8 * s);
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(done, 0);
+  __syncwarp();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  __syncthreads();
+  const bool good = ok && (s_fail == 0);
+  if (good) {
+    const int row = m0 + warp * 32 + lane;
+    float* crow = C + (long)bz * sC + (long)row * ldc;
+#pragma unroll 1
+    for (int c0 = 0; c0 < TC_BN; c0 += 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+          "%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + c0 + j;
+          if (col < N) crow[col] = __uint_as_float(r[j]);
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+  }
+  if (tid == 0) {  // make sure no copy of this CTA is still landing in shared memory
+    for (int kb = (issued > TC_STAGES ? issued - TC_STAGES : 0); kb < issued; ++kb)
+      mbar_wait(full0 + 8 * (kb % TC_STAGES), (kb / TC_STAGES) & 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// rows x K (elements) per batch, row stride ld, batch stride sb (elements)
+static int make_map(CUtensorMap* tm, const void* ptr, int rows, int K, long ld, long sb, int batch, bool bf16) {
+  auto enc = get_encode();
+  if (!enc) return TSVD_ERR_CUDA;
+  const size_t es = bf16 ? 2 : 4;
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)(ld * es), (cuuint64_t)(sb * es)};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / es), (cuuint32_t)TC_BM, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)ptr, dims,
+                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? TSVD_OK : TSVD_ERR_UNSUPPORTED;
+}
+
+bool tc_gemm_supported(const void* A, long lda, long sA, const void* B, long ldb, long sB, int batch, bool bf16) {
+  const long es = bf16 ? 2 : 4;
+  auto al = [](long bytes) { return bytes % 16 == 0; };
+  if (((uintptr_t)A & 15) || ((uintptr_t)B & 15)) return false;
+  if (!al(lda * es) || !al(ldb * es)) return false;
+  if (batch > 1 && (!al(sA * es) || !al(sB * es))) return false;
+  return batch <= 65535;
+}
+
+int tc_gemm(const void* A, long lda, long sA, int M, const void* B, long ldb, long sB, int N, int K, float* C, long ldc,
+            long sC, int batch, bool bf16, int* err, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || batch <= 0) return TSVD_OK;
+  if (!tc_gemm_supported(A, lda, sA, B, ldb, sB, batch, bf16)) return TSVD_ERR_UNSUPPORTED;
+  CUtensorMap ta, tb;
+  TSVD_TRY(make_map(&ta, A, M, K, lda, sA, batch, bf16));
+  TSVD_TRY(make_map(&tb, B, N, K, ldb, sB, batch, bf16));
+  const int kelem = bf16 ? 64 : 32;
+  const int nk = (K + kelem - 1) / kelem;
+  dim3 grid(cdiv(N, TC_BN), cdiv(M, TC_BM), batch);
+  if (bf16) {
+    cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    k_tc_gemm<true><<<grid, 128, TC_SMEM, s>>>(ta, tb, C, ldc, sC, M, N, nk, err);
+  } else {
+    cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    k_tc_gemm<false><<<grid, 128, TC_SMEM, s>>>(ta, tb, C, ldc, sC, M, N, nk, err);
+  }
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Expanded real forms of a thin complex factor Y (K x N per batch, interleaved,
+// leading dim ldy), as E (2N x 2K per batch, leading dim lde), so that for an
+// interleaved complex X (rows x K) seen as a real rows x 2K matrix,
+// real(X) * E^T is the interleaved complex product:
+//   mode 0 (X Y):       E[2n][2k] = Yr, E[2n][2k+1] = -Yi, E[2n+1][2k] = Yi, E[2n+1][2k+1] = Yr
+//   mode 1 (conj(X) Y): E[2n][2k] = Yr, E[2n][2k+1] =  Yi, E[2n+1][2k] = Yi, E[2n+1][2k+1] = -Yr
+// ---------------------------------------------------------------------------
+template <typename O>
+__device__ __forceinline__ O cvt_out(float v);
+template <>
+__device__ __forceinline__ float cvt_out<float>(float v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt_out<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+
+template <typename O>
+__global__ void k_expand(const float2* __restrict__ Y, long ldy, long sy, int K, int N, O* __restrict__ E, long lde,
+                         long se, int batch, int mode) {
+  const long total = (long)batch * K * N;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int n = idx % N;
+    const long t = idx / N;
+    const int k = t % K;
+    const int b = t / K;
+    const float2 y = Y[(long)b * sy + (long)k * ldy + n];
+    O* e0 = E + (long)b * se + (long)(2 * n) * lde + 2 * k;
+    O* e1 = e0 + lde;
+    if (mode == 0) {
+      e0[0] = cvt_out<O>(y.x);
+      e0[1] = cvt_out<O>(-y.y);
+      e1[0] = cvt_out<O>(y.y);
+      e1[1] = cvt_out<O>(y.x);
+    } else {
+      e0[0] = cvt_out<O>(y.x);
+      e0[1] = cvt_out<O>(y.y);
+      e1[0] = cvt_out<O>(y.y);
+      e1[1] = cvt_out<O>(-y.x);
+    }
+  }
+}
+
+int expand_thin(const float2* Y, long ldy, long sy, int K, int N, void* E, long lde, long se, int batch, int mode,
+                bool bf16, cudaStream_t s) {
+  const long total = (long)batch * K * N;
+  if (total <= 0) return TSVD_OK;
+  const unsigned grid = std::min<long>(cdiv(total, 256), 8192);
+  if (bf16)
+    k_expand<__nv_bfloat16><<<grid, 256, 0, s>>>(Y, ldy, sy, K, N, (__nv_bfloat16*)E, lde, se, batch, mode);
+  else
+    k_expand<float><<<grid, 256, 0, s>>>(Y, ldy, sy, K, N, (float*)E, lde, se, batch, mode);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
+// rows x cols FP32 (leading dim ldx) to BF16 (round to nearest even) or FP32
+// with leading dim ldy; the padding columns are zeroed
+template <typename O>
+__global__ void k_copy_rows(const float* __restrict__ x, long ldx, O* __restrict__ y, long ldy, int cols, long rows) {
+  const long total = rows * ldy;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const long r = i / ldy;
+    const long c = i % ldy;
+    y[i] = cvt_out<O>(c < cols ? x[r * ldx + c] : 0.0f);
+  }
+}
+
+int copy_rows(const float* x, long ldx, void* y, long ldy, int cols, long rows, bool bf16, cudaStream_t s) {
+  const long total = rows * ldy;
+  if (total <= 0) return TSVD_OK;
+  const unsigned grid = std::min<long>(cdiv(total, 256), 8192);
+  if (bf16) k_copy_rows<__nv_bfloat16><<<grid, 256, 0, s>>>(x, ldx, (__nv_bfloat16*)y, ldy, cols, rows);
+  else k_copy_rows<float><<<grid, 256, 0, s>>>(x, ldx, (float*)y, ldy, cols, rows);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
+}  // namespace tsvd

@@ -21,6 +21,11 @@ static int check_prec(int precision) {
   return TSVD_ERR_INVALID_ARG;
 }
 
+static int check_prec_fwd(int precision) {
+  if (precision >= TSVD_FP64 && precision <= TSVD_MIXED_BF16) return TSVD_OK;
+  return TSVD_ERR_INVALID_ARG;
+}
+
 static GemmArgs gm(char opA, char opB, int M, int N, int K, double alpha, const void* A, long lda, const void* B,
                    long ldb, double beta, void* Cm, long ldc, int batch) {
   GemmArgs g;
@@ -83,6 +88,67 @@ static int tprod_run(const T* A, const T* B, T* Cout, int n1, int n2, int n4, in
   {
     TSVD_STAGE("tprod_irfft", s);
     TSVD_TRY(launch_irfft3<T>(w.Ch, Cout, (long)n1 * n4, n3, s));
+  }
+  return TSVD_OK;
+}
+
+// Tensor-core forward: the slice products as one real GEMM per slice,
+// real(A_k) (n1 x 2n2) times E(B_k)^T, E(B_k) (2n4 x 2n2) the expanded real
+// form of B_k; the interleaved complex product comes out directly.
+struct TprodTcWs {
+  float2 *Ah, *Bh, *Ch;
+  void* Aop;  // operand copy (BF16, or FP32 with padded rows) or null
+  void* E;
+  int* err;
+  long lda, lde;
+  size_t bytes;
+};
+static TprodTcWs carve_tprod_tc(void* base, int n1, int n2, int n4, int n3, bool bf16) {
+  Carver cv(base);
+  const size_t h = n3 / 2 + 1;
+  TprodTcWs w;
+  const long k2 = 2L * n2;
+  w.lda = (k2 + 7) / 8 * 8;
+  w.lde = w.lda;
+  w.Ah = cv.take<float2>(h * n1 * n2);
+  w.Bh = cv.take<float2>(h * n2 * n4);
+  w.Ch = cv.take<float2>(h * n1 * n4);
+  const bool copy = bf16 || (k2 % 4 != 0);
+  w.Aop = copy ? cv.take<float>(h * n1 * w.lda) : nullptr;  // big enough for either element type
+  w.E = cv.take<float>(h * 2 * (size_t)n4 * w.lde);
+  w.err = cv.take<int>(4);
+  w.bytes = cv.bytes();
+  return w;
+}
+
+static int tprod_tc_run(const float* A, const float* B, float* Cout, int n1, int n2, int n4, int n3, bool bf16,
+                        void* ws, cudaStream_t s) {
+  TprodTcWs w = carve_tprod_tc(ws, n1, n2, n4, n3, bf16);
+  const int h = n3 / 2 + 1;
+  const long k2 = 2L * n2;
+  {
+    TSVD_STAGE("tprod_rfft", s);
+    TSVD_TRY(launch_rfft3<float>(A, w.Ah, (long)n1 * n2, n3, s));
+    TSVD_TRY(launch_rfft3<float>(B, w.Bh, (long)n2 * n4, n3, s));
+  }
+  {
+    TSVD_STAGE("tprod_expand", s);
+    TSVD_TRY(expand_thin(w.Bh, n4, (long)n2 * n4, n2, n4, w.E, w.lde, 2L * n4 * w.lde, h, 0, bf16, s));
+    const void* Aop = w.Ah;
+    long lda = k2;
+    if (w.Aop) {  // BF16 operand, or FP32 rows padded to 16 bytes
+      TSVD_TRY(copy_rows((const float*)w.Ah, k2, w.Aop, w.lda, (int)k2, (long)h * n1, bf16, s));
+      Aop = w.Aop;
+      lda = w.lda;
+    }
+    if (cudaMemsetAsync(w.err, 0, sizeof(int), s) != cudaSuccess) return TSVD_ERR_CUDA;
+    TSVD_STAGE("tprod_gemm_tc", s);
+    TSVD_TRY(tc_gemm(Aop, lda, (long)n1 * lda, n1, w.E, w.lde, 2L * n4 * w.lde, 2 * n4, (int)k2, (float*)w.Ch,
+                     2L * n4, 2L * n1 * n4, h, bf16, w.err, s));
+  }
+  {
+    TSVD_STAGE("tprod_irfft", s);
+    TSVD_TRY(launch_irfft3<float>(w.Ch, Cout, (long)n1 * n4, n3, s));
   }
   return TSVD_OK;
 }
@@ -203,9 +269,10 @@ using namespace tsvd;
 
 extern "C" int tprod_workspace_size(int n1, int n2, int n4, int n3, int precision, size_t* bytes) {
   if (!bytes || !dims_ok(n1, n2, n4, n3)) return TSVD_ERR_INVALID_ARG;
-  TSVD_TRY(check_prec(precision));
-  *bytes = precision == TSVD_FP64 ? carve_tprod<double>(nullptr, n1, n2, n4, n3).bytes
-                                  : carve_tprod<float>(nullptr, n1, n2, n4, n3).bytes;
+  TSVD_TRY(check_prec_fwd(precision));
+  if (precision == TSVD_FP64) *bytes = carve_tprod<double>(nullptr, n1, n2, n4, n3).bytes;
+  else if (precision == TSVD_FP32) *bytes = carve_tprod<float>(nullptr, n1, n2, n4, n3).bytes;
+  else *bytes = carve_tprod_tc(nullptr, n1, n2, n4, n3, precision == TSVD_MIXED_BF16).bytes;
   return TSVD_OK;
 }
 
@@ -218,7 +285,10 @@ extern "C" int tprod(const void* A, const void* B, void* C, int n1, int n2, int 
   cudaStream_t s = (cudaStream_t)stream;
   if (precision == TSVD_FP64)
     return tprod_run<double>((const double*)A, (const double*)B, (double*)C, n1, n2, n4, n3, ws, s);
-  return tprod_run<float>((const float*)A, (const float*)B, (float*)C, n1, n2, n4, n3, ws, s);
+  if (precision == TSVD_FP32)
+    return tprod_run<float>((const float*)A, (const float*)B, (float*)C, n1, n2, n4, n3, ws, s);
+  return tprod_tc_run((const float*)A, (const float*)B, (float*)C, n1, n2, n4, n3, precision == TSVD_MIXED_BF16, ws,
+                      s);
 }
 
 extern "C" int tprod_backward_workspace_size(int n1, int n2, int n4, int n3, int precision, size_t* bytes) {

@@ -116,3 +116,26 @@ def test_autograd_gradcheck_fp64(api):
     Q = dev(rand(4, 6, 2)).requires_grad_(True)
     X = dev(rand(4, 6, 3)).requires_grad_(True)
     assert torch.autograd.gradcheck(lambda q, x: api.tproj(q, x), (Q, X), eps=1e-6, atol=1e-8)
+
+
+# tensor-core t-product: TF32 / BF16 operands, FP32 accumulation (tcgen05)
+TC_SHAPES = [(128, 128, 64, 4), (200, 96, 150, 7), (33, 70, 65, 3), (256, 512, 40, 16), (64, 31, 17, 5)]
+
+
+@pytest.mark.parametrize("n1,n2,n4,n3", TC_SHAPES)
+@pytest.mark.parametrize("precision,tol", [("tf32", 3e-3), ("bf16", 2e-2)])
+def test_tprod_tensor_core(api, orc, n1, n2, n4, n3, precision, tol):
+    A, B = rand(n3, n1, n2), rand(n3, n2, n4)
+    A32, B32 = A.astype(np.float32), B.astype(np.float32)
+    with api.profile() as pr:
+        C = api.tprod(dev(A32, torch.float32), dev(B32, torch.float32), precision)
+        torch.cuda.synchronize()
+    assert "tprod_gemm_tc" in pr.stages  # the tcgen05 kernel ran
+    C = C.cpu().numpy()
+    ref = orc.tprod(A32.astype(np.float64), B32.astype(np.float64))
+    # operands rounded to TF32 (11-bit) / BF16 (8-bit significand): normwise relative error
+    rel = np.linalg.norm((C - ref).ravel()) / np.linalg.norm(ref.ravel())
+    assert rel < tol, rel
+    # and element-wise against the scale of the summands
+    scale = np.sqrt(n2 * n3) * np.max(np.abs(A32)) * np.max(np.abs(B32))
+    assert np.max(np.abs(C - ref)) < 10 * tol * scale
