@@ -111,13 +111,278 @@ static int tile_e(int n3, size_t elem, size_t celem, bool inverse) {
   return 32;
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-radix FFT of the tubes (Stockham autosort, radices 4, 2, 3, 5 and any
+// remaining prime).  A CTA owns a tile of FFT_TUBES consecutive tubes; two real
+// tubes are packed into one complex sequence z = x + i y and each warp
+// transforms whole sequences in shared memory (lane-parallel butterflies,
+// warp barriers between passes).  The half spectra are separated as
+// X_k = (Z_k + conj Z_{n-k}) / 2, Y_k = (Z_k - conj Z_{n-k}) / (2i); the inverse
+// packs Z = X + i Y over the full (Hermitian) spectrum.  Global reads and writes
+// run along the plane index, so they stay coalesced.
+// ---------------------------------------------------------------------------
+constexpr int FFT_WARPS = 8;
+constexpr int FFT_LOADS = 8;
+constexpr int FFT_MAXR = 24;
+struct FftPlan {
+  int n, nr, tubes;
+  int radix[FFT_MAXR];
+};
+
+static bool make_plan(int n, FftPlan* p) {
+  p->n = n;
+  p->nr = 0;
+  int m = n;
+  while (m % 4 == 0) { p->radix[p->nr++] = 4; m /= 4; }
+  while (m % 2 == 0) { p->radix[p->nr++] = 2; m /= 2; }
+  for (int f = 3; m > 1; f += 2) {
+    while (m % f == 0) {
+      if (p->nr >= FFT_MAXR) return false;
+      p->radix[p->nr++] = f;
+      m /= f;
+    }
+  }
+  return true;
+}
+
+// one Stockham pass of radix R (sign of the exponent in tw): in -> out
+template <typename C, int R>
+__device__ __forceinline__ void fft_pass_fixed(const C* __restrict__ in, C* __restrict__ out, const C* __restrict__ tw,
+                                               int n, int Ns, int lane) {
+  const int nR = n / R, tstep = n / (Ns * R);
+  for (int j = lane; j < nR; j += 32) {
+    const int k = j % Ns;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      v[r] = in[j + r * nR];
+      if (r > 0) v[r] = cmul(v[r], tw[(r * k * tstep) % n]);
+    }
+    C o[R];
+    if (R == 2) {
+      o[0] = cadd(v[0], v[1]);
+      o[1] = csub(v[0], v[1]);
+    } else if (R == 4) {
+      // omega_4 = tw[n/4] is exactly +-i
+      const C w = tw[n / 4];
+      const C a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+      const C c = cadd(v[1], v[3]), d = cmul(csub(v[1], v[3]), w);
+      o[0] = cadd(a, c);
+      o[2] = csub(a, c);
+      o[1] = cadd(b, d);
+      o[3] = csub(b, d);
+    } else {
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        C acc = v[0];
+#pragma unroll
+        for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(v[r], tw[((q * r) % R) * (n / R)]));
+        o[q] = acc;
+      }
+    }
+    const int idxD = (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[idxD + r * Ns] = o[r];
+  }
+}
+
+template <typename C>
+__device__ void fft_pass_generic(const C* __restrict__ in, C* __restrict__ out, const C* __restrict__ tw, int n, int Ns,
+                                 int R, int lane) {
+  const int nR = n / R, tstep = n / (Ns * R);
+  for (int j = lane; j < nR; j += 32) {
+    const int k = j % Ns;
+    const int idxD = (j / Ns) * Ns * R + k;
+    for (int q = 0; q < R; ++q) {
+      C acc = in[j];
+      for (int r = 1; r < R; ++r) {
+        const C vr = cmul(in[j + r * nR], tw[(r * k * tstep) % n]);
+        acc = cadd(acc, cmul(vr, tw[((q * r) % R) * (n / R)]));
+      }
+      out[idxD + q * Ns] = acc;
+    }
+  }
+}
+
+// in-place (ping-pong) FFT of a length-n sequence in a / b; returns the buffer holding the result
+template <typename C>
+__device__ C* fft_run(C* a, C* b, const C* tw, const FftPlan& P, int lane) {
+  int Ns = 1;
+  for (int s = 0; s < P.nr; ++s) {
+    const int R = P.radix[s];
+    if (R == 4) fft_pass_fixed<C, 4>(a, b, tw, P.n, Ns, lane);
+    else if (R == 2) fft_pass_fixed<C, 2>(a, b, tw, P.n, Ns, lane);
+    else if (R == 3) fft_pass_fixed<C, 3>(a, b, tw, P.n, Ns, lane);
+    else if (R == 5) fft_pass_fixed<C, 5>(a, b, tw, P.n, Ns, lane);
+    else fft_pass_generic<C>(a, b, tw, P.n, Ns, R, lane);
+    __syncwarp();
+    C* t = a;
+    a = b;
+    b = t;
+    Ns *= R;
+  }
+  return a;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FFT_WARPS * 32) k_rfft3_fft(const T* __restrict__ X, cx_t<T>* __restrict__ Xh,
+                                                              long plane, FftPlan P) {
+  using C = cx_t<T>;
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const int n = P.n, h = n / 2 + 1, TT = P.tubes;
+  C* tw = (C*)fsm;                                  // [n]
+  C* zb = tw + n;                                   // [FFT_WARPS][2][n]
+  C* otile = zb + (size_t)FFT_WARPS * 2 * n;        // [h][TT] complex
+  T* itile = (T*)(otile + (size_t)h * TT);          // [n][TT] real
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long e0 = (long)blockIdx.x * TT;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) tw[p] = twiddle<T>(p, n, -1);
+  {
+    // FFT_LOADS independent loads in flight per thread (memory-level parallelism)
+    const int total = n * TT;
+    for (int base = threadIdx.x; base < total; base += FFT_LOADS * blockDim.x) {
+      T v[FFT_LOADS];
+#pragma unroll
+      for (int u = 0; u < FFT_LOADS; ++u) {
+        const int idx = base + u * blockDim.x;
+        const int t = idx / TT, e = idx - t * TT;
+        const long ge = e0 + e;
+        v[u] = (idx < total && ge < plane) ? __ldg(X + (long)t * plane + ge) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < FFT_LOADS; ++u) {
+        const int idx = base + u * blockDim.x;
+        if (idx < total) itile[idx] = v[u];
+      }
+    }
+  }
+  __syncthreads();
+  C* za = zb + (size_t)warp * 2 * n;
+  C* zc = za + n;
+  const T hf = T(0.5);
+  for (int s = warp; s < TT / 2; s += FFT_WARPS) {
+    for (int t = lane; t < n; t += 32) za[t] = mkc(itile[t * TT + 2 * s], itile[t * TT + 2 * s + 1]);
+    __syncwarp();
+    const C* Z = fft_run<C>(za, zc, tw, P, lane);
+    for (int k = lane; k < h; k += 32) {
+      const C zk = Z[k], zn = Z[(n - k) % n];
+      otile[k * TT + 2 * s] = mkc(hf * (zk.x + zn.x), hf * (zk.y - zn.y));      // X_k
+      otile[k * TT + 2 * s + 1] = mkc(hf * (zk.y + zn.y), hf * (zn.x - zk.x));  // Y_k
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < h * TT; idx += blockDim.x) {
+    const int k = idx / TT, e = idx - k * TT;
+    const long ge = e0 + e;
+    if (ge < plane) Xh[(long)k * plane + ge] = otile[idx];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FFT_WARPS * 32) k_irfft3_fft(const cx_t<T>* __restrict__ Xh, T* __restrict__ X,
+                                                               long plane, FftPlan P) {
+  using C = cx_t<T>;
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const int n = P.n, h = n / 2 + 1, TT = P.tubes;
+  C* tw = (C*)fsm;                                  // [n]
+  C* zb = tw + n;                                   // [FFT_WARPS][2][n]
+  C* itile = zb + (size_t)FFT_WARPS * 2 * n;        // [h][TT] complex
+  T* otile = (T*)(itile + (size_t)h * TT);          // [n][TT] real
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long e0 = (long)blockIdx.x * TT;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) tw[p] = twiddle<T>(p, n, +1);
+  {
+    const int total = h * TT;
+    for (int base = threadIdx.x; base < total; base += FFT_LOADS * blockDim.x) {
+      C v[FFT_LOADS];
+#pragma unroll
+      for (int u = 0; u < FFT_LOADS; ++u) {
+        const int idx = base + u * blockDim.x;
+        const int k = idx / TT, e = idx - k * TT;
+        const long ge = e0 + e;
+        v[u] = mkc(T(0), T(0));
+        if (idx < total && ge < plane) v[u] = Xh[(long)k * plane + ge];
+        if (k == 0 || 2 * k == n) v[u].y = T(0);  // c2r: the DC and Nyquist slices are real
+      }
+#pragma unroll
+      for (int u = 0; u < FFT_LOADS; ++u) {
+        const int idx = base + u * blockDim.x;
+        if (idx < total) itile[idx] = v[u];
+      }
+    }
+  }
+  __syncthreads();
+  C* za = zb + (size_t)warp * 2 * n;
+  C* zc = za + n;
+  const T inv = T(1) / T(n);
+  for (int s = warp; s < TT / 2; s += FFT_WARPS) {
+    for (int k = lane; k < n; k += 32) {
+      C x, y;
+      if (k < h) {
+        x = itile[k * TT + 2 * s];
+        y = itile[k * TT + 2 * s + 1];
+      } else {
+        x = cconj(itile[(n - k) * TT + 2 * s]);
+        y = cconj(itile[(n - k) * TT + 2 * s + 1]);
+      }
+      za[k] = mkc(x.x - y.y, x.y + y.x);  // Z = X + i Y
+    }
+    __syncwarp();
+    const C* z = fft_run<C>(za, zc, tw, P, lane);
+    for (int t = lane; t < n; t += 32) {
+      otile[t * TT + 2 * s] = z[t].x * inv;
+      otile[t * TT + 2 * s + 1] = z[t].y * inv;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * TT; idx += blockDim.x) {
+    const int t = idx / TT, e = idx - t * TT;
+    const long ge = e0 + e;
+    if (ge < plane) X[(long)t * plane + ge] = otile[idx];
+  }
+}
+
+// shared bytes of the FFT kernels for tile width tt (0 when the plan does not exist)
+template <typename T>
+static size_t fft_smem(int n, int tt) {
+  const int h = n / 2 + 1;
+  return sizeof(cx_t<T>) * ((size_t)n + (size_t)FFT_WARPS * 2 * n + (size_t)h * tt) + sizeof(T) * (size_t)n * tt;
+}
+
+template <typename T>
+static bool fft_setup(int n, FftPlan* P, size_t* smem) {
+  if (!make_plan(n, P)) return false;
+  for (int tt = 64; tt >= 16; tt >>= 1) {
+    const size_t b = fft_smem<T>(n, tt);
+    if (b <= 110 * 1024) {
+      P->tubes = tt;
+      *smem = b;
+      return true;
+    }
+  }
+  return false;
+}
+
 template <typename T>
 int launch_rfft3(const T* X, cx_t<T>* Xh, long plane, int n3, cudaStream_t s) {
   if (plane <= 0) return TSVD_OK;
+  FftPlan P;
+  size_t smem;
+  if (fft_setup<T>(n3, &P, &smem)) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_rfft3_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_rfft3_fft<T><<<cdiv(plane, P.tubes), FFT_WARPS * 32, smem, s>>>(X, Xh, plane, P);
+    TSVD_LAUNCHED();
+    return TSVD_OK;
+  }
+  // very long tubes: direct transform
   const int te = tile_e(n3, sizeof(T), sizeof(cx_t<T>), false);
-  const size_t smem = (size_t)n3 * sizeof(cx_t<T>) + (size_t)n3 * te * sizeof(T);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_rfft3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_rfft3<T><<<cdiv(plane, te), 256, smem, s>>>(X, Xh, plane, n3, te);
+  const size_t sm = (size_t)n3 * sizeof(cx_t<T>) + (size_t)n3 * te * sizeof(T);
+  if (sm > 227 * 1024) return TSVD_ERR_UNSUPPORTED;
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_rfft3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_rfft3<T><<<cdiv(plane, te), 256, sm, s>>>(X, Xh, plane, n3, te);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }
@@ -125,11 +390,21 @@ int launch_rfft3(const T* X, cx_t<T>* Xh, long plane, int n3, cudaStream_t s) {
 template <typename T>
 int launch_irfft3(const cx_t<T>* Xh, T* X, long plane, int n3, cudaStream_t s) {
   if (plane <= 0) return TSVD_OK;
+  FftPlan P;
+  size_t smem;
+  if (fft_setup<T>(n3, &P, &smem)) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_irfft3_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_irfft3_fft<T><<<cdiv(plane, P.tubes), FFT_WARPS * 32, smem, s>>>(Xh, X, plane, P);
+    TSVD_LAUNCHED();
+    return TSVD_OK;
+  }
   const int h = n3 / 2 + 1;
   const int te = tile_e(n3, sizeof(T), sizeof(cx_t<T>), true);
-  const size_t smem = (size_t)n3 * sizeof(cx_t<T>) + (size_t)h * te * sizeof(cx_t<T>);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_irfft3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_irfft3<T><<<cdiv(plane, te), 256, smem, s>>>(Xh, X, plane, n3, te);
+  const size_t sm = (size_t)n3 * sizeof(cx_t<T>) + (size_t)h * te * sizeof(cx_t<T>);
+  if (sm > 227 * 1024) return TSVD_ERR_UNSUPPORTED;
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_irfft3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_irfft3<T><<<cdiv(plane, te), 256, sm, s>>>(Xh, X, plane, n3, te);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }

@@ -297,10 +297,10 @@ __global__ void k_expand(const float2* __restrict__ Y, long ldy, long sy, int K,
                          long se, int batch, int mode) {
   const long total = (long)batch * K * N;
   for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-    const int n = idx % N;
-    const long t = idx / N;
-    const int k = t % K;
-    const int b = t / K;
+    const int k = idx % K;  // k fastest: consecutive threads write consecutive columns of E
+    const long t = idx / K;
+    const int n = t % N;
+    const int b = t / N;
     const float2 y = Y[(long)b * sy + (long)k * ldy + n];
     O* e0 = E + (long)b * se + (long)(2 * n) * lde + 2 * k;
     O* e1 = e0 + lde;
