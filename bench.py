@@ -271,6 +271,57 @@ def main():
                 "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
     roof["stage_ms"] = {k: round(v, 3) for k, v in sorted(stages.items(), key=lambda kv: -kv[1])}
 
+    # reconstruction error of this path and of the FP64 path on the same tensor ("equal error")
+    def rel_err(U, S, V, Xref):
+        Sf = torch.zeros((d["n3"], d["R"], d["R"]), dtype=torch.float64, device=dev)
+        Sf.diagonal(dim1=1, dim2=2).copy_(S.double())
+        VT = torch.zeros((d["n3"], d["R"], d["n2"]), dtype=torch.float64, device=dev)
+        VT[0] = V[0].double().T
+        VT[1:] = V.double().flip(0)[:-1].transpose(1, 2)      # tensor transpose (Sec. 2)
+        Xr = api.tprod(api.tprod(U.double(), Sf, "fp64"), VT, "fp64")
+        return float(torch.linalg.vector_norm(Xref - Xr) / torch.linalg.vector_norm(Xref))
+
+    X64 = Xd.double()
+    err_path = rel_err(plan.U, plan.S, plan.V, X64)
+    plan64 = api.RbkPlan(d["n1"], d["n2"], d["n3"], d["R"], d["P"], d["q"], seed=0, precision="fp64", device=dev)
+    plan64(X64)
+    torch.cuda.synchronize(dev)
+    ev64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+    for a, b in ev64:
+        flush.zero_()
+        a.record(stream)
+        plan64(X64)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    fp64_ms = sum(a.elapsed_time(b) for a, b in ev64) / len(ev64)
+    err_fp64 = rel_err(plan64.U, plan64.S, plan64.V, X64)
+    opt = float(np.sqrt(wl.optimal_error2(wl.c2_sigma(d["n1"]), d["R"])) / torch.linalg.vector_norm(X64).item())
+
+    # t-product throughput on the paper-shaped products (flops 8 n1 n2 n4 h, whole call incl. FFTs)
+    tprod_tflops = {}
+    for name, n1, n2, n4, n3 in (("2048x2048x128*2048x120x128", 2048, 2048, 120, 128),
+                                 ("1024x1024x64*1024x1024x64", 1024, 1024, 1024, 64),
+                                 ("256x20x100*20x256x100", 256, 20, 256, 100)):
+        fl = 8.0 * n1 * n2 * n4 * (n3 // 2 + 1)
+        row = {}
+        for prec in ("fp64", "fp32", "tf32", "bf16"):
+            dt = torch.float64 if prec == "fp64" else torch.float32
+            A = torch.randn(n3, n1, n2, device=dev, dtype=dt)
+            B = torch.randn(n3, n2, n4, device=dev, dtype=dt)
+            api.tprod(A, B, prec)
+            ts = []
+            for _ in range(3):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                api.tprod(A, B, prec)
+                b.record(stream)
+                torch.cuda.synchronize(dev)
+                ts.append(a.elapsed_time(b))
+            row[prec] = round(fl / (min(ts) * 1e-3) / 1e12, 3)
+            del A, B
+        tprod_tflops[name] = row
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "T-SVD/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
@@ -279,7 +330,13 @@ def main():
                 "config": {"workload": d["name"], "precision": args.precision, "m_eff": d["m"],
                            "l2": "flushed between steps (256 MB write)", "parallelism": "dp%d" % world},
                 "e2e": {"value": e2e_value, "unit": "T-SVD/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches_timed, "roofline": roof, "clocks": clk.summary()}
+                "gpu_launches": launches_timed, "roofline": roof, "clocks": clk.summary(),
+                "paths": {"this": {"precision": args.precision, "ms_per_tsvd": 1000 * total_s / args.steps,
+                                   "rel_error": err_path},
+                          "fp64": {"ms_per_tsvd": fp64_ms, "tsvd_per_s": 1000.0 / fp64_ms, "rel_error": err_fp64},
+                          "speedup_vs_fp64": fp64_ms / (1000 * total_s / args.steps),
+                          "eckart_young_optimum_rel_error": opt},
+                "tprod_tflops": tprod_tflops}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(X, d)
         print(json.dumps(line), flush=True)

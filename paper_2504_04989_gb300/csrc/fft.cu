@@ -23,6 +23,11 @@ __device__ __forceinline__ cx_t<T> twiddle(int p, int n, int sign) {
   if (2 * p == n) return mkc(T(-1), T(0));
   if (4 * p == n) return mkc(T(0), T(sign));
   if (4 * p == 3 * n) return mkc(T(0), T(-sign));
+  if (sizeof(T) == sizeof(float)) {
+    float s, c;
+    sincospif(2.0f * (float)p / (float)n, &s, &c);
+    return mkc((T)c, (T)(sign * s));
+  }
   double s, c;
   sincospi(2.0 * (double)p / (double)n, &s, &c);
   return mkc((T)c, (T)(sign * s));
@@ -232,8 +237,9 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_rfft3_fft(const T* __restric
   const int n = P.n, h = n / 2 + 1, TT = P.tubes;
   C* tw = (C*)fsm;                                  // [n]
   C* zb = tw + n;                                   // [FFT_WARPS][2][n]
-  C* otile = zb + (size_t)FFT_WARPS * 2 * n;        // [h][TT] complex
-  T* itile = (T*)(otile + (size_t)h * TT);          // [n][TT] real
+  const int LD = TT + 1;                            // padded row stride: conflict-free column walks
+  C* otile = zb + (size_t)FFT_WARPS * 2 * n;        // [h][LD] complex
+  T* itile = (T*)(otile + (size_t)h * LD);          // [n][LD] real
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long e0 = (long)blockIdx.x * TT;
   for (int p = threadIdx.x; p < n; p += blockDim.x) tw[p] = twiddle<T>(p, n, -1);
@@ -252,7 +258,7 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_rfft3_fft(const T* __restric
 #pragma unroll
       for (int u = 0; u < FFT_LOADS; ++u) {
         const int idx = base + u * blockDim.x;
-        if (idx < total) itile[idx] = v[u];
+        if (idx < total) itile[(idx / TT) * LD + idx % TT] = v[u];
       }
     }
   }
@@ -261,13 +267,13 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_rfft3_fft(const T* __restric
   C* zc = za + n;
   const T hf = T(0.5);
   for (int s = warp; s < TT / 2; s += FFT_WARPS) {
-    for (int t = lane; t < n; t += 32) za[t] = mkc(itile[t * TT + 2 * s], itile[t * TT + 2 * s + 1]);
+    for (int t = lane; t < n; t += 32) za[t] = mkc(itile[t * LD + 2 * s], itile[t * LD + 2 * s + 1]);
     __syncwarp();
     const C* Z = fft_run<C>(za, zc, tw, P, lane);
     for (int k = lane; k < h; k += 32) {
       const C zk = Z[k], zn = Z[(n - k) % n];
-      otile[k * TT + 2 * s] = mkc(hf * (zk.x + zn.x), hf * (zk.y - zn.y));      // X_k
-      otile[k * TT + 2 * s + 1] = mkc(hf * (zk.y + zn.y), hf * (zn.x - zk.x));  // Y_k
+      otile[k * LD + 2 * s] = mkc(hf * (zk.x + zn.x), hf * (zk.y - zn.y));      // X_k
+      otile[k * LD + 2 * s + 1] = mkc(hf * (zk.y + zn.y), hf * (zn.x - zk.x));  // Y_k
     }
     __syncwarp();
   }
@@ -275,7 +281,7 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_rfft3_fft(const T* __restric
   for (int idx = threadIdx.x; idx < h * TT; idx += blockDim.x) {
     const int k = idx / TT, e = idx - k * TT;
     const long ge = e0 + e;
-    if (ge < plane) Xh[(long)k * plane + ge] = otile[idx];
+    if (ge < plane) Xh[(long)k * plane + ge] = otile[k * LD + e];
   }
 }
 
@@ -287,8 +293,9 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_irfft3_fft(const cx_t<T>* __
   const int n = P.n, h = n / 2 + 1, TT = P.tubes;
   C* tw = (C*)fsm;                                  // [n]
   C* zb = tw + n;                                   // [FFT_WARPS][2][n]
-  C* itile = zb + (size_t)FFT_WARPS * 2 * n;        // [h][TT] complex
-  T* otile = (T*)(itile + (size_t)h * TT);          // [n][TT] real
+  const int LD = TT + 1;                            // padded row stride: conflict-free column walks
+  C* itile = zb + (size_t)FFT_WARPS * 2 * n;        // [h][LD] complex
+  T* otile = (T*)(itile + (size_t)h * LD);          // [n][LD] real
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long e0 = (long)blockIdx.x * TT;
   for (int p = threadIdx.x; p < n; p += blockDim.x) tw[p] = twiddle<T>(p, n, +1);
@@ -308,7 +315,7 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_irfft3_fft(const cx_t<T>* __
 #pragma unroll
       for (int u = 0; u < FFT_LOADS; ++u) {
         const int idx = base + u * blockDim.x;
-        if (idx < total) itile[idx] = v[u];
+        if (idx < total) itile[(idx / TT) * LD + idx % TT] = v[u];
       }
     }
   }
@@ -320,19 +327,19 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_irfft3_fft(const cx_t<T>* __
     for (int k = lane; k < n; k += 32) {
       C x, y;
       if (k < h) {
-        x = itile[k * TT + 2 * s];
-        y = itile[k * TT + 2 * s + 1];
+        x = itile[k * LD + 2 * s];
+        y = itile[k * LD + 2 * s + 1];
       } else {
-        x = cconj(itile[(n - k) * TT + 2 * s]);
-        y = cconj(itile[(n - k) * TT + 2 * s + 1]);
+        x = cconj(itile[(n - k) * LD + 2 * s]);
+        y = cconj(itile[(n - k) * LD + 2 * s + 1]);
       }
       za[k] = mkc(x.x - y.y, x.y + y.x);  // Z = X + i Y
     }
     __syncwarp();
     const C* z = fft_run<C>(za, zc, tw, P, lane);
     for (int t = lane; t < n; t += 32) {
-      otile[t * TT + 2 * s] = z[t].x * inv;
-      otile[t * TT + 2 * s + 1] = z[t].y * inv;
+      otile[t * LD + 2 * s] = z[t].x * inv;
+      otile[t * LD + 2 * s + 1] = z[t].y * inv;
     }
     __syncwarp();
   }
@@ -340,7 +347,7 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_irfft3_fft(const cx_t<T>* __
   for (int idx = threadIdx.x; idx < n * TT; idx += blockDim.x) {
     const int t = idx / TT, e = idx - t * TT;
     const long ge = e0 + e;
-    if (ge < plane) X[(long)t * plane + ge] = otile[idx];
+    if (ge < plane) X[(long)t * plane + ge] = otile[t * LD + e];
   }
 }
 
@@ -348,7 +355,8 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_irfft3_fft(const cx_t<T>* __
 template <typename T>
 static size_t fft_smem(int n, int tt) {
   const int h = n / 2 + 1;
-  return sizeof(cx_t<T>) * ((size_t)n + (size_t)FFT_WARPS * 2 * n + (size_t)h * tt) + sizeof(T) * (size_t)n * tt;
+  return sizeof(cx_t<T>) * ((size_t)n + (size_t)FFT_WARPS * 2 * n + (size_t)h * (tt + 1)) +
+         sizeof(T) * (size_t)n * (tt + 1);
 }
 
 template <typename T>
