@@ -155,6 +155,25 @@ TSVD_API int tproj_backward(const void* Q, const void* A, const void* dY, void* 
                    int precision, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * ttranspose -- tensor transpose (Sec. 2, Definition of the transpose):
+ * AT(:,:,1) = A(:,:,1)^T and AT(:,:,k) = A(:,:,n3+2-k)^T for k = 2..n3 (1-based).
+ *   A device (n3, n1, n2), AT device out (n3, n2, n1); double for TSVD_FP64,
+ *   float otherwise.  Out of place (A and AT must not overlap).
+ */
+TSVD_API int ttranspose(const void* A, void* AT, int n1, int n2, int n3, int precision, void* stream);
+
+/*
+ * tsvd_masked_residual -- residual of the completion objective
+ * ||P_Omega(C) - P_Omega(X)||_F^2 (the observation operator of Ex. 3):
+ *   R = M .* (C - X) element-wise and *loss = sum(R^2) (FP64, device).
+ *   C, X, R device arrays of n elements (double for TSVD_FP64, float
+ *   otherwise); mask device uint8 (nonzero = observed); partial device
+ *   scratch of 1024 doubles.  The sum is reduced in a fixed order.
+ */
+TSVD_API int tsvd_masked_residual(const void* C, const void* X, const uint8_t* mask, void* R, double* loss,
+                                  double* partial, long n, int precision, void* stream);
+
+/*
  * tprod_noalloc -- the t-product C = A * B of tprod(), for callers that cannot
  * allocate device memory (an arena or pool that must not grow, a plug-in whose
  * host process owns every device allocation, a real-time loop where an

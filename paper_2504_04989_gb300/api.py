@@ -273,3 +273,33 @@ class profile:
 def launch_count():
     """Kernels launched by libtsvd so far in this process."""
     return int(_lib.load().tsvd_launch_count())
+
+
+def ttranspose(A, precision=None):
+    """Tensor transpose (Sec. 2): (n3, n1, n2) -> (n3, n2, n1)."""
+    lib = _lib.load()
+    precision = _precision_of(A, precision)
+    A = A.contiguous()
+    _need_cuda(A, dtype=_DT[precision])
+    n3, n1, n2 = A.shape
+    out = torch.empty((n3, n2, n1), dtype=A.dtype, device=A.device)
+    with torch.cuda.device(A.device):
+        _lib.check(lib.ttranspose(_ptr(A), _ptr(out), n1, n2, n3, _prec(precision), _stream(A.device)), "ttranspose")
+    return out
+
+
+def masked_residual(C, X, mask, out=None, loss=None, partial=None):
+    """R = mask .* (C - X) and the FP64 sum of R^2 (device scalar)."""
+    lib = _lib.load()
+    precision = _precision_of(C, None)
+    C, X = C.contiguous(), X.contiguous()
+    _need_cuda(C, X, dtype=C.dtype)
+    if mask.dtype != torch.uint8 or not mask.is_cuda or mask.numel() != C.numel():
+        raise ValueError("mask must be a CUDA uint8 tensor with C's number of elements")
+    R = torch.empty_like(C) if out is None else out
+    loss = torch.empty((), dtype=torch.float64, device=C.device) if loss is None else loss
+    partial = torch.empty(1024, dtype=torch.float64, device=C.device) if partial is None else partial
+    with torch.cuda.device(C.device):
+        _lib.check(lib.tsvd_masked_residual(_ptr(C), _ptr(X), _ptr(mask), _ptr(R), _ptr(loss), _ptr(partial),
+                                            C.numel(), _prec(precision), _stream(C.device)), "masked_residual")
+    return R, loss

@@ -1,0 +1,125 @@
+"""Differentiable completion (the data-completion application of Ex. 3 in
+gradient form): tensor transpose, fused masked residual, gradient of the
+masked loss through the hand-written t-product backward (against finite
+differences and the FP64 oracle gradient), and the 256 x 256 x 100 tubal-rank-20
+workload with a Bernoulli(0.3) mask."""
+import numpy as np
+import pytest
+
+from paper_2504_04989_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+rng = np.random.default_rng(7)
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2504_04989_gb300 import api, completion
+    return api, completion
+
+
+def dev(x, dt=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda", dt)
+
+
+@pytest.mark.parametrize("n1,n2,n3", [(1, 1, 1), (33, 70, 5), (64, 31, 8)])
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+def test_ttranspose(mods, orc, n1, n2, n3, dt):
+    api, _ = mods
+    A = rng.standard_normal((n3, n1, n2))
+    got = api.ttranspose(dev(A, dt)).double().cpu().numpy()
+    ref = orc.ttranspose(A.astype(np.float32).astype(np.float64) if dt == torch.float32 else A)
+    np.testing.assert_array_equal(got, ref)  # a permutation: bit exact
+
+
+@pytest.mark.parametrize("n", [1, 1000, 1 << 20])
+def test_masked_residual(mods, n):
+    api, _ = mods
+    C, X = rng.standard_normal(n), rng.standard_normal(n)
+    M = (rng.random(n) < 0.3).astype(np.uint8)
+    R, loss = api.masked_residual(dev(C), dev(X), torch.from_numpy(M).cuda())
+    ref = M * (C - X)
+    np.testing.assert_array_equal(R.cpu().numpy(), ref)
+    assert np.isclose(loss.item(), np.sum(ref ** 2), rtol=1e-12)
+
+
+def test_masked_loss_gradient_fd_and_oracle(mods, orc):
+    api, comp = mods
+    n1, n2, n3, R = 9, 7, 6, 3
+    X = rng.standard_normal((n3, n1, n2))
+    M = (rng.random(X.shape) < 0.4).astype(np.uint8)
+    U, W = rng.standard_normal((n3, n1, R)), rng.standard_normal((n3, R, n2))
+    loss, dU, dW = comp.masked_loss_grad(dev(U), dev(W), dev(X), torch.from_numpy(M).cuda(), "fp64")
+    # FP64 oracle reference gradient: dC = 2 M .* (U * W - X) through the oracle adjoint
+    Cr = orc.tprod(U, W)
+    rU, rW = orc.tprod_backward(U, W, 2.0 * M * (Cr - X))
+    np.testing.assert_allclose(dU.cpu().numpy(), rU, atol=1e-11)
+    np.testing.assert_allclose(dW.cpu().numpy(), rW, atol=1e-11)
+    assert np.isclose(loss.item(), np.sum((M * (Cr - X)) ** 2), rtol=1e-12)
+    # central finite differences of the loss (quadratic in each factor: exact up to rounding)
+    f = lambda U_, W_: np.sum((M * (orc.tprod_bcirc(U_, W_) - X)) ** 2)
+    for _ in range(3):
+        E, F = rng.standard_normal(U.shape), rng.standard_normal(W.shape)
+        eps = 1e-4
+        fd = (f(U + eps * E, W + eps * F) - f(U - eps * E, W - eps * F)) / (2 * eps)
+        an = np.sum(dU.cpu().numpy() * E) + np.sum(dW.cpu().numpy() * F)
+        assert np.isclose(fd, an, rtol=1e-6)
+
+
+def test_fp32_gradient_against_fp64_reference(mods, orc):
+    api, comp = mods
+    n1, n2, n3, R = 40, 30, 10, 4
+    X = rng.standard_normal((n3, n1, n2)).astype(np.float32).astype(np.float64)
+    M = (rng.random(X.shape) < 0.3).astype(np.uint8)
+    U = rng.standard_normal((n3, n1, R)).astype(np.float32).astype(np.float64)
+    W = rng.standard_normal((n3, R, n2)).astype(np.float32).astype(np.float64)
+    _, dU, dW = comp.masked_loss_grad(dev(U, torch.float32), dev(W, torch.float32), dev(X, torch.float32),
+                                      torch.from_numpy(M).cuda(), "fp32")
+    Cr = orc.tprod(U, W)
+    rU, rW = orc.tprod_backward(U, W, 2.0 * M * (Cr - X))
+    for g, r in ((dU, rU), (dW, rW)):
+        rel = np.linalg.norm(g.double().cpu().numpy() - r) / np.linalg.norm(r)
+        assert rel < 1e-5, rel
+
+
+@pytest.mark.slow
+def test_completion_c5_converges(mods):
+    """256 x 256 x 100, tubal rank 20, 30% of the entries observed: the
+    gradient iterations from the Krylov initialisation reduce the error on the
+    unobserved entries by orders of magnitude."""
+    api, comp = mods
+    X, mask = wl.make_c5(0)
+    Xd = dev(X, torch.float32)
+    Md = torch.from_numpy(mask.astype(np.uint8)).cuda()
+    Xobs = Xd * Md
+
+    def rec_err(U, W):
+        C = api.tprod(U, W, "fp32")
+        return float(torch.linalg.vector_norm(C - Xd) / torch.linalg.vector_norm(Xd))
+
+    U0, W0 = comp.spectral_init(Xobs, Md, 20)
+    e0 = rec_err(U0, W0)
+    U, W, losses = comp.complete(Xobs, Md, 20, steps=300)
+    e1 = rec_err(U, W)
+    assert losses[-1] < losses[0] * 1e-4, (losses[0], losses[-1])
+    assert e1 < 0.1 * e0 and e1 < 1e-2, (e0, e1)
+
+
+@pytest.mark.slow
+def test_completion_fill_in_iteration(mods):
+    """The fill-in iteration of Ex. 3 with Alg. 2 as the low-rank operator:
+    the error on the same workload falls below 5% within 60 iterations and
+    never rises by more than rounding from one iteration to the next."""
+    api, comp = mods
+    X, mask = wl.make_c5(0)
+    Xd = dev(X, torch.float32)
+    Md = torch.from_numpy(mask.astype(np.uint8)).cuda()
+    errs = []
+    comp.complete_fill_in(Xd * Md, Md, 20, iters=60,
+                          callback=lambda it, Xr: errs.append(
+                              float(torch.linalg.vector_norm(Xr - Xd) / torch.linalg.vector_norm(Xd))))
+    assert errs[-1] < 0.05, errs[-1]
+    assert all(b <= a * 1.01 for a, b in zip(errs, errs[1:])), errs
