@@ -174,6 +174,24 @@ TSVD_API int tsvd_masked_residual(const void* C, const void* X, const uint8_t* m
                                   double* partial, long n, int precision, void* stream);
 
 /*
+ * tsvd_error -- squared approximation error ||X - U * S * V^T||_F^2 of a
+ * truncated T-SVD (the error measure of the experiments, Sec. 5), evaluated
+ * in the Fourier domain: Parseval (Sec. 2) over the floor(n3/2)+1 leading
+ * Fourier slices with weight 1 for slice 0 and slice n3/2 (n3 even) and 2 for
+ * the rest, one fused pass per slice that forms X_k - U_k diag(s_k) V_k^H
+ * tile by tile and accumulates only its squared modulus (FP64).
+ *   X device (n3, n1, n2); U device (n3, n1, R); S device (n3, R) diagonal
+ *   tubes of the f-diagonal S; V device (n3, n2, R) (tsvd_rbk's layouts).
+ *   err2   device out, one double.
+ *   precision TSVD_FP64 (double arrays, FP64 arithmetic) or any other
+ *   (float arrays; FP32 products, FP64 accumulation of the squares).
+ *   ws, ws_bytes  device workspace of tsvd_error_workspace_size bytes.
+ */
+TSVD_API int tsvd_error_workspace_size(int n1, int n2, int n3, int R, int precision, size_t* bytes);
+TSVD_API int tsvd_error(const void* X, const void* U, const void* S, const void* V, int n1, int n2, int n3, int R,
+                        int precision, double* err2, void* ws, size_t ws_bytes, void* stream);
+
+/*
  * tprod_noalloc -- the t-product C = A * B of tprod(), for callers that cannot
  * allocate device memory (an arena or pool that must not grow, a plug-in whose
  * host process owns every device allocation, a real-time loop where an

@@ -47,6 +47,8 @@ SIGNATURES = {
     "tproj_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _sz, _vp]),
     "ttranspose": (_i, [_vp, _vp, _i, _i, _i, _i, _vp]),
     "tsvd_masked_residual": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_long, _i, _vp]),
+    "tsvd_error_workspace_size": (_i, [_i, _i, _i, _i, _i, C.POINTER(C.c_size_t)]),
+    "tsvd_error": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, C.c_size_t, _vp]),
     "tprod_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp]),
     "tsvd_gaussian": (_i, [_u64, _u32, _u32, _l, _vp, _vp]),
     "tsvd_philox_words": (_i, [C.POINTER(_u32), _u32, _u32, _u32, _l, _vp, _vp]),

@@ -288,6 +288,29 @@ def ttranspose(A, precision=None):
     return out
 
 
+def tsvd_error(X, U, S, V, precision=None):
+    """||X - U * S * V^T||_F^2 (device FP64 scalar) for the layouts of rbk:
+    X (n3, n1, n2), U (n3, n1, R), S (n3, R) diagonal tubes, V (n3, n2, R).
+    Fused Fourier-domain evaluation (Parseval over the half spectrum)."""
+    lib = _lib.load()
+    precision = _precision_of(X, precision)
+    pr = _prec(precision)
+    X, U, S, V = (t.contiguous() for t in (X, U, S, V))
+    _need_cuda(X, U, S, V, dtype=_DT[precision])
+    n3, n1, n2 = X.shape
+    R = U.shape[2]
+    if U.shape != (n3, n1, R) or S.shape != (n3, R) or V.shape != (n3, n2, R):
+        raise ValueError("tsvd_error: U (n3,n1,R), S (n3,R), V (n3,n2,R) required")
+    nbytes = C.c_size_t()
+    _lib.check(lib.tsvd_error_workspace_size(n1, n2, n3, R, pr, C.byref(nbytes)), "tsvd_error_workspace_size")
+    ws = _workspace(nbytes.value, X.device)
+    out = torch.empty((), dtype=torch.float64, device=X.device)
+    with torch.cuda.device(X.device):
+        _lib.check(lib.tsvd_error(_ptr(X), _ptr(U), _ptr(S), _ptr(V), n1, n2, n3, R, pr, _ptr(out), _ptr(ws),
+                                  nbytes.value, _stream(X.device)), "tsvd_error")
+    return out
+
+
 def masked_residual(C, X, mask, out=None, loss=None, partial=None):
     """R = mask .* (C - X) and the FP64 sum of R^2 (device scalar)."""
     lib = _lib.load()

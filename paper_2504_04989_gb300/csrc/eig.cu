@@ -211,6 +211,335 @@ __global__ void __launch_bounds__(512) k_hetrd(double2* __restrict__ G, long ldg
   }
 }
 
+// ---------------------------------------------------------------------------
+// Householder tridiagonalisation with the lower triangle resident in shared
+// memory.  One cluster of CL CTAs per slice; CTA c owns global rows
+// g = c + CL q, stored packed (row g holds columns 0..g).  GB300 issues FP64
+// at 2 DFMA per clock per SM, so the kernel is organised to spend its FP64
+// instructions on the 16 DFMA per trailing element and step that the method
+// needs, on full warps:
+//   * the rank-2 update of step j-1 is applied lazily inside step j's pass
+//     over the trailing triangle (one visit per element and step);
+//   * the work of a pass is cut into equal contiguous segments, one per
+//     thread, of a row-major enumeration (row part sum_k A(g,k) v_k) and of
+//     a column-major enumeration (transposed part sum_g conj(A(g,k)) v_g), so
+//     every accumulation is private to a thread; rows or columns split
+//     between threads are summed from per-thread slots in thread order
+//     (deterministic);
+//   * the column x_j and the partial products are exchanged through
+//     distributed shared memory with two cluster barriers per step.
+// Step j (A^{(j)} = the matrix after j reflectors; the stored S lags one
+// update behind: S = A^{(j-1)} on the trailing block):
+//   x_g = S(g,j) - v'_g conj(w'_j) - w'_g conj(v'_j)      (v', w' of step j-1)
+//   alpha = -e^{i arg x_0} ||x||,  v = (x - alpha e_1) / ||x - alpha e_1||
+//   S(g,k) <- S(g,k) - v'_g conj(w'_k) - w'_g conj(v'_k)   (k <= g, both > j)
+//   p = 2 A^{(j)} v,  w = p - (v^H p) v
+// ---------------------------------------------------------------------------
+constexpr int HS_THREADS = 256;
+
+__host__ __device__ __forceinline__ int hs_own_rows(int m, int c, int CL) { return (c < m) ? (m - 1 - c) / CL + 1 : 0; }
+__host__ __device__ __forceinline__ int hs_rowbase(int q, int c, int CL) { return q * (c + 1) + CL * q * (q - 1) / 2; }
+// first own row index q with c + CL q > j
+__host__ __device__ __forceinline__ int hs_qfirst(int j, int c, int CL) { return (j < c) ? 0 : (j - c) / CL + 1; }
+
+static size_t hetrd_smem_elems(int m, int CL) {
+  int mx = 0;
+  for (int c = 0; c < CL; ++c) mx = std::max(mx, hs_rowbase(hs_own_rows(m, c, CL), c, CL));
+  return (size_t)mx;
+}
+static size_t hetrd_smem_bytes(int m, int CL) {
+  const size_t el = (hetrd_smem_elems(m, CL) + 5 * (size_t)m + 2 * HS_THREADS) * sizeof(double2);
+  return el + (size_t)(m + 1) * sizeof(int);
+}
+
+// segment start of thread t when E elements are cut into HS_THREADS pieces
+__device__ __forceinline__ int hs_seg(int t, int E) { return (int)(((long)t * E) / HS_THREADS); }
+// the thread whose segment holds element e (the last t with hs_seg(t) <= e)
+__device__ __forceinline__ int hs_owner(int e, int E) {
+  int t = (int)(((long)e * HS_THREADS) / E);
+  while (t + 1 < HS_THREADS && hs_seg(t + 1, E) <= e) ++t;
+  while (t > 0 && hs_seg(t, E) > e) --t;
+  return t;
+}
+
+template <int CL>
+__global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_smem(const double2* __restrict__ G, long ldg, long sG, int m,
+                                                           int s_elems, EigScratch e) {
+  extern __shared__ __align__(16) double2 hsm[];
+  double2* S = hsm;                            // own rows, packed
+  double2* bufV = S + s_elems;                 // [2][m] v of this and of the previous step
+  double2* bufW = bufV + 2 * m;                // [2][m] w
+  double2* pv = bufW + 2 * m;                  // [m] this CTA's part of p
+  double2* slotF = pv + m;                     // [T] partial of a thread's first (split) row / column
+  double2* slotL = slotF + HS_THREADS;         // [T] partial of a thread's last (split) row / column
+  int* CP = (int*)(slotL + HS_THREADS);        // [m+1] prefix of the per-column own-row counts
+  __shared__ double red[2 * (HS_THREADS / 32)];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int c = (CL > 1) ? (int)cluster.block_rank() : 0;
+  const int b = blockIdx.x / CL;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = HS_THREADS / 32;
+  G += (long)b * sG;
+  double2* Hv = e.Hv + (long)b * m * m;
+  const int nq = hs_own_rows(m, c, CL);
+
+  // load the own rows of the lower triangle; column prefix counts
+  for (int q = warp; q < nq; q += NW) {
+    const int g = c + CL * q;
+    const double2* src = G + (long)g * ldg;
+    double2* dst = S + hs_rowbase(q, c, CL);
+    for (int k = lane; k <= g; k += 32) dst[k] = __ldcg(src + k);
+  }
+  if (tid == 0) {
+    int acc = 0;
+    for (int k = 0; k < m; ++k) {
+      CP[k] = acc;
+      acc += max(0, nq - hs_qfirst(k, c, CL));
+    }
+    CP[m] = acc;
+  }
+  for (int i = tid; i < 4 * m; i += HS_THREADS) bufV[i] = make_double2(0, 0);  // v', w' of "step -1"
+  if (CL > 1) cluster.sync();
+  else __syncthreads();
+
+  for (int j = 0; j < m - 1; ++j) {
+    const int cur = j & 1;
+    double2* v = bufV + cur * m;
+    double2* w = bufW + cur * m;
+    const double2* vp = bufV + (cur ^ 1) * m;
+    const double2* wp = bufW + (cur ^ 1) * m;
+    const bool lag = j > 0;
+    // (0) column j of A^{(j)} from the own rows, pushed to every CTA's v
+    {
+      const double2 vpj = vp[j], wpj = wp[j];
+      for (int q = hs_qfirst(j, c, CL) + tid; q < nq; q += HS_THREADS) {
+        const int g = c + CL * q;
+        double2 a = S[hs_rowbase(q, c, CL) + j];
+        if (lag) {
+          const double2 vg = vp[g], wg = wp[g];
+          a.x -= vg.x * wpj.x + vg.y * wpj.y + wg.x * vpj.x + wg.y * vpj.y;
+          a.y -= vg.y * wpj.x - vg.x * wpj.y + wg.y * vpj.x - wg.x * vpj.y;
+        }
+#pragma unroll
+        for (int rr = 0; rr < CL; ++rr) {
+          double2* dst = (CL > 1) ? cluster.map_shared_rank(v, rr) : v;
+          dst[g] = a;
+        }
+      }
+      if (tid == 0 && (j % CL) == c) {
+        const double2 s = S[hs_rowbase((j - c) / CL, c, CL) + j];
+        e.d[(long)b * m + j] = s.x - 2.0 * (vpj.x * wpj.x + vpj.y * wpj.y);
+      }
+    }
+    if (CL > 1) cluster.sync();
+    else __syncthreads();
+    // (1) the reflector (every CTA forms the same v)
+    const int n = m - j - 1;
+    const double2 x0 = v[j + 1];
+    double part = 0;
+    for (int i = tid; i < n; i += HS_THREADS) part += cabs2(v[j + 1 + i]);
+    for (int i = tid; i < n; i += HS_THREADS) pv[j + 1 + i] = make_double2(0, 0);
+    const double nrm2 = block_sum(part, red);
+    const bool skip = !(nrm2 > 0.0);
+    double2 alpha = make_double2(0, 0);
+    double vinv = 0.0;
+    if (!skip) {
+      const double nrm = sqrt(nrm2), ax0 = sqrt(cabs2(x0));
+      const double2 ph = (ax0 > 0) ? cscale(x0, 1.0 / ax0) : make_double2(1, 0);
+      alpha = cscale(ph, -nrm);
+      vinv = 1.0 / sqrt(2.0 * nrm * (nrm + ax0));
+    }
+    for (int i = tid; i < n; i += HS_THREADS) {
+      double2 vi = v[j + 1 + i];
+      if (i == 0) vi = csub(vi, alpha);
+      vi = cscale(vi, vinv);
+      v[j + 1 + i] = vi;
+      if (c == 0) Hv[(long)j * m + j + 1 + i] = vi;
+    }
+    if (c == 0 && tid == 0) e.alpha[(long)b * m + j] = alpha;
+    __syncthreads();
+
+    // (2) row pass: lazy update of S and the row part of A v over own rows g > j, columns j+1..g
+    const int q0 = hs_qfirst(j, c, CL);
+    const int nr = max(0, nq - q0);
+    const int g0 = c + CL * q0;
+    const int E1 = nr * (g0 - j) + CL * nr * (nr - 1) / 2;  // sum of the row lengths g - j
+    if (E1 > 0) {
+      const int e0 = hs_seg(tid, E1), e1 = hs_seg(tid + 1, E1);
+      if (e0 < e1) {
+        // row i holds elements [P(i), P(i+1)), P(i) = i (g0 - j) + CL i (i - 1) / 2
+        int lo = 0, hi = nr - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (mid * (g0 - j) + CL * mid * (mid - 1) / 2 <= e0) lo = mid;
+          else hi = mid - 1;
+        }
+        int i = lo;
+        int Pi = i * (g0 - j) + CL * i * (i - 1) / 2;
+        int g = g0 + CL * i;
+        int k = j + 1 + (e0 - Pi);
+        double2* row = S + hs_rowbase(q0 + i, c, CL);
+        bool whole = (e0 == Pi), first = true;
+        double2 vg = vp[g], wg = wp[g];
+        double2 acc = make_double2(0, 0);
+        for (int el = e0; el < e1; ++el) {
+          double2 a = row[k];
+          if (lag) {
+            const double2 wk = wp[k], vk = vp[k];
+            a.x = fma(-vg.x, wk.x, a.x);
+            a.x = fma(-vg.y, wk.y, a.x);
+            a.x = fma(-wg.x, vk.x, a.x);
+            a.x = fma(-wg.y, vk.y, a.x);
+            a.y = fma(-vg.y, wk.x, a.y);
+            a.y = fma(vg.x, wk.y, a.y);
+            a.y = fma(-wg.y, vk.x, a.y);
+            a.y = fma(wg.x, vk.y, a.y);
+            if (k == g) a.y = 0.0;  // the diagonal stays real
+            row[k] = a;
+          }
+          cfma(acc, a, v[k]);
+          if (++k > g) {  // row g done
+            if (whole) pv[g] = acc;
+            else slotF[tid] = acc;  // a row ending here but started earlier is this thread's first row
+            first = false;
+            whole = true;
+            acc = make_double2(0, 0);
+            row += g + 1;
+            g += CL;
+            k = j + 1;
+            if (el + 1 < e1) {
+              vg = vp[g];
+              wg = wp[g];
+            }
+          }
+        }
+        if (k != j + 1) {  // the segment ends inside row g
+          if (first) slotF[tid] = acc;
+          else slotL[tid] = acc;
+        }
+      }
+      __syncthreads();
+      // rows split between threads: fixed-order sum of the slots
+      for (int i = tid; i < nr; i += HS_THREADS) {
+        const int Pi = i * (g0 - j) + CL * i * (i - 1) / 2;
+        const int len = g0 + CL * i - j;
+        const int ta = hs_owner(Pi, E1), tb = hs_owner(Pi + len - 1, E1);
+        if (ta == tb) continue;
+        double2 s = (hs_seg(ta, E1) == Pi) ? slotF[ta] : slotL[ta];
+        for (int t = ta + 1; t <= tb; ++t)
+          if (hs_seg(t, E1) < hs_seg(t + 1, E1)) s = cadd(s, slotF[t]);
+        pv[g0 + CL * i] = s;
+      }
+    }
+    __syncthreads();
+
+    // (3) column pass: transposed part sum_{g > k} conj(S(g,k)) v_g, columns k > j
+    const int cb = CP[j + 1];
+    const int E2 = CP[m] - cb;
+    if (E2 > 0) {
+      const int e0 = hs_seg(tid, E2), e1 = hs_seg(tid + 1, E2);
+      if (e0 < e1) {
+        int lo = j + 1, hi = m - 1;  // last column k with CP[k] <= cb + e0
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (CP[mid] <= cb + e0) lo = mid;
+          else hi = mid - 1;
+        }
+        int k = lo;
+        int o = cb + e0 - CP[k];
+        int cnt = CP[k + 1] - CP[k];
+        int q = hs_qfirst(k, c, CL) + o;
+        int g = c + CL * q, base = hs_rowbase(q, c, CL);
+        bool whole = (o == 0), first = true;
+        double2 acc = make_double2(0, 0);
+        for (int el = e0; el < e1; ++el) {
+          cfmac(acc, S[base + k], v[g]);
+          base += g + 1;  // next own row
+          g += CL;
+          if (++o == cnt) {  // column k done
+            if (whole) pv[k] = cadd(pv[k], acc);
+            else slotF[tid] = acc;
+            first = false;
+            whole = true;
+            acc = make_double2(0, 0);
+            if (el + 1 < e1) {
+              do {
+                ++k;
+              } while (CP[k + 1] == CP[k]);
+              cnt = CP[k + 1] - CP[k];
+              q = hs_qfirst(k, c, CL);
+              g = c + CL * q;
+              base = hs_rowbase(q, c, CL);
+              o = 0;
+            }
+          }
+        }
+        if (o != cnt && o != 0) {  // the segment ends inside column k
+          if (first) slotF[tid] = acc;
+          else slotL[tid] = acc;
+        }
+      }
+      __syncthreads();
+      for (int k = j + 1 + tid; k < m; k += HS_THREADS) {
+        const int cnt = CP[k + 1] - CP[k];
+        if (cnt == 0) continue;
+        const int s0 = CP[k] - cb;
+        const int ta = hs_owner(s0, E2), tb = hs_owner(s0 + cnt - 1, E2);
+        if (ta == tb) continue;
+        double2 s = (hs_seg(ta, E2) == s0) ? slotF[ta] : slotL[ta];
+        for (int t = ta + 1; t <= tb; ++t)
+          if (hs_seg(t, E2) < hs_seg(t + 1, E2)) s = cadd(s, slotF[t]);
+        pv[k] = cadd(pv[k], s);
+      }
+    }
+    if (CL > 1) cluster.sync();
+    else __syncthreads();
+
+    // (4) p = 2 sum over the cluster's parts (fixed order), w = p - (v^H p) v
+    double2 kp = make_double2(0, 0);
+    for (int i = j + 1 + tid; i < m; i += HS_THREADS) {
+      double2 pi = make_double2(0, 0);
+#pragma unroll
+      for (int rr = 0; rr < CL; ++rr) {
+        const double2* src = (CL > 1) ? cluster.map_shared_rank(pv, rr) : pv;
+        pi = cadd(pi, src[i]);
+      }
+      pi = cscale(pi, 2.0);
+      w[i] = pi;
+      cfmac(kp, v[i], pi);
+    }
+    const double K = block_sum2(kp, red).x;
+    for (int i = j + 1 + tid; i < m; i += HS_THREADS) w[i] = csub(w[i], cscale(v[i], K));
+    __syncthreads();
+  }
+  // last diagonal entry: apply the pending update of step m-2
+  if (tid == 0 && ((m - 1) % CL) == c) {
+    const double2 s = S[hs_rowbase((m - 1 - c) / CL, c, CL) + m - 1];
+    const double2 vq = bufV[((m - 2) & 1) * m + m - 1], wq = bufW[((m - 2) & 1) * m + m - 1];
+    e.d[(long)b * m + m - 1] = (m > 1) ? s.x - 2.0 * (vq.x * wq.x + vq.y * wq.y) : s.x;
+  }
+  __threadfence();
+  if (CL > 1) cluster.sync();
+  else __syncthreads();
+  if (c == 0 && tid == 0) {
+    double2 dl = make_double2(1, 0);
+    e.delta[(long)b * m] = dl;
+    double tn = 0;
+    for (int jj = 0; jj < m - 1; ++jj) {
+      const double2 a = __ldcg(e.alpha + (long)b * m + jj);
+      const double aa = sqrt(cabs2(a));
+      e.f[(long)b * m + jj] = aa;
+      if (aa > 0) dl = cmul(dl, cscale(a, 1.0 / aa));
+      e.delta[(long)b * m + jj + 1] = dl;
+    }
+    for (int jj = 0; jj < m; ++jj) {
+      const double fl = (jj > 0) ? e.f[(long)b * m + jj - 1] : 0.0, fr = (jj < m - 1) ? e.f[(long)b * m + jj] : 0.0;
+      tn = fmax(tn, fabs(__ldcg(e.d + (long)b * m + jj)) + fl + fr);
+    }
+    e.tnorm[b] = tn;
+  }
+}
+
 // Number of eigenvalues below x of the symmetric tridiagonal (d, f) (scaled
 // to norm ~1): sign changes of the Sturm sequence P_0 = 1, P_1 = d_0 - x,
 // P_i = (d_{i-1} - x) P_{i-1} - f_{i-2}^2 P_{i-2}, i.e. negative ratios
@@ -500,6 +829,68 @@ __global__ void __launch_bounds__(BT_WARPS * 32) k_backtransform(int m, int R, E
   for (int i = lane; i < m; i += 32) Ub[(long)i * ldu + r] = u[i];
 }
 
+static int device_attr(cudaDeviceAttr a, int fallback) {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, a, dev) != cudaSuccess || v <= 0) {
+    cudaGetLastError();
+    return fallback;
+  }
+  return v;
+}
+
+// Cluster size of the shared-memory tridiagonalisation, or 0 when the slice's
+// rows do not fit: the largest CL in {8,4,2,1} with batch * CL CTAs resident
+// at once (one per SM), at least 48 rows per CTA (else the per-step barriers
+// dominate) and the packed rows within the opt-in shared memory.
+static int hetrd_smem_cluster(int m, int batch) {
+  if (m < 2) return 0;
+  const int sms = device_attr(cudaDevAttrMultiProcessorCount, 148);
+  const size_t smax = (size_t)device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin, 232448) - 256;
+  for (int CL = 8; CL >= 1; CL >>= 1) {
+    if (CL > 1 && ((long)batch * CL > sms || m / CL < 48)) continue;
+    if (hetrd_smem_bytes(m, CL) <= smax) return CL;
+  }
+  return 0;
+}
+
+template <int CL>
+static int launch_hetrd_smem_t(const double2* G, long ldg, long sG, int m, int batch, const EigScratch& e,
+                               cudaStream_t s) {
+  const size_t smem = hetrd_smem_bytes(m, CL);
+  if (cudaFuncSetAttribute(k_hetrd_smem<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return TSVD_ERR_CUDA;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(batch * CL);
+  cfg.blockDim = dim3(HS_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_hetrd_smem<CL>, G, ldg, sG, m, (int)hetrd_smem_elems(m, CL), e) != cudaSuccess) {
+    cudaGetLastError();
+    return TSVD_ERR_CUDA;
+  }
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
+static int launch_hetrd_smem(int CL, const double2* G, long ldg, long sG, int m, int batch, const EigScratch& e,
+                             cudaStream_t s) {
+  switch (CL) {
+    case 8: return launch_hetrd_smem_t<8>(G, ldg, sG, m, batch, e, s);
+    case 4: return launch_hetrd_smem_t<4>(G, ldg, sG, m, batch, e, s);
+    case 2: return launch_hetrd_smem_t<2>(G, ldg, sG, m, batch, e, s);
+    default: return launch_hetrd_smem_t<1>(G, ldg, sG, m, batch, e, s);
+  }
+}
+
 template <typename C>
 int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double* lam, C* U, long ldu, long sU,
                   void* scratch, int* status, cudaStream_t s) {
@@ -507,7 +898,10 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
   if (m <= 0 || R <= 0 || batch <= 0) return TSVD_OK;
   if (R > m || R > 128 || m > 768) return TSVD_ERR_UNSUPPORTED;  // shared memory of k_hetrd
   EigScratch e = carve_eig(scratch, m, R, batch, nullptr);
-  {
+  if (int CLs = hetrd_smem_cluster(m, batch); CLs > 0) {
+    TSVD_STAGE("eig_hetrd", s);
+    TSVD_TRY(launch_hetrd_smem(CLs, G, ldg, sG, m, batch, e, s));
+  } else {
     TSVD_STAGE("eig_hetrd", s);
     const size_t smem = (2 + 16) * (size_t)m * sizeof(double2);  // v, p and 16 warps' partials
     if (smem > 48 * 1024) {

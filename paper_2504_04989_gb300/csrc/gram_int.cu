@@ -1,0 +1,136 @@
+// gram_int.cu -- the Hermitian Gram G = C C^H of the small SVD of Alg. 2
+// (T-SVD(C) through the eigenpairs of C C^H) on the FP32 path, summed exactly
+// in integer arithmetic.
+//
+// C^H (n2 x m per slice) holds FP32 data.  Each column i is written as
+// 2^(e_i - B) times a vector of integers of at most B+1 bits (one power of two
+// per column, e_i the exponent of the column's largest component), which moves
+// every entry by at most 2^(e_i - B - 1): a perturbation of C of the size of its
+// own FP32 rounding.  The Gram of the scaled integers is then exact in 64-bit
+// integer multiply-adds, and G_ij = 2^(e_i + e_j - 2B) sum_l conj(q_li) q_lj is
+// rounded once, to FP64.  An FP32 Gram would put rounding errors of the order
+// eps32 ||C||^2 on the small eigenvalues sigma_i^2 the method keeps; this form
+// keeps the error at the level of a perturbation of C itself, as the FP64 Gram
+// does, while running on the integer pipe instead of GB300's narrow FP64 unit.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace tsvd {
+
+// mantissa bits B: 2 products per component and n2 terms must stay below 2^63
+static int gram_bits(int n2) {
+  int lg = 0;
+  while ((1L << lg) < n2) ++lg;
+  return std::min(23, (61 - lg) / 2);
+}
+
+// one thread per column of one slice: exponent of the largest |component|,
+// then the scaled integers (round to nearest even)
+__global__ void k_gram_quantize(const float2* __restrict__ CH, long ldc, long sC, int n2, int m, int B,
+                                int2* __restrict__ Q, int* __restrict__ colexp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (i >= m) return;
+  const float2* src = CH + (long)k * sC + i;
+  float mx = 0.0f;
+  for (int l = 0; l < n2; ++l) {
+    const float2 x = src[(long)l * ldc];
+    mx = fmaxf(mx, fmaxf(fabsf(x.x), fabsf(x.y)));
+  }
+  int e = 0;
+  if (mx > 0.0f) frexpf(mx, &e);  // mx < 2^e
+  colexp[(long)k * m + i] = e;
+  int2* dst = Q + (long)k * n2 * m + i;
+  for (int l = 0; l < n2; ++l) {
+    const float2 x = src[(long)l * ldc];
+    dst[(long)l * m] = make_int2((int)rintf(ldexpf(x.x, B - e)), (int)rintf(ldexpf(x.y, B - e)));
+  }
+}
+
+constexpr int GI_TILE = 64;
+constexpr int GI_KC = 16;
+
+// Upper-triangle tiles (ti <= tj) of G per slice; each thread 4 x 4 entries
+// with 64-bit accumulators; the tile and its conjugate transpose are written.
+__global__ void __launch_bounds__(256) k_gram_int(const int2* __restrict__ Q, const int* __restrict__ colexp, int n2,
+                                                  int m, int B, double2* __restrict__ G, long ldg, long sG) {
+  __shared__ int2 Qa[GI_KC][GI_TILE];
+  __shared__ int2 Qb[GI_KC][GI_TILE];
+  const int nt = (m + GI_TILE - 1) / GI_TILE;
+  int ti = 0, rem = blockIdx.x;
+  while (rem >= nt - ti) {
+    rem -= nt - ti;
+    ++ti;
+  }
+  const int tj = ti + rem;
+  const int k = blockIdx.y;
+  const int i0 = ti * GI_TILE, j0 = tj * GI_TILE;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int2* Qk = Q + (long)k * n2 * m;
+  long long re[4][4], im[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) re[a][b] = im[a][b] = 0;
+  for (int l0 = 0; l0 < n2; l0 += GI_KC) {
+    for (int e = threadIdx.x; e < GI_KC * GI_TILE; e += 256) {
+      const int ll = e / GI_TILE, c = e % GI_TILE, l = l0 + ll;
+      const bool lok = l < n2;
+      Qa[ll][c] = (lok && i0 + c < m) ? Qk[(long)l * m + i0 + c] : make_int2(0, 0);
+      Qb[ll][c] = (lok && j0 + c < m) ? Qk[(long)l * m + j0 + c] : make_int2(0, 0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int ll = 0; ll < GI_KC; ++ll) {
+      int2 a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = Qa[ll][ty + 16 * u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) b[u] = Qb[ll][tx + 16 * u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int nai = -a[u].y;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
+          re[u][v] += (long long)a[u].x * b[v].x;
+          re[u][v] += (long long)a[u].y * b[v].y;
+          im[u][v] += (long long)a[u].x * b[v].y;
+          im[u][v] += (long long)nai * b[v].x;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int* ek = colexp + (long)k * m;
+  double2* Gk = G + (long)k * sG;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + ty + 16 * u;
+    if (i >= m) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int j = j0 + tx + 16 * v;
+      if (j >= m) continue;
+      const int sc = ek[i] + ek[j] - 2 * B;
+      const double2 g = make_double2(ldexp((double)re[u][v], sc), ldexp((double)im[u][v], sc));
+      Gk[(long)i * ldg + j] = g;
+      if (ti != tj) Gk[(long)j * ldg + i] = make_double2(g.x, -g.y);
+    }
+  }
+}
+
+int gram_int_fp32(const float2* CH, long ldc, long sC, int n2, int m, int batch, int2* Q, int* colexp, double2* G,
+                  long ldg, long sG, cudaStream_t s) {
+  if (n2 <= 0 || m <= 0 || batch <= 0) return TSVD_OK;
+  if (batch > 65535) return TSVD_ERR_UNSUPPORTED;
+  const int B = gram_bits(n2);
+  k_gram_quantize<<<dim3(cdiv(m, 128), batch), 128, 0, s>>>(CH, ldc, sC, n2, m, B, Q, colexp);
+  TSVD_LAUNCHED();
+  const int nt = cdiv(m, GI_TILE);
+  k_gram_int<<<dim3(nt * (nt + 1) / 2, batch), 256, 0, s>>>(Q, colexp, n2, m, B, G, ldg, sG);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
+}  // namespace tsvd

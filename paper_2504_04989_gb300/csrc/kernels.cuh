@@ -113,4 +113,11 @@ int sigma_from_lambda(const double* lam, int R, int batch, double* sig, cx_t<T>*
 template <typename T>
 int scale_columns_inv(cx_t<T>* V, long ldv, long sV, int rows, int R, const double* lam, int batch, cudaStream_t s);
 
+// gram_int.cu -- G = C C^H (Hermitian, FP64 out) from FP32 C^H (n2 x m per
+// slice, leading dimension ldc): per-column power-of-two scaling to integers
+// and an exact 64-bit integer Gram.  Q (batch x n2 x m int2) and colexp
+// (batch x m) are scratch.
+int gram_int_fp32(const float2* CH, long ldc, long sC, int n2, int m, int batch, int2* Q, int* colexp, double2* G,
+                  long ldg, long sG, cudaStream_t s);
+
 }  // namespace tsvd

@@ -65,7 +65,9 @@ struct RbkWs {
   void* Pl;    // Gram-Schmidt coefficients (m x b)
   void* Gl;    // block Gram matrix (b x b)
   C* CHt;
-  double2* CH64;
+  double2* CH64;  // C^H in FP64 for the Gram (FP64 path: alias of CHt)
+  int2* Qint;     // C^H as scaled integers for the exact Gram (FP32 paths)
+  int* colexp;    // their per-column exponents
   double2* Rs;
   uint32_t* dead;
   int* counters;  // [0] status, [1] dead columns
@@ -100,7 +102,9 @@ static RbkWs<T> carve_rbk(void* base, const RbkDims& d) {
   w.Pl = cv.take<CL>(h * d.m * d.b);
   w.Gl = cv.take<CL>(h * d.b * d.b);
   w.CHt = cv.take<C>(h * d.n2 * d.m);
-  w.CH64 = dbl ? (double2*)w.CHt : cv.take<double2>(h * d.n2 * d.m);
+  w.CH64 = dbl ? (double2*)w.CHt : nullptr;
+  w.Qint = dbl ? nullptr : cv.take<int2>(h * d.n2 * d.m);
+  w.colexp = dbl ? nullptr : cv.take<int>(h * d.m);
   w.Rs = cv.take<double2>(h * d.b * d.b);
   w.dead = cv.take<uint32_t>(h * 4);
   w.counters = cv.take<int>(8);
@@ -202,15 +206,6 @@ static int to_orth(const RbkWs<T>& w, const RbkDims& d, int cols, cudaStream_t s
   return convert_c32_to_c64((const float2*)w.Wt, d.b, sW, (double2*)w.Wl, d.b, sW, d.n1, cols, d.h, s);
 }
 
-// to FP64 (no-op when T is double)
-template <typename T>
-static int to64(const cx_t<T>* src, long lds, long ss, double2* dst, long ldd, long sd, int rows, int cols, int batch,
-                cudaStream_t s) {
-  if (std::is_same<T, double>::value) return TSVD_OK;
-  TSVD_STAGE("convert", s);
-  return convert_c32_to_c64((const float2*)src, lds, ss, dst, ldd, sd, rows, cols, batch, s);
-}
-
 template <typename T, typename L>
 static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* Omega, T* U, T* S, T* V,
                    double* sig, void* ws, cudaStream_t s, tsvd_info* info) {
@@ -268,12 +263,16 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
                     w.splitk, w.splitk_elems * 2, s));
   }
 
-  // G = C C^H (FP64) and its top-R eigenpairs
-  TSVD_TRY(to64<T>(w.CHt, m, sCH, w.CH64, m, sCH, n2, m, h, s));
+  // G = C C^H in FP64 (FP64 path) or exactly in integers from the FP32 C^H, and its top-R eigenpairs
   {
   TSVD_STAGE("gram_c", s);
-  TSVD_TRY(cgemm_herm<double2>(gemm('H', 'N', m, m, n2, 1.0, w.CH64, m, sCH, w.CH64, m, sCH, 0.0, w.G, m, (long)m * m, h),
-                          w.splitk, w.splitk_elems, s));
+  if constexpr (std::is_same<T, double>::value) {
+    TSVD_TRY(cgemm_herm<double2>(gemm('H', 'N', m, m, n2, 1.0, w.CH64, m, sCH, w.CH64, m, sCH, 0.0, w.G, m,
+                                      (long)m * m, h),
+                                 w.splitk, w.splitk_elems, s));
+  } else {
+    TSVD_TRY(gram_int_fp32((const float2*)w.CHt, m, sCH, n2, m, h, w.Qint, w.colexp, w.G, m, (long)m * m, s));
+  }
   }
   TSVD_TRY(herm_eig_topR<C>(w.G, m, (long)m * m, m, R, h, w.lam, w.Uct, R, (long)m * R, w.eig, w.counters, s));
   {
