@@ -540,6 +540,431 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_smem(const double2* __r
   }
 }
 
+// ---------------------------------------------------------------------------
+// Double-float variant of k_hetrd_smem for the FP32 path.  GB300 issues FP32
+// at 64x its FP64 rate, so the same reduction is carried in unevaluated pairs
+// (hi, lo) of floats (about 48 significant bits) built from the error-free
+// transformations TwoSum (Knuth) and TwoProduct via FMA (Dekker): a
+// multiply-add costs about 15 FP32 instructions instead of one DFMA at 1/64
+// of the rate.  G is first scaled by a power of two so its entries stay far
+// inside the FP32 exponent range; the per-step scalars (norm, alpha, the
+// scale of v, v^H p) are formed in FP64 by one thread.  The rounding level
+// (about 2^-47 ||G|| per operation) is far below what the FP32 path's
+// accuracy needs; the FP64 path keeps k_hetrd_smem.
+// ---------------------------------------------------------------------------
+struct dfl {
+  float hi, lo;
+};
+struct cdf {  // complex double-float, 16 bytes like double2
+  float rh, rl, ih, il;
+};
+
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return dfl{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfl df_fast_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+  const float s = a + b;
+  return dfl{s, b - (s - a)};
+}
+// a + x y
+__device__ __forceinline__ dfl df_fma(dfl a, dfl x, dfl y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e));
+  const dfl s = df_two_sum(a.hi, p);
+  return df_fast_two_sum(s.hi, s.lo + (a.lo + e));
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const dfl s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return dfl{-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl df_from(double x) {
+  const float h = (float)x;
+  return dfl{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dfl cre(cdf a) { return dfl{a.rh, a.rl}; }
+__device__ __forceinline__ dfl cim(cdf a) { return dfl{a.ih, a.il}; }
+__device__ __forceinline__ cdf cdf_make(dfl r, dfl i) { return cdf{r.hi, r.lo, i.hi, i.lo}; }
+__device__ __forceinline__ cdf cdf_from(double2 x) { return cdf_make(df_from(x.x), df_from(x.y)); }
+__device__ __forceinline__ double2 cdf_to(cdf a) { return make_double2(df_to(cre(a)), df_to(cim(a))); }
+__device__ __forceinline__ cdf cdf_zero() { return cdf{0.f, 0.f, 0.f, 0.f}; }
+__device__ __forceinline__ cdf cdf_add(cdf a, cdf b) { return cdf_make(df_add(cre(a), cre(b)), df_add(cim(a), cim(b))); }
+// acc += a b
+__device__ __forceinline__ void cdf_fma(cdf& acc, cdf a, cdf b) {
+  dfl r = cre(acc), i = cim(acc);
+  r = df_fma(r, cre(a), cre(b));
+  r = df_fma(r, df_neg(cim(a)), cim(b));
+  i = df_fma(i, cre(a), cim(b));
+  i = df_fma(i, cim(a), cre(b));
+  acc = cdf_make(r, i);
+}
+// acc += conj(a) b
+__device__ __forceinline__ void cdf_fmac(cdf& acc, cdf a, cdf b) {
+  dfl r = cre(acc), i = cim(acc);
+  r = df_fma(r, cre(a), cre(b));
+  r = df_fma(r, cim(a), cim(b));
+  i = df_fma(i, cre(a), cim(b));
+  i = df_fma(i, df_neg(cim(a)), cre(b));
+  acc = cdf_make(r, i);
+}
+// a - vg conj(wk) - wg conj(vk)
+__device__ __forceinline__ cdf cdf_lag(cdf a, cdf vg, cdf wg, cdf vk, cdf wk) {
+  dfl r = cre(a), i = cim(a);
+  r = df_fma(r, df_neg(cre(vg)), cre(wk));
+  r = df_fma(r, df_neg(cim(vg)), cim(wk));
+  r = df_fma(r, df_neg(cre(wg)), cre(vk));
+  r = df_fma(r, df_neg(cim(wg)), cim(vk));
+  i = df_fma(i, df_neg(cim(vg)), cre(wk));
+  i = df_fma(i, cre(vg), cim(wk));
+  i = df_fma(i, df_neg(cim(wg)), cre(vk));
+  i = df_fma(i, cre(wg), cim(vk));
+  return cdf_make(r, i);
+}
+// x * s for a real double-float s
+__device__ __forceinline__ cdf cdf_scale(cdf x, dfl s) {
+  const dfl z{0.f, 0.f};
+  return cdf_make(df_fma(z, cre(x), s), df_fma(z, cim(x), s));
+}
+__device__ __forceinline__ dfl df_shfl_xor(dfl a, int o) {
+  return dfl{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+// block-wide sum in a fixed order, result on every thread (two barriers)
+__device__ __forceinline__ dfl df_block_sum(dfl v, dfl* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  dfl t = (lane < nw) ? red[lane] : dfl{0.f, 0.f};
+  for (int o = 16; o > 0; o >>= 1) t = df_add(t, df_shfl_xor(t, o));
+  return t;
+}
+
+template <int CL>
+__global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_df(const double2* __restrict__ G, long ldg, long sG, int m,
+                                                            int s_elems, EigScratch e) {
+  extern __shared__ __align__(16) cdf dsm[];
+  cdf* S = dsm;
+  cdf* bufV = S + s_elems;
+  cdf* bufW = bufV + 2 * m;
+  cdf* pv = bufW + 2 * m;
+  cdf* slotF = pv + m;
+  cdf* slotL = slotF + HS_THREADS;
+  int* CP = (int*)(slotL + HS_THREADS);
+  __shared__ dfl red[HS_THREADS / 32];
+  __shared__ double s_scal[4];  // alpha (re, im), vinv, K
+  __shared__ int s_exp;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int c = (CL > 1) ? (int)cluster.block_rank() : 0;
+  const int b = blockIdx.x / CL;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = HS_THREADS / 32;
+  G += (long)b * sG;
+  double2* Hv = e.Hv + (long)b * m * m;
+  const int nq = hs_own_rows(m, c, CL);
+
+  // power-of-two scale from the largest diagonal entry (identical in every CTA)
+  {
+    double mx = 0;
+    for (int i = tid; i < m; i += HS_THREADS) mx = fmax(mx, fabs(__ldcg(G + (long)i * ldg + i).x));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ double wmx[NW];
+    if (lane == 0) wmx[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0;
+      for (int w = 0; w < NW; ++w) t = fmax(t, wmx[w]);
+      int ex = 0;
+      if (t > 0 && isfinite(t)) frexp(t, &ex);
+      s_exp = ex;
+    }
+    __syncthreads();
+  }
+  const int ex = s_exp;
+  for (int q = warp; q < nq; q += NW) {
+    const int g = c + CL * q;
+    const double2* src = G + (long)g * ldg;
+    cdf* dst = S + hs_rowbase(q, c, CL);
+    for (int k = lane; k <= g; k += 32) {
+      const double2 x = __ldcg(src + k);
+      dst[k] = cdf_from(make_double2(ldexp(x.x, -ex), ldexp(x.y, -ex)));
+    }
+  }
+  if (tid == 0) {
+    int acc = 0;
+    for (int k = 0; k < m; ++k) {
+      CP[k] = acc;
+      acc += max(0, nq - hs_qfirst(k, c, CL));
+    }
+    CP[m] = acc;
+  }
+  for (int i = tid; i < 4 * m; i += HS_THREADS) bufV[i] = cdf_zero();
+  if (CL > 1) cluster.sync();
+  else __syncthreads();
+
+  for (int j = 0; j < m - 1; ++j) {
+    const int cur = j & 1;
+    cdf* v = bufV + cur * m;
+    cdf* w = bufW + cur * m;
+    const cdf* vp = bufV + (cur ^ 1) * m;
+    const cdf* wp = bufW + (cur ^ 1) * m;
+    const bool lag = j > 0;
+    {
+      const cdf vpj = vp[j], wpj = wp[j];
+      for (int q = hs_qfirst(j, c, CL) + tid; q < nq; q += HS_THREADS) {
+        const int g = c + CL * q;
+        cdf a = S[hs_rowbase(q, c, CL) + j];
+        if (lag) a = cdf_lag(a, vp[g], wp[g], vpj, wpj);
+#pragma unroll
+        for (int rr = 0; rr < CL; ++rr) {
+          cdf* dst = (CL > 1) ? cluster.map_shared_rank(v, rr) : v;
+          dst[g] = a;
+        }
+      }
+      if (tid == 0 && (j % CL) == c) {
+        const cdf sj = S[hs_rowbase((j - c) / CL, c, CL) + j];
+        dfl t = cre(sj);
+        t = df_fma(t, df_neg(cre(vpj)), cre(wpj));
+        t = df_fma(t, df_neg(cim(vpj)), cim(wpj));
+        t = df_fma(t, df_neg(cre(vpj)), cre(wpj));
+        t = df_fma(t, df_neg(cim(vpj)), cim(wpj));
+        e.d[(long)b * m + j] = ldexp(df_to(t), ex);
+      }
+    }
+    if (CL > 1) cluster.sync();
+    else __syncthreads();
+    const int n = m - j - 1;
+    {
+      dfl part{0.f, 0.f};
+      for (int i = tid; i < n; i += HS_THREADS) {
+        const cdf x = v[j + 1 + i];
+        part = df_fma(part, cre(x), cre(x));
+        part = df_fma(part, cim(x), cim(x));
+      }
+      for (int i = tid; i < n; i += HS_THREADS) pv[j + 1 + i] = cdf_zero();
+      const dfl nrm2d = df_block_sum(part, red);
+      if (tid == 0) {
+        const double nrm2 = df_to(nrm2d);
+        double2 alpha = make_double2(0, 0);
+        double vinv = 0.0;
+        if (nrm2 > 0.0) {
+          const double2 x0 = cdf_to(v[j + 1]);
+          const double nrm = sqrt(nrm2), ax0 = sqrt(cabs2(x0));
+          const double2 ph = (ax0 > 0) ? cscale(x0, 1.0 / ax0) : make_double2(1, 0);
+          alpha = cscale(ph, -nrm);
+          vinv = 1.0 / sqrt(2.0 * nrm * (nrm + ax0));
+        }
+        s_scal[0] = alpha.x;
+        s_scal[1] = alpha.y;
+        s_scal[2] = vinv;
+        if (c == 0) e.alpha[(long)b * m + j] = make_double2(ldexp(alpha.x, ex), ldexp(alpha.y, ex));
+      }
+      __syncthreads();
+    }
+    {
+      const cdf am = cdf_make(df_from(-s_scal[0]), df_from(-s_scal[1]));
+      const dfl vinv = df_from(s_scal[2]);
+      for (int i = tid; i < n; i += HS_THREADS) {
+        cdf vi = v[j + 1 + i];
+        if (i == 0) vi = cdf_add(vi, am);
+        vi = cdf_scale(vi, vinv);
+        v[j + 1 + i] = vi;
+        if (c == 0) Hv[(long)j * m + j + 1 + i] = cdf_to(vi);
+      }
+    }
+    __syncthreads();
+
+    // row pass (as in k_hetrd_smem)
+    const int q0 = hs_qfirst(j, c, CL);
+    const int nr = max(0, nq - q0);
+    const int g0 = c + CL * q0;
+    const int E1 = nr * (g0 - j) + CL * nr * (nr - 1) / 2;
+    if (E1 > 0) {
+      const int e0 = hs_seg(tid, E1), e1 = hs_seg(tid + 1, E1);
+      if (e0 < e1) {
+        int lo = 0, hi = nr - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (mid * (g0 - j) + CL * mid * (mid - 1) / 2 <= e0) lo = mid;
+          else hi = mid - 1;
+        }
+        int i = lo;
+        const int Pi = i * (g0 - j) + CL * i * (i - 1) / 2;
+        int g = g0 + CL * i;
+        int k = j + 1 + (e0 - Pi);
+        cdf* row = S + hs_rowbase(q0 + i, c, CL);
+        bool whole = (e0 == Pi), first = true;
+        cdf vg = vp[g], wg = wp[g];
+        cdf acc = cdf_zero();
+        for (int el = e0; el < e1; ++el) {
+          cdf a = row[k];
+          if (lag) {
+            a = cdf_lag(a, vg, wg, vp[k], wp[k]);
+            if (k == g) {
+              a.ih = 0.f;
+              a.il = 0.f;
+            }
+            row[k] = a;
+          }
+          cdf_fma(acc, a, v[k]);
+          if (++k > g) {
+            if (whole) pv[g] = acc;
+            else slotF[tid] = acc;
+            first = false;
+            whole = true;
+            acc = cdf_zero();
+            row += g + 1;
+            g += CL;
+            k = j + 1;
+            if (el + 1 < e1) {
+              vg = vp[g];
+              wg = wp[g];
+            }
+          }
+        }
+        if (k != j + 1) {
+          if (first) slotF[tid] = acc;
+          else slotL[tid] = acc;
+        }
+      }
+      __syncthreads();
+      for (int i = tid; i < nr; i += HS_THREADS) {
+        const int Pi = i * (g0 - j) + CL * i * (i - 1) / 2;
+        const int len = g0 + CL * i - j;
+        const int ta = hs_owner(Pi, E1), tb = hs_owner(Pi + len - 1, E1);
+        if (ta == tb) continue;
+        cdf sacc = (hs_seg(ta, E1) == Pi) ? slotF[ta] : slotL[ta];
+        for (int t = ta + 1; t <= tb; ++t)
+          if (hs_seg(t, E1) < hs_seg(t + 1, E1)) sacc = cdf_add(sacc, slotF[t]);
+        pv[g0 + CL * i] = sacc;
+      }
+    }
+    __syncthreads();
+
+    // column pass
+    const int cb = CP[j + 1];
+    const int E2 = CP[m] - cb;
+    if (E2 > 0) {
+      const int e0 = hs_seg(tid, E2), e1 = hs_seg(tid + 1, E2);
+      if (e0 < e1) {
+        int lo = j + 1, hi = m - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (CP[mid] <= cb + e0) lo = mid;
+          else hi = mid - 1;
+        }
+        int k = lo;
+        int o = cb + e0 - CP[k];
+        int cnt = CP[k + 1] - CP[k];
+        int q = hs_qfirst(k, c, CL) + o;
+        int g = c + CL * q, base = hs_rowbase(q, c, CL);
+        bool whole = (o == 0), first = true;
+        cdf acc = cdf_zero();
+        for (int el = e0; el < e1; ++el) {
+          cdf_fmac(acc, S[base + k], v[g]);
+          base += g + 1;
+          g += CL;
+          if (++o == cnt) {
+            if (whole) pv[k] = cdf_add(pv[k], acc);
+            else slotF[tid] = acc;
+            first = false;
+            whole = true;
+            acc = cdf_zero();
+            if (el + 1 < e1) {
+              do {
+                ++k;
+              } while (CP[k + 1] == CP[k]);
+              cnt = CP[k + 1] - CP[k];
+              q = hs_qfirst(k, c, CL);
+              g = c + CL * q;
+              base = hs_rowbase(q, c, CL);
+              o = 0;
+            }
+          }
+        }
+        if (o != cnt && o != 0) {
+          if (first) slotF[tid] = acc;
+          else slotL[tid] = acc;
+        }
+      }
+      __syncthreads();
+      for (int k = j + 1 + tid; k < m; k += HS_THREADS) {
+        const int cnt = CP[k + 1] - CP[k];
+        if (cnt == 0) continue;
+        const int s0 = CP[k] - cb;
+        const int ta = hs_owner(s0, E2), tb = hs_owner(s0 + cnt - 1, E2);
+        if (ta == tb) continue;
+        cdf sacc = (hs_seg(ta, E2) == s0) ? slotF[ta] : slotL[ta];
+        for (int t = ta + 1; t <= tb; ++t)
+          if (hs_seg(t, E2) < hs_seg(t + 1, E2)) sacc = cdf_add(sacc, slotF[t]);
+        pv[k] = cdf_add(pv[k], sacc);
+      }
+    }
+    if (CL > 1) cluster.sync();
+    else __syncthreads();
+
+    // p = 2 sum of the parts; K = Re(v^H p); w = p - K v
+    dfl kp{0.f, 0.f};
+    for (int i = j + 1 + tid; i < m; i += HS_THREADS) {
+      cdf pi = cdf_zero();
+#pragma unroll
+      for (int rr = 0; rr < CL; ++rr) {
+        const cdf* src = (CL > 1) ? cluster.map_shared_rank(pv, rr) : pv;
+        pi = cdf_add(pi, src[i]);
+      }
+      pi = cdf_make(dfl{2.f * pi.rh, 2.f * pi.rl}, dfl{2.f * pi.ih, 2.f * pi.il});
+      w[i] = pi;
+      const cdf vi = v[i];
+      kp = df_fma(kp, cre(vi), cre(pi));
+      kp = df_fma(kp, cim(vi), cim(pi));
+    }
+    const dfl K = df_block_sum(kp, red);
+    const dfl nK = df_neg(K);
+    for (int i = j + 1 + tid; i < m; i += HS_THREADS) {
+      const cdf vi = v[i];
+      cdf wi = w[i];
+      wi = cdf_make(df_fma(cre(wi), cre(vi), nK), df_fma(cim(wi), cim(vi), nK));
+      w[i] = wi;
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && ((m - 1) % CL) == c) {
+    const cdf sl = S[hs_rowbase((m - 1 - c) / CL, c, CL) + m - 1];
+    dfl t = cre(sl);
+    if (m > 1) {
+      const cdf vq = bufV[((m - 2) & 1) * m + m - 1], wq = bufW[((m - 2) & 1) * m + m - 1];
+      t = df_fma(t, df_neg(cre(vq)), cre(wq));
+      t = df_fma(t, df_neg(cim(vq)), cim(wq));
+      t = df_fma(t, df_neg(cre(vq)), cre(wq));
+      t = df_fma(t, df_neg(cim(vq)), cim(wq));
+    }
+    e.d[(long)b * m + m - 1] = ldexp(df_to(t), ex);
+  }
+  __threadfence();
+  if (CL > 1) cluster.sync();
+  else __syncthreads();
+  if (c == 0 && tid == 0) {
+    double2 dl = make_double2(1, 0);
+    e.delta[(long)b * m] = dl;
+    double tn = 0;
+    for (int jj = 0; jj < m - 1; ++jj) {
+      const double2 a = __ldcg(e.alpha + (long)b * m + jj);
+      const double aa = sqrt(cabs2(a));
+      e.f[(long)b * m + jj] = aa;
+      if (aa > 0) dl = cmul(dl, cscale(a, 1.0 / aa));
+      e.delta[(long)b * m + jj + 1] = dl;
+    }
+    for (int jj = 0; jj < m; ++jj) {
+      const double fl = (jj > 0) ? e.f[(long)b * m + jj - 1] : 0.0, fr = (jj < m - 1) ? e.f[(long)b * m + jj] : 0.0;
+      tn = fmax(tn, fabs(__ldcg(e.d + (long)b * m + jj)) + fl + fr);
+    }
+    e.tnorm[b] = tn;
+  }
+}
+
 // Number of eigenvalues below x of the symmetric tridiagonal (d, f) (scaled
 // to norm ~1): sign changes of the Sturm sequence P_0 = 1, P_1 = d_0 - x,
 // P_i = (d_{i-1} - x) P_{i-1} - f_{i-2}^2 P_{i-2}, i.e. negative ratios
@@ -853,11 +1278,12 @@ static int hetrd_smem_cluster(int m, int batch) {
   return 0;
 }
 
-template <int CL>
+template <int CL, bool DF>
 static int launch_hetrd_smem_t(const double2* G, long ldg, long sG, int m, int batch, const EigScratch& e,
                                cudaStream_t s) {
   const size_t smem = hetrd_smem_bytes(m, CL);
-  if (cudaFuncSetAttribute(k_hetrd_smem<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  auto kern = DF ? k_hetrd_df<CL> : k_hetrd_smem<CL>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return TSVD_ERR_CUDA;
   }
@@ -873,7 +1299,7 @@ static int launch_hetrd_smem_t(const double2* G, long ldg, long sG, int m, int b
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, k_hetrd_smem<CL>, G, ldg, sG, m, (int)hetrd_smem_elems(m, CL), e) != cudaSuccess) {
+  if (cudaLaunchKernelEx(&cfg, kern, G, ldg, sG, m, (int)hetrd_smem_elems(m, CL), e) != cudaSuccess) {
     cudaGetLastError();
     return TSVD_ERR_CUDA;
   }
@@ -881,13 +1307,14 @@ static int launch_hetrd_smem_t(const double2* G, long ldg, long sG, int m, int b
   return TSVD_OK;
 }
 
+template <bool DF>
 static int launch_hetrd_smem(int CL, const double2* G, long ldg, long sG, int m, int batch, const EigScratch& e,
                              cudaStream_t s) {
   switch (CL) {
-    case 8: return launch_hetrd_smem_t<8>(G, ldg, sG, m, batch, e, s);
-    case 4: return launch_hetrd_smem_t<4>(G, ldg, sG, m, batch, e, s);
-    case 2: return launch_hetrd_smem_t<2>(G, ldg, sG, m, batch, e, s);
-    default: return launch_hetrd_smem_t<1>(G, ldg, sG, m, batch, e, s);
+    case 8: return launch_hetrd_smem_t<8, DF>(G, ldg, sG, m, batch, e, s);
+    case 4: return launch_hetrd_smem_t<4, DF>(G, ldg, sG, m, batch, e, s);
+    case 2: return launch_hetrd_smem_t<2, DF>(G, ldg, sG, m, batch, e, s);
+    default: return launch_hetrd_smem_t<1, DF>(G, ldg, sG, m, batch, e, s);
   }
 }
 
@@ -900,7 +1327,9 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
   EigScratch e = carve_eig(scratch, m, R, batch, nullptr);
   if (int CLs = hetrd_smem_cluster(m, batch); CLs > 0) {
     TSVD_STAGE("eig_hetrd", s);
-    TSVD_TRY(launch_hetrd_smem(CLs, G, ldg, sG, m, batch, e, s));
+    // FP32 path (C = float2): double-float reduction; FP64 path: FP64
+    constexpr bool kDoubleFloat = std::is_same<C, float2>::value;
+    TSVD_TRY((launch_hetrd_smem<kDoubleFloat>(CLs, G, ldg, sG, m, batch, e, s)));
   } else {
     TSVD_STAGE("eig_hetrd", s);
     const size_t smem = (2 + 16) * (size_t)m * sizeof(double2);  // v, p and 16 warps' partials
