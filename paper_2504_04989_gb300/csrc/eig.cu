@@ -247,20 +247,25 @@ static size_t hetrd_smem_elems(int m, int CL) {
   for (int c = 0; c < CL; ++c) mx = std::max(mx, hs_rowbase(hs_own_rows(m, c, CL), c, CL));
   return (size_t)mx;
 }
-static size_t hetrd_smem_bytes(int m, int CL) {
-  const size_t el = (hetrd_smem_elems(m, CL) + 5 * (size_t)m + 2 * HS_THREADS) * sizeof(double2);
+static size_t hetrd_smem_bytes(int m, int CL, int nt = HS_THREADS) {
+  const size_t vown = (size_t)(m + CL - 1) / CL;  // v at the own rows, compacted
+  const size_t el = (hetrd_smem_elems(m, CL) + 5 * (size_t)m + 2 * (size_t)nt + vown) * sizeof(double2);
   return el + (size_t)(m + 1) * sizeof(int);
 }
 
-// segment start of thread t when E elements are cut into HS_THREADS pieces
-__device__ __forceinline__ int hs_seg(int t, int E) { return (int)(((long)t * E) / HS_THREADS); }
-// the thread whose segment holds element e (the last t with hs_seg(t) <= e)
-__device__ __forceinline__ int hs_owner(int e, int E) {
-  int t = (int)(((long)e * HS_THREADS) / E);
-  while (t + 1 < HS_THREADS && hs_seg(t + 1, E) <= e) ++t;
-  while (t > 0 && hs_seg(t, E) > e) --t;
-  return t;
+// A pass of E elements is cut into contiguous segments of L elements (the
+// last one shorter), one per thread: L is odd and at least 9, so the
+// addresses of neighbouring lanes inside a row differ by an odd multiple of
+// 16 bytes and fall in different shared-memory bank groups.
+template <int NT>
+__device__ __forceinline__ int hs_seglen(int E) {
+  int L = max(9, E / NT) | 1;
+  while ((E + L - 1) / L > NT) L += 2;
+  return L;
 }
+__device__ __forceinline__ int hs_seg(int t, int E, int L) { return min(t * L, E); }
+// the segment holding element e
+__device__ __forceinline__ int hs_owner(int e, int L) { return e / L; }
 
 template <int CL>
 __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_smem(const double2* __restrict__ G, long ldg, long sG, int m,
@@ -272,7 +277,8 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_smem(const double2* __r
   double2* pv = bufW + 2 * m;                  // [m] this CTA's part of p
   double2* slotF = pv + m;                     // [T] partial of a thread's first (split) row / column
   double2* slotL = slotF + HS_THREADS;         // [T] partial of a thread's last (split) row / column
-  int* CP = (int*)(slotL + HS_THREADS);        // [m+1] prefix of the per-column own-row counts
+  double2* vown = slotL + HS_THREADS;          // [ceil(m/CL)] v at the own rows (odd lane stride in the column pass)
+  int* CP = (int*)(vown + (m + CL - 1) / CL);  // [m+1] prefix of the per-column own-row counts
   __shared__ double red[2 * (HS_THREADS / 32)];
   cg::cluster_group cluster = cg::this_cluster();
   const int c = (CL > 1) ? (int)cluster.block_rank() : 0;
@@ -361,11 +367,13 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_smem(const double2* __r
 
     // (2) row pass: lazy update of S and the row part of A v over own rows g > j, columns j+1..g
     const int q0 = hs_qfirst(j, c, CL);
+    for (int q = q0 + tid; q < nq; q += HS_THREADS) vown[q] = v[c + CL * q];
     const int nr = max(0, nq - q0);
     const int g0 = c + CL * q0;
     const int E1 = nr * (g0 - j) + CL * nr * (nr - 1) / 2;  // sum of the row lengths g - j
     if (E1 > 0) {
-      const int e0 = hs_seg(tid, E1), e1 = hs_seg(tid + 1, E1);
+      const int L1 = hs_seglen<HS_THREADS>(E1);
+      const int e0 = hs_seg(tid, E1, L1), e1 = hs_seg(tid + 1, E1, L1);
       if (e0 < e1) {
         // row i holds elements [P(i), P(i+1)), P(i) = i (g0 - j) + CL i (i - 1) / 2
         int lo = 0, hi = nr - 1;
@@ -423,11 +431,11 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_smem(const double2* __r
       for (int i = tid; i < nr; i += HS_THREADS) {
         const int Pi = i * (g0 - j) + CL * i * (i - 1) / 2;
         const int len = g0 + CL * i - j;
-        const int ta = hs_owner(Pi, E1), tb = hs_owner(Pi + len - 1, E1);
+        const int ta = hs_owner(Pi, L1), tb = hs_owner(Pi + len - 1, L1);
         if (ta == tb) continue;
-        double2 s = (hs_seg(ta, E1) == Pi) ? slotF[ta] : slotL[ta];
+        double2 s = (hs_seg(ta, E1, L1) == Pi) ? slotF[ta] : slotL[ta];
         for (int t = ta + 1; t <= tb; ++t)
-          if (hs_seg(t, E1) < hs_seg(t + 1, E1)) s = cadd(s, slotF[t]);
+          if (hs_seg(t, E1, L1) < hs_seg(t + 1, E1, L1)) s = cadd(s, slotF[t]);
         pv[g0 + CL * i] = s;
       }
     }
@@ -437,7 +445,8 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_smem(const double2* __r
     const int cb = CP[j + 1];
     const int E2 = CP[m] - cb;
     if (E2 > 0) {
-      const int e0 = hs_seg(tid, E2), e1 = hs_seg(tid + 1, E2);
+      const int L2 = hs_seglen<HS_THREADS>(E2);
+      const int e0 = hs_seg(tid, E2, L2), e1 = hs_seg(tid + 1, E2, L2);
       if (e0 < e1) {
         int lo = j + 1, hi = m - 1;  // last column k with CP[k] <= cb + e0
         while (lo < hi) {
@@ -453,9 +462,10 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_smem(const double2* __r
         bool whole = (o == 0), first = true;
         double2 acc = make_double2(0, 0);
         for (int el = e0; el < e1; ++el) {
-          cfmac(acc, S[base + k], v[g]);
+          cfmac(acc, S[base + k], vown[q]);
           base += g + 1;  // next own row
           g += CL;
+          ++q;
           if (++o == cnt) {  // column k done
             if (whole) pv[k] = cadd(pv[k], acc);
             else slotF[tid] = acc;
@@ -484,11 +494,11 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_smem(const double2* __r
         const int cnt = CP[k + 1] - CP[k];
         if (cnt == 0) continue;
         const int s0 = CP[k] - cb;
-        const int ta = hs_owner(s0, E2), tb = hs_owner(s0 + cnt - 1, E2);
+        const int ta = hs_owner(s0, L2), tb = hs_owner(s0 + cnt - 1, L2);
         if (ta == tb) continue;
-        double2 s = (hs_seg(ta, E2) == s0) ? slotF[ta] : slotL[ta];
+        double2 s = (hs_seg(ta, E2, L2) == s0) ? slotF[ta] : slotL[ta];
         for (int t = ta + 1; t <= tb; ++t)
-          if (hs_seg(t, E2) < hs_seg(t + 1, E2)) s = cadd(s, slotF[t]);
+          if (hs_seg(t, E2, L2) < hs_seg(t + 1, E2, L2)) s = cadd(s, slotF[t]);
         pv[k] = cadd(pv[k], s);
       }
     }
@@ -580,6 +590,28 @@ __device__ __forceinline__ dfl df_add(dfl a, dfl b) {
   return df_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
 }
 __device__ __forceinline__ dfl df_neg(dfl a) { return dfl{-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return df_fast_two_sum(p, e);
+}
+// square root: correctly rounded FP32 root, then one correction with the
+// exactly computed residual a - x^2 (about 46 correct bits)
+__device__ __forceinline__ dfl df_sqrt(dfl a) {
+  if (!(a.hi > 0.f)) return dfl{0.f, 0.f};
+  const float x = sqrtf(a.hi);
+  const float p = x * x, pe = fmaf(x, x, -p);
+  const float r = ((a.hi - p) - pe) + a.lo;
+  return df_fast_two_sum(x, r / (2.f * x));
+}
+// quotient: FP32 quotient, then one correction with the residual a - q b
+__device__ __forceinline__ dfl df_div(dfl a, dfl b) {
+  const float q = a.hi / b.hi;
+  const float p = q * b.hi, pe = fmaf(q, b.hi, -p);
+  const float r = (((a.hi - p) - pe) + a.lo) - q * b.lo;
+  return df_fast_two_sum(q, r / b.hi);
+}
 __device__ __forceinline__ dfl df_from(double x) {
   const float h = (float)x;
   return dfl{h, (float)(x - (double)h)};
@@ -643,8 +675,8 @@ __device__ __forceinline__ dfl df_block_sum(dfl v, dfl* red) {
   return t;
 }
 
-template <int CL>
-__global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_df(const double2* __restrict__ G, long ldg, long sG, int m,
+template <int CL, int NT>
+__global__ void __launch_bounds__(NT, 1) k_hetrd_df(const double2* __restrict__ G, long ldg, long sG, int m,
                                                             int s_elems, EigScratch e) {
   extern __shared__ __align__(16) cdf dsm[];
   cdf* S = dsm;
@@ -652,24 +684,24 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_df(const double2* __res
   cdf* bufW = bufV + 2 * m;
   cdf* pv = bufW + 2 * m;
   cdf* slotF = pv + m;
-  cdf* slotL = slotF + HS_THREADS;
-  int* CP = (int*)(slotL + HS_THREADS);
-  __shared__ dfl red[HS_THREADS / 32];
-  __shared__ double s_scal[4];  // alpha (re, im), vinv, K
+  cdf* slotL = slotF + NT;
+  cdf* vown = slotL + NT;
+  int* CP = (int*)(vown + (m + CL - 1) / CL);
+  __shared__ dfl red[NT / 32];
   __shared__ int s_exp;
   cg::cluster_group cluster = cg::this_cluster();
   const int c = (CL > 1) ? (int)cluster.block_rank() : 0;
   const int b = blockIdx.x / CL;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int NW = HS_THREADS / 32;
+  constexpr int NW = NT / 32;
   G += (long)b * sG;
-  double2* Hv = e.Hv + (long)b * m * m;
+  float2* Hv32 = (float2*)e.Hv + (long)b * m * m;
   const int nq = hs_own_rows(m, c, CL);
 
   // power-of-two scale from the largest diagonal entry (identical in every CTA)
   {
     double mx = 0;
-    for (int i = tid; i < m; i += HS_THREADS) mx = fmax(mx, fabs(__ldcg(G + (long)i * ldg + i).x));
+    for (int i = tid; i < m; i += NT) mx = fmax(mx, fabs(__ldcg(G + (long)i * ldg + i).x));
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     __shared__ double wmx[NW];
     if (lane == 0) wmx[warp] = mx;
@@ -701,7 +733,7 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_df(const double2* __res
     }
     CP[m] = acc;
   }
-  for (int i = tid; i < 4 * m; i += HS_THREADS) bufV[i] = cdf_zero();
+  for (int i = tid; i < 4 * m; i += NT) bufV[i] = cdf_zero();
   if (CL > 1) cluster.sync();
   else __syncthreads();
 
@@ -714,7 +746,7 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_df(const double2* __res
     const bool lag = j > 0;
     {
       const cdf vpj = vp[j], wpj = wp[j];
-      for (int q = hs_qfirst(j, c, CL) + tid; q < nq; q += HS_THREADS) {
+      for (int q = hs_qfirst(j, c, CL) + tid; q < nq; q += NT) {
         const int g = c + CL * q;
         cdf a = S[hs_rowbase(q, c, CL) + j];
         if (lag) a = cdf_lag(a, vp[g], wp[g], vpj, wpj);
@@ -739,51 +771,53 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_df(const double2* __res
     const int n = m - j - 1;
     {
       dfl part{0.f, 0.f};
-      for (int i = tid; i < n; i += HS_THREADS) {
+      for (int i = tid; i < n; i += NT) {
         const cdf x = v[j + 1 + i];
         part = df_fma(part, cre(x), cre(x));
         part = df_fma(part, cim(x), cim(x));
       }
-      for (int i = tid; i < n; i += HS_THREADS) pv[j + 1 + i] = cdf_zero();
+      for (int i = tid; i < n; i += NT) pv[j + 1 + i] = cdf_zero();
       const dfl nrm2d = df_block_sum(part, red);
-      if (tid == 0) {
-        const double nrm2 = df_to(nrm2d);
-        double2 alpha = make_double2(0, 0);
-        double vinv = 0.0;
-        if (nrm2 > 0.0) {
-          const double2 x0 = cdf_to(v[j + 1]);
-          const double nrm = sqrt(nrm2), ax0 = sqrt(cabs2(x0));
-          const double2 ph = (ax0 > 0) ? cscale(x0, 1.0 / ax0) : make_double2(1, 0);
-          alpha = cscale(ph, -nrm);
-          vinv = 1.0 / sqrt(2.0 * nrm * (nrm + ax0));
+      // reflector scalars in double-float on every thread (identical values, no serial section)
+      cdf am = cdf_zero();  // -alpha
+      dfl vinv{0.f, 0.f};
+      if (nrm2d.hi > 0.f) {
+        const cdf x0 = v[j + 1];
+        const dfl nrm = df_sqrt(nrm2d);
+        const dfl ax2 = df_fma(df_fma(dfl{0.f, 0.f}, cre(x0), cre(x0)), cim(x0), cim(x0));
+        const dfl ax0 = df_sqrt(ax2);
+        dfl phr{1.f, 0.f}, phi{0.f, 0.f};
+        if (ax0.hi > 0.f) {
+          phr = df_div(cre(x0), ax0);
+          phi = df_div(cim(x0), ax0);
         }
-        s_scal[0] = alpha.x;
-        s_scal[1] = alpha.y;
-        s_scal[2] = vinv;
-        if (c == 0) e.alpha[(long)b * m + j] = make_double2(ldexp(alpha.x, ex), ldexp(alpha.y, ex));
+        am = cdf_make(df_mul(phr, nrm), df_mul(phi, nrm));
+        const dfl t = df_mul(df_add(nrm, nrm), df_add(nrm, ax0));
+        vinv = df_div(dfl{1.f, 0.f}, df_sqrt(t));
       }
-      __syncthreads();
-    }
-    {
-      const cdf am = cdf_make(df_from(-s_scal[0]), df_from(-s_scal[1]));
-      const dfl vinv = df_from(s_scal[2]);
-      for (int i = tid; i < n; i += HS_THREADS) {
+      if (c == 0 && tid == 0) {
+        const double2 al = cdf_to(am);
+        e.alpha[(long)b * m + j] = make_double2(-ldexp(al.x, ex), -ldexp(al.y, ex));
+      }
+      for (int i = tid; i < n; i += NT) {
         cdf vi = v[j + 1 + i];
         if (i == 0) vi = cdf_add(vi, am);
         vi = cdf_scale(vi, vinv);
         v[j + 1 + i] = vi;
-        if (c == 0) Hv[(long)j * m + j + 1 + i] = cdf_to(vi);
+        if (c == 0) Hv32[(long)j * m + j + 1 + i] = make_float2(vi.rh, vi.ih);  // read by the FP32 back-transform
       }
     }
     __syncthreads();
 
     // row pass (as in k_hetrd_smem)
     const int q0 = hs_qfirst(j, c, CL);
+    for (int q = q0 + tid; q < nq; q += NT) vown[q] = v[c + CL * q];
     const int nr = max(0, nq - q0);
     const int g0 = c + CL * q0;
     const int E1 = nr * (g0 - j) + CL * nr * (nr - 1) / 2;
     if (E1 > 0) {
-      const int e0 = hs_seg(tid, E1), e1 = hs_seg(tid + 1, E1);
+      const int L1 = hs_seglen<NT>(E1);
+      const int e0 = hs_seg(tid, E1, L1), e1 = hs_seg(tid + 1, E1, L1);
       if (e0 < e1) {
         int lo = 0, hi = nr - 1;
         while (lo < hi) {
@@ -831,14 +865,14 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_df(const double2* __res
         }
       }
       __syncthreads();
-      for (int i = tid; i < nr; i += HS_THREADS) {
+      for (int i = tid; i < nr; i += NT) {
         const int Pi = i * (g0 - j) + CL * i * (i - 1) / 2;
         const int len = g0 + CL * i - j;
-        const int ta = hs_owner(Pi, E1), tb = hs_owner(Pi + len - 1, E1);
+        const int ta = hs_owner(Pi, L1), tb = hs_owner(Pi + len - 1, L1);
         if (ta == tb) continue;
-        cdf sacc = (hs_seg(ta, E1) == Pi) ? slotF[ta] : slotL[ta];
+        cdf sacc = (hs_seg(ta, E1, L1) == Pi) ? slotF[ta] : slotL[ta];
         for (int t = ta + 1; t <= tb; ++t)
-          if (hs_seg(t, E1) < hs_seg(t + 1, E1)) sacc = cdf_add(sacc, slotF[t]);
+          if (hs_seg(t, E1, L1) < hs_seg(t + 1, E1, L1)) sacc = cdf_add(sacc, slotF[t]);
         pv[g0 + CL * i] = sacc;
       }
     }
@@ -848,7 +882,8 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_df(const double2* __res
     const int cb = CP[j + 1];
     const int E2 = CP[m] - cb;
     if (E2 > 0) {
-      const int e0 = hs_seg(tid, E2), e1 = hs_seg(tid + 1, E2);
+      const int L2 = hs_seglen<NT>(E2);
+      const int e0 = hs_seg(tid, E2, L2), e1 = hs_seg(tid + 1, E2, L2);
       if (e0 < e1) {
         int lo = j + 1, hi = m - 1;
         while (lo < hi) {
@@ -864,9 +899,10 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_df(const double2* __res
         bool whole = (o == 0), first = true;
         cdf acc = cdf_zero();
         for (int el = e0; el < e1; ++el) {
-          cdf_fmac(acc, S[base + k], v[g]);
+          cdf_fmac(acc, S[base + k], vown[q]);
           base += g + 1;
           g += CL;
+          ++q;
           if (++o == cnt) {
             if (whole) pv[k] = cdf_add(pv[k], acc);
             else slotF[tid] = acc;
@@ -891,15 +927,15 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_df(const double2* __res
         }
       }
       __syncthreads();
-      for (int k = j + 1 + tid; k < m; k += HS_THREADS) {
+      for (int k = j + 1 + tid; k < m; k += NT) {
         const int cnt = CP[k + 1] - CP[k];
         if (cnt == 0) continue;
         const int s0 = CP[k] - cb;
-        const int ta = hs_owner(s0, E2), tb = hs_owner(s0 + cnt - 1, E2);
+        const int ta = hs_owner(s0, L2), tb = hs_owner(s0 + cnt - 1, L2);
         if (ta == tb) continue;
-        cdf sacc = (hs_seg(ta, E2) == s0) ? slotF[ta] : slotL[ta];
+        cdf sacc = (hs_seg(ta, E2, L2) == s0) ? slotF[ta] : slotL[ta];
         for (int t = ta + 1; t <= tb; ++t)
-          if (hs_seg(t, E2) < hs_seg(t + 1, E2)) sacc = cdf_add(sacc, slotF[t]);
+          if (hs_seg(t, E2, L2) < hs_seg(t + 1, E2, L2)) sacc = cdf_add(sacc, slotF[t]);
         pv[k] = cdf_add(pv[k], sacc);
       }
     }
@@ -908,7 +944,7 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_df(const double2* __res
 
     // p = 2 sum of the parts; K = Re(v^H p); w = p - K v
     dfl kp{0.f, 0.f};
-    for (int i = j + 1 + tid; i < m; i += HS_THREADS) {
+    for (int i = j + 1 + tid; i < m; i += NT) {
       cdf pi = cdf_zero();
 #pragma unroll
       for (int rr = 0; rr < CL; ++rr) {
@@ -923,7 +959,7 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_df(const double2* __res
     }
     const dfl K = df_block_sum(kp, red);
     const dfl nK = df_neg(K);
-    for (int i = j + 1 + tid; i < m; i += HS_THREADS) {
+    for (int i = j + 1 + tid; i < m; i += NT) {
       const cdf vi = v[i];
       cdf wi = w[i];
       wi = cdf_make(df_fma(cre(wi), cre(vi), nK), df_fma(cim(wi), cim(vi), nK));
@@ -1219,7 +1255,7 @@ __global__ void __launch_bounds__(256) k_cluster_orth(int m, int R, EigScratch e
 constexpr int BT_WARPS = 8;
 template <typename C>
 __global__ void __launch_bounds__(BT_WARPS * 32) k_backtransform(int m, int R, EigScratch e, C* __restrict__ U,
-                                                                 long ldu, long sU) {
+                                                                 long ldu, long sU, int hv32) {
   using Rt = decltype(C().x);
   extern __shared__ __align__(16) unsigned char bts[];
   const int b = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1229,16 +1265,18 @@ __global__ void __launch_bounds__(BT_WARPS * 32) k_backtransform(int m, int R, E
   const double* z = e.Z + ((long)b * R + r) * m;
   const double2* dl = e.delta + (long)b * m;
   const double2* Hv = e.Hv + (long)b * m * m;
+  const float2* Hf = (const float2*)e.Hv + (long)b * m * m;  // FP32 vectors of the double-float reduction
   for (int i = lane; i < m; i += 32) u[i] = from_c64<C>(cscale(dl[i], z[i]));
   __syncwarp();
   for (int j = m - 2; j >= 0; --j) {
     const int n = m - j - 1;
     const double2* v = Hv + (long)j * m + j + 1;
+    const float2* vf = Hf + (long)j * m + j + 1;
     C acc;
     acc.x = Rt(0);
     acc.y = Rt(0);
     for (int i = lane; i < n; i += 32) {
-      const C vi = from_c64<C>(v[i]), ui = u[j + 1 + i];
+      const C vi = hv32 ? C{Rt(vf[i].x), Rt(vf[i].y)} : from_c64<C>(v[i]), ui = u[j + 1 + i];
       acc.x = fma(vi.x, ui.x, acc.x);  // acc += conj(v_i) u_i
       acc.x = fma(vi.y, ui.y, acc.x);
       acc.y = fma(vi.x, ui.y, acc.y);
@@ -1247,7 +1285,10 @@ __global__ void __launch_bounds__(BT_WARPS * 32) k_backtransform(int m, int R, E
     acc.x = warp_sum(acc.x);
     acc.y = warp_sum(acc.y);
     const C s2 = cscale(acc, Rt(2));
-    for (int i = lane; i < n; i += 32) u[j + 1 + i] = csub(u[j + 1 + i], cmul(from_c64<C>(v[i]), s2));
+    for (int i = lane; i < n; i += 32) {
+      const C vi = hv32 ? C{Rt(vf[i].x), Rt(vf[i].y)} : from_c64<C>(v[i]);
+      u[j + 1 + i] = csub(u[j + 1 + i], cmul(vi, s2));
+    }
     __syncwarp();
   }
   C* Ub = U + (long)b * sU;
@@ -1267,13 +1308,13 @@ static int device_attr(cudaDeviceAttr a, int fallback) {
 // rows do not fit: the largest CL in {8,4,2,1} with batch * CL CTAs resident
 // at once (one per SM), at least 48 rows per CTA (else the per-step barriers
 // dominate) and the packed rows within the opt-in shared memory.
-static int hetrd_smem_cluster(int m, int batch) {
+static int hetrd_smem_cluster(int m, int batch, int nt) {
   if (m < 2) return 0;
   const int sms = device_attr(cudaDevAttrMultiProcessorCount, 148);
   const size_t smax = (size_t)device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin, 232448) - 256;
   for (int CL = 8; CL >= 1; CL >>= 1) {
     if (CL > 1 && ((long)batch * CL > sms || m / CL < 48)) continue;
-    if (hetrd_smem_bytes(m, CL) <= smax) return CL;
+    if (hetrd_smem_bytes(m, CL, nt) <= smax) return CL;
   }
   return 0;
 }
@@ -1281,15 +1322,16 @@ static int hetrd_smem_cluster(int m, int batch) {
 template <int CL, bool DF>
 static int launch_hetrd_smem_t(const double2* G, long ldg, long sG, int m, int batch, const EigScratch& e,
                                cudaStream_t s) {
-  const size_t smem = hetrd_smem_bytes(m, CL);
-  auto kern = DF ? k_hetrd_df<CL> : k_hetrd_smem<CL>;
+  constexpr int NT = DF ? 2 * HS_THREADS : HS_THREADS;
+  const size_t smem = hetrd_smem_bytes(m, CL, NT);
+  auto kern = DF ? k_hetrd_df<CL, NT> : k_hetrd_smem<CL>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return TSVD_ERR_CUDA;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(batch * CL);
-  cfg.blockDim = dim3(HS_THREADS);
+  cfg.blockDim = dim3(NT);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -1325,10 +1367,12 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
   if (m <= 0 || R <= 0 || batch <= 0) return TSVD_OK;
   if (R > m || R > 128 || m > 768) return TSVD_ERR_UNSUPPORTED;  // shared memory of k_hetrd
   EigScratch e = carve_eig(scratch, m, R, batch, nullptr);
-  if (int CLs = hetrd_smem_cluster(m, batch); CLs > 0) {
+  // FP32 path (C = float2): double-float reduction (twice the threads); FP64 path: FP64
+  constexpr bool kDoubleFloat = std::is_same<C, float2>::value;
+  const int CLs = hetrd_smem_cluster(m, batch, kDoubleFloat ? 2 * HS_THREADS : HS_THREADS);
+  const int hv32 = (kDoubleFloat && CLs > 0) ? 1 : 0;  // Householder vectors stored as float2
+  if (CLs > 0) {
     TSVD_STAGE("eig_hetrd", s);
-    // FP32 path (C = float2): double-float reduction; FP64 path: FP64
-    constexpr bool kDoubleFloat = std::is_same<C, float2>::value;
     TSVD_TRY((launch_hetrd_smem<kDoubleFloat>(CLs, G, ldg, sG, m, batch, e, s)));
   } else {
     TSVD_STAGE("eig_hetrd", s);
@@ -1377,7 +1421,7 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
   const size_t smem_bt = (size_t)BT_WARPS * m * sizeof(C);
   if (smem_bt > 48 * 1024)
     cudaFuncSetAttribute(k_backtransform<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bt);
-  k_backtransform<C><<<dim3(cdiv(R, BT_WARPS), batch), BT_WARPS * 32, smem_bt, s>>>(m, R, e, U, ldu, sU);
+  k_backtransform<C><<<dim3(cdiv(R, BT_WARPS), batch), BT_WARPS * 32, smem_bt, s>>>(m, R, e, U, ldu, sU, hv32);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }
