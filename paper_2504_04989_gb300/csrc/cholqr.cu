@@ -3,9 +3,10 @@
 // shifted), the right triangular solve W <- W R^{-1}, and the replacement of
 // numerically dependent columns by fresh orthonormal directions.
 //
-// The Gram matrix and the triangular solve run in the precision of the basis
-// (FP64, or FP32 on the FP32 / mixed paths); the small Cholesky itself always
-// runs in FP64.
+// The Gram matrix, its Cholesky factorisation and the triangular solve all run
+// in the precision of the basis (FP64, or FP32 on the FP32 / mixed paths), as
+// in the analysis of shifted CholeskyQR (Fukaya et al.), which takes every step
+// in the working precision.
 #include <type_traits>
 
 #include "common.cuh"
@@ -17,75 +18,84 @@ __device__ __forceinline__ int pidx(int i, int j, int n) { return i * n - (i * (
 
 // ---------------------------------------------------------------------------
 // Cholesky (upper, right-looking) R^H R = G + s I of one nb x nb Gram matrix
-// per CTA, in FP64 from a Gram of either precision.  s = shift_rel * trace(G).
+// per CTA, in the Gram's own precision.  s = shift_rel * trace(G).
 // Pivot test: shifted pass -> dead iff d_j <= 0; plain pass -> dead iff
 // d_j <= dead_rel * G_jj.  Dead columns get R_jj = 1 and R_jk = 0.
+// One barrier per column: the scaling of row j is folded into the trailing
+// update S(i,k) -= conj(S(j,i)) S(j,k) / d_j, and row j is scaled by
+// 1/sqrt(d_j) at the end.
 // ---------------------------------------------------------------------------
 template <typename GC>
 __global__ void __launch_bounds__(256) k_chol_upper(const GC* __restrict__ G, long ldg, long sG,
                                                     double2* __restrict__ Rm, long ldr, long sR, int nb,
                                                     double shift_rel, double dead_rel,
                                                     uint32_t* __restrict__ dead_out) {
-  extern __shared__ __align__(16) double2 S[];  // packed upper triangle
-  __shared__ double dg[128];
+  using Rt = decltype(GC().x);
+  extern __shared__ __align__(16) unsigned char chsm[];
+  GC* S = (GC*)chsm;          // packed upper triangle
+  __shared__ Rt dg[128];      // diagonal of G (pivot test of the plain passes)
+  __shared__ Rt dj[128];      // pivots d_j (0 for a dead column)
   __shared__ double red[16];
-  __shared__ uint32_t dmask[4];
-  __shared__ double rjj;
-  __shared__ int isdead;
   const int b = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   G += (long)b * sG;
   Rm += (long)b * sR;
   for (int e = tid; e < nb * nb; e += blockDim.x) {
     const int i = e / nb, j = e - i * nb;
-    if (j >= i) S[pidx(i, j, nb)] = to_c64(G[(long)i * ldg + j]);
+    if (j >= i) S[pidx(i, j, nb)] = G[(long)i * ldg + j];
   }
-  if (tid < nb) dg[tid] = (double)G[(long)tid * ldg + tid].x;
-  if (tid < 4) dmask[tid] = 0;
+  if (tid < nb) dg[tid] = G[(long)tid * ldg + tid].x;
   __syncthreads();
-  const double trace = block_sum(tid < nb ? dg[tid] : 0.0, red);
-  const double sft = (shift_rel > 0.0) ? shift_rel * trace : 0.0;
+  const double trace = block_sum(tid < nb ? (double)dg[tid] : 0.0, red);
+  const Rt sft = (shift_rel > 0.0) ? (Rt)(shift_rel * trace) : Rt(0);
   if (tid < nb) S[pidx(tid, tid, nb)].x += sft;
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    if (tid == 0) {
-      const double d = S[pidx(j, j, nb)].x;
-      const bool dead = (shift_rel > 0.0) ? !(d > 0.0) : !(d > dead_rel * dg[j]);
-      isdead = dead;
-      rjj = dead ? 1.0 : sqrt(d);
-      if (dead) dmask[j >> 5] |= 1u << (j & 31);
-    }
-    __syncthreads();
-    const double r = rjj;
-    const bool dead = isdead;
-    for (int k = j + 1 + tid; k < nb; k += blockDim.x) {
-      const int p = pidx(j, k, nb);
-      S[p] = dead ? make_double2(0, 0) : cscale(S[p], 1.0 / r);
-    }
-    if (tid == 0) S[pidx(j, j, nb)] = make_double2(r, 0);
-    __syncthreads();
-    // trailing update S(i, k) -= conj(S(j, i)) S(j, k) for j < i <= k, one warp per row i
-    const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    const int offj = pidx(j, j, nb);
-    for (int i = j + 1 + warp; i < nb; i += nwarp) {
-      const double2 a = S[offj + (i - j)];
-      const int offi = pidx(i, i, nb);
-      for (int k = i + lane; k < nb; k += 32) {
-        const double2 c = S[offj + (k - j)];
-        double2 t = S[offi + (k - i)];
-        t.x = fma(-a.x, c.x, t.x);
-        t.x = fma(-a.y, c.y, t.x);
-        t.y = fma(-a.x, c.y, t.y);
-        t.y = fma(a.y, c.x, t.y);
-        S[offi + (k - i)] = t;
+    const Rt d = S[pidx(j, j, nb)].x;
+    const bool dead = (shift_rel > 0.0) ? !(d > Rt(0)) : !(d > (Rt)dead_rel * dg[j]);
+    if (tid == 0) dj[j] = dead ? Rt(0) : d;
+    if (!dead) {
+      const Rt inv = Rt(1) / d;
+      const int offj = pidx(j, j, nb);
+      for (int i = j + 1 + warp; i < nb; i += nwarp) {
+        GC a = S[offj + (i - j)];  // S(j, i); the update uses conj(a) / d
+        a.x *= inv;
+        a.y *= inv;
+        const int offi = pidx(i, i, nb);
+        for (int k = i + lane; k < nb; k += 32) {
+          const GC cjk = S[offj + (k - j)];
+          GC t = S[offi + (k - i)];
+          t.x = fma(-a.x, cjk.x, t.x);
+          t.x = fma(-a.y, cjk.y, t.x);
+          t.y = fma(-a.x, cjk.y, t.y);
+          t.y = fma(a.y, cjk.x, t.y);
+          S[offi + (k - i)] = t;
+        }
       }
     }
     __syncthreads();
   }
   for (int e = tid; e < nb * nb; e += blockDim.x) {
     const int i = e / nb, k = e - i * nb;
-    Rm[(long)i * ldr + k] = (k >= i) ? S[pidx(i, k, nb)] : make_double2(0, 0);
+    double2 r = make_double2(0, 0);
+    const Rt d = dj[i];
+    if (k == i) {
+      r.x = (d > Rt(0)) ? sqrt((double)d) : 1.0;
+    } else if (k > i && d > Rt(0)) {
+      const double sc = 1.0 / sqrt((double)d);
+      const GC v = S[pidx(i, k, nb)];
+      r = make_double2((double)v.x * sc, (double)v.y * sc);
+    }
+    Rm[(long)i * ldr + k] = r;
   }
-  if (tid < 4) dead_out[b * 4 + tid] = dmask[tid];
+  if (tid < 4) {
+    uint32_t msk = 0;
+    for (int q = 0; q < 32; ++q) {
+      const int jj = tid * 32 + q;
+      if (jj < nb && !(dj[jj] > Rt(0))) msk |= 1u << q;
+    }
+    dead_out[b * 4 + tid] = msk;
+  }
 }
 
 template <typename GC>
@@ -93,7 +103,7 @@ int chol_upper(const GC* G, long ldg, long sG, double2* Rm, long ldr, long sR, i
                double dead_rel, uint32_t* dead, cudaStream_t s) {
   if (nb <= 0 || batch <= 0) return TSVD_OK;
   if (nb > 128) return TSVD_ERR_UNSUPPORTED;
-  const size_t smem = (size_t)nb * (nb + 1) / 2 * sizeof(double2);
+  const size_t smem = (size_t)nb * (nb + 1) / 2 * sizeof(GC);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_chol_upper<GC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_chol_upper<GC><<<batch, 256, smem, s>>>(G, ldg, sG, Rm, ldr, sR, nb, shift_rel, dead_rel, dead);
   TSVD_LAUNCHED();
@@ -105,26 +115,28 @@ template int chol_upper<float2>(const float2*, long, long, double2*, long, long,
                                 cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// W <- W R^{-1}: each thread owns one row x of its CTA's tile and solves
-// x R = w column by column in right-looking order (x_j = w_j / R_jj, then
-// w_k -= x_j R_jk for every k > j: independent updates, so the FMA pipe stays
-// busy).  R (packed, in W's precision) and the rows live in shared memory.
+// W <- W R^{-1} by forward substitution x R = w, one warp per TS_ROWS rows of
+// W: lane l keeps columns l, l+32, l+64, l+96 of its rows in registers; for
+// each j the solved x_j is broadcast by a shuffle and every lane updates its
+// columns k > j with R(j, k) (R packed in shared memory, diagonal stored as
+// 1/R_jj, 0 for a dead column).
 // ---------------------------------------------------------------------------
+constexpr int TS_ROWS = 4;
+constexpr int TS_WARPS = 8;
+
 template <typename C>
-__global__ void __launch_bounds__(64) k_trsm_right_upper(C* __restrict__ W, long ldw, long sW,
-                                                               const double2* __restrict__ Rm, long ldr, long sR,
-                                                               int n1, int nb, const uint32_t* __restrict__ dead) {
+__global__ void __launch_bounds__(TS_WARPS * 32) k_trsm_right_upper(C* __restrict__ W, long ldw, long sW,
+                                                                   const double2* __restrict__ Rm, long ldr, long sR,
+                                                                   int n1, int nb, const uint32_t* __restrict__ dead) {
   using R = decltype(C().x);
   extern __shared__ __align__(16) unsigned char smraw[];
-  C* Rp = (C*)smraw;                       // packed upper, nb(nb+1)/2; diagonal holds 1/R_jj
-  C* Ws = Rp + nb * (nb + 1) / 2;          // [rows][nb + 1], rows = blockDim.x
-  const int b = blockIdx.y, tid = threadIdx.x, rows = blockDim.x;
-  const int r0 = blockIdx.x * rows;
+  C* Rp = (C*)smraw;  // packed upper, nb(nb+1)/2
+  const int b = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   W += (long)b * sW;
   Rm += (long)b * sR;
   uint32_t dm[4];
 #pragma unroll
-  for (int w = 0; w < 4; ++w) dm[w] = dead[b * 4 + w];
+  for (int q = 0; q < 4; ++q) dm[q] = dead[b * 4 + q];
   for (int e = tid; e < nb * nb; e += blockDim.x) {
     const int i = e / nb, j = e - i * nb;
     if (j < i) continue;
@@ -140,33 +152,52 @@ __global__ void __launch_bounds__(64) k_trsm_right_upper(C* __restrict__ W, long
     }
     Rp[pidx(i, j, nb)] = out;
   }
-  const int ld = nb + 1;
-  for (int e = tid; e < rows * nb; e += blockDim.x) {
-    const int r = e / nb, j = e - r * nb;
-    C v;
-    v.x = R(0);
-    v.y = R(0);
-    if (r0 + r < n1) v = W[(long)(r0 + r) * ldw + j];
-    Ws[r * ld + j] = v;
-  }
   __syncthreads();
-  C* x = Ws + tid * ld;
-  for (int j = 0; j < nb; ++j) {
-    const C xj = cscale(x[j], Rp[pidx(j, j, nb)].x);  // dead columns: scale 0
-    x[j] = xj;
-    for (int k = j + 1; k < nb; ++k) {
-      const C rjk = Rp[pidx(j, k, nb)];
-      C t = x[k];
-      t.x -= xj.x * rjk.x - xj.y * rjk.y;
-      t.y -= xj.x * rjk.y + xj.y * rjk.x;
-      x[k] = t;
+  const int r0 = (blockIdx.x * TS_WARPS + warp) * TS_ROWS;
+  if (r0 >= n1) return;
+  C x[TS_ROWS][4];
+#pragma unroll
+  for (int r = 0; r < TS_ROWS; ++r)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = lane + 32 * u;
+      x[r][u] = (r0 + r < n1 && k < nb) ? W[(long)(r0 + r) * ldw + k] : C{R(0), R(0)};
+    }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    for (int jj = 0; jj < 32; ++jj) {
+      const int j = 32 * u + jj;
+      if (j >= nb) break;
+      const int offj = pidx(j, j, nb);
+      const R rinv = Rp[offj].x;
+      C xj[TS_ROWS];
+#pragma unroll
+      for (int r = 0; r < TS_ROWS; ++r) {
+        xj[r].x = __shfl_sync(0xffffffffu, x[r][u].x, jj) * rinv;
+        xj[r].y = __shfl_sync(0xffffffffu, x[r][u].y, jj) * rinv;
+        if (lane == jj) x[r][u] = xj[r];
+      }
+#pragma unroll
+      for (int v = u; v < 4; ++v) {
+        const int k = lane + 32 * v;
+        if (k > j && k < nb) {
+          const C rjk = Rp[offj + (k - j)];
+#pragma unroll
+          for (int r = 0; r < TS_ROWS; ++r) {
+            x[r][v].x -= xj[r].x * rjk.x - xj[r].y * rjk.y;
+            x[r][v].y -= xj[r].x * rjk.y + xj[r].y * rjk.x;
+          }
+        }
+      }
     }
   }
-  __syncthreads();
-  for (int e = tid; e < rows * nb; e += blockDim.x) {
-    const int r = e / nb, j = e - r * nb;
-    if (r0 + r < n1) W[(long)(r0 + r) * ldw + j] = Ws[r * ld + j];
-  }
+#pragma unroll
+  for (int r = 0; r < TS_ROWS; ++r)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = lane + 32 * u;
+      if (r0 + r < n1 && k < nb) W[(long)(r0 + r) * ldw + k] = x[r][u];
+    }
 }
 
 template <typename C>
@@ -174,17 +205,15 @@ int trsm_right_upper(C* W, long ldw, long sW, const double2* Rm, long ldr, long 
                      const uint32_t* dead, cudaStream_t s) {
   if (nb <= 0 || n1 <= 0 || batch <= 0) return TSVD_OK;
   if (nb > 128) return TSVD_ERR_UNSUPPORTED;
-  int rows = 64;
-  size_t smem = ((size_t)nb * (nb + 1) / 2 + (size_t)rows * (nb + 1)) * sizeof(C);
-  if (smem > 200 * 1024) {
-    rows = 32;
-    smem = ((size_t)nb * (nb + 1) / 2 + (size_t)rows * (nb + 1)) * sizeof(C);
+  const size_t smem = (size_t)nb * (nb + 1) / 2 * sizeof(C);
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k_trsm_right_upper<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return TSVD_ERR_CUDA;
   }
-  if (smem > 227 * 1024) return TSVD_ERR_UNSUPPORTED;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_trsm_right_upper<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  dim3 grid(cdiv(n1, rows), batch);
-  k_trsm_right_upper<C><<<grid, rows, smem, s>>>(W, ldw, sW, Rm, ldr, sR, n1, nb, dead);
+  dim3 grid(cdiv(n1, TS_ROWS * TS_WARPS), batch);
+  k_trsm_right_upper<C><<<grid, TS_WARPS * 32, smem, s>>>(W, ldw, sW, Rm, ldr, sR, n1, nb, dead);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }
