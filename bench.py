@@ -27,7 +27,17 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(name="image-like 512x512x64 fp32, sigma_i=i^-1.5 full rank, R=50 P=10 q=4",
                 n1=512, n2=512, n3=64, R=50, P=10, q=4)
 METRIC = "rank-R T-SVD approximations/s"
-FP64_PEAK_TFLOPS = 1.20   # FMA-chain probe on this GB300 (nominal 1.25)
+# ALU peaks from unit counts and clocks (GB300: 152 SMs at 2.07 GHz; per SM and
+# clock 2 FP64 FMA lanes, 128 FP32 FMA lanes).
+SMS, CLOCK_GHZ = 152, 2.07
+FP64_PEAK_TFLOPS = SMS * CLOCK_GHZ * 2 * 2 / 1e3            # 1.259
+FP32_ISSUE_TINST = SMS * CLOCK_GHZ * 128 / 1e3               # 40.3 T FP32 instructions/s
+DF_FMA_INSTR = 15                                            # FP32 instructions per double-float multiply-add
+DF_PEAK_TFLOPS = FP32_ISSUE_TINST / DF_FMA_INSTR * 2         # 5.37 (FP64-accuracy flops on the FP32 pipe)
+# DRAM bytes per launch of the dominant kernel from the committed ncu capture of
+# the same kernel and workload (profiles/k_hetrd_df_512x512x64_fp32.md); None
+# once the kernel changes.
+NCU_TRAFFIC = {"eig_hetrd": 24.80e6}
 
 
 def peaks():
@@ -163,6 +173,23 @@ def run_reference(args, d, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x, device=None):
+    """The largest x over all ranks (x itself without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(steps, world, seconds):
+    """Whole-job throughput: every rank runs `steps` units of its own tensor
+    (weak scaling), timed by the slowest rank."""
+    return world * steps / seconds
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -219,12 +246,8 @@ def main():
         barrier()
         launches_timed = api.launch_count() - l0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1000.0
-    if world > 1:
-        t = torch.tensor([total_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * args.steps / total_s
+    total_s = max_over_ranks(sum(step_ms) / 1000.0, dev)
+    value = job_value(args.steps, world, total_s)
 
     # end to end through the public API: pinned host input -> device -> T-SVD -> host outputs
     Xh = torch.from_numpy(X).pin_memory()
@@ -243,12 +266,8 @@ def main():
             dst.copy_(src, non_blocking=True)
         b.record(stream)
     barrier()
-    e2e_s = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1000.0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * args.steps / e2e_s
+    e2e_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev) / 1000.0, dev)
+    e2e_value = job_value(args.steps, world, e2e_s)
 
     # per-stage times (CUDA events recorded by the library on this stream)
     with api.profile() as pr:
@@ -258,18 +277,35 @@ def main():
     stages = {k: v[0] / 3 for k, v in pr.stages.items()}
     launches = {k: v[1] // 3 for k, v in pr.stages.items()}
     dom = max(stages, key=stages.get)
-    work = algorithmic(dom, d, args.precision)
     pk = peaks()
-    if "flops" in work:
-        achieved = work["flops"] / (stages[dom] * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 FMA-chain probe on this GB300 (not in MEASURED_PEAKS.json)"}
-    else:
-        achieved = work.get("bytes", 0) / (stages[dom] * 1e-3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+
+    def roofline_of(stage):
+        work = algorithmic(stage, d, args.precision)
+        t = stages[stage] * 1e-3
+        if "flops" in work:
+            if args.precision == "fp64":
+                peak, src = FP64_PEAK_TFLOPS, "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz"
+            elif stage == "eig_hetrd":
+                peak, src = DF_PEAK_TFLOPS, "derived: FP32 issue rate / 15 instructions per double-float FMA"
+            elif stage == "gram_c":
+                peak, src = 2 * FP32_ISSUE_TINST, "derived: one 32x32->64-bit multiply-add per lane and clock"
+            else:
+                peak, src = 2 * FP32_ISSUE_TINST, "derived: 152 SMs x 128 FP32 FMA/clk x 2.07 GHz"
+            a = work["flops"] / t / 1e12
+            return {"kernel": stage, "bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s",
+                    "frac": a / peak, "traffic": NCU_TRAFFIC.get(stage), "peak_source": src}
+        if "bytes" in work:
+            a = work["bytes"] / t / 1e9
+            return {"kernel": stage, "bound": "hbm", "achieved": a, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": a / pk["hbm_gbs"], "traffic": NCU_TRAFFIC.get(stage),
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+        return None
+
+    roof = roofline_of(dom) or {"kernel": dom, "bound": None}
     roof["stage_ms"] = {k: round(v, 3) for k, v in sorted(stages.items(), key=lambda kv: -kv[1])}
+    roof["stages"] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in r.items()
+                          if kk in ("bound", "achieved", "peak", "unit", "frac")}
+                      for k in stages for r in [roofline_of(k)] if r}
 
     # reconstruction error of this path and of the FP64 path on the same tensor ("equal error")
     def rel_err(U, S, V, Xref):
@@ -325,7 +361,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "T-SVD/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32" else "f64",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64+f64" if args.precision == "fp32" else "f64",
                 "data": "synthetic",
                 "config": {"workload": d["name"], "precision": args.precision, "m_eff": d["m"],
                            "l2": "flushed between steps (256 MB write)", "parallelism": "dp%d" % world},
