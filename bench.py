@@ -333,6 +333,25 @@ def main():
     err_fp64 = rel_err(plan64.U, plan64.S, plan64.V, X64)
     opt = float(np.sqrt(wl.optimal_error2(wl.c2_sigma(d["n1"]), d["R"])) / torch.linalg.vector_norm(X64).item())
 
+    # mixed paths: basis-building products on tcgen05 (TF32 / BF16), the rest as on the FP32 path
+    mixed = {}
+    if args.precision == "fp32":
+        for prec in ("tf32", "bf16"):
+            pl = api.RbkPlan(d["n1"], d["n2"], d["n3"], d["R"], d["P"], d["q"], seed=0, precision=prec, device=dev)
+            pl(Xd)
+            torch.cuda.synchronize(dev)
+            evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+            for a, b in evm:
+                flush.zero_()
+                a.record(stream)
+                pl(Xd)
+                b.record(stream)
+            torch.cuda.synchronize(dev)
+            ms_m = sum(a.elapsed_time(b) for a, b in evm) / len(evm)
+            mixed[prec] = {"ms_per_tsvd": ms_m, "tsvd_per_s": 1000.0 / ms_m,
+                           "rel_error": rel_err(pl.U, pl.S, pl.V, X64)}
+            del pl
+
     # t-product throughput on the paper-shaped products (flops 8 n1 n2 n4 h, whole call incl. FFTs)
     tprod_tflops = {}
     for name, n1, n2, n4, n3 in (("2048x2048x128*2048x120x128", 2048, 2048, 120, 128),
@@ -370,6 +389,7 @@ def main():
                 "paths": {"this": {"precision": args.precision, "ms_per_tsvd": 1000 * total_s / args.steps,
                                    "rel_error": err_path},
                           "fp64": {"ms_per_tsvd": fp64_ms, "tsvd_per_s": 1000.0 / fp64_ms, "rel_error": err_fp64},
+                          **mixed,
                           "speedup_vs_fp64": fp64_ms / (1000 * total_s / args.steps),
                           "eckart_young_optimum_rel_error": opt},
                 "tprod_tflops": tprod_tflops}

@@ -30,6 +30,7 @@ namespace tsvd {
 
 struct RbkDims {
   int n1, n2, n3, h, R, P, q, b, m;
+  int tc;  // basis-building products on tcgen05: 0 none, 1 TF32, 2 BF16
 };
 
 static int rbk_dims(int n1, int n2, int n3, const tsvd_params* p, RbkDims* d) {
@@ -44,6 +45,7 @@ static int rbk_dims(int n1, int n2, int n3, const tsvd_params* p, RbkDims* d) {
   d->P = p->P;
   d->q = p->q;
   d->b = p->R + p->P;
+  d->tc = (p->precision == TSVD_MIXED_TF32) ? 1 : (p->precision == TSVD_MIXED_BF16) ? 2 : 0;
   long m = (long)(p->q + 1) * d->b;
   m = std::min<long>(m, std::min(n1, n2));
   d->m = (int)m;
@@ -78,6 +80,11 @@ struct RbkWs {
   C* Vh;
   C* Sh;
   void* eig;
+  void* Aop;      // tcgen05 operand: X-hat as real rows of 2 n2 (TF32 = FP32 storage, or BF16), padded
+  long lda;
+  void* E;        // expanded real form of the thin right factor (2b x 2 n2 per slice)
+  long lde;
+  int* tc_err;    // set by a tcgen05 pipeline wait that timed out
   double2* splitk;
   size_t splitk_elems;
   size_t bytes;
@@ -115,6 +122,16 @@ static RbkWs<T> carve_rbk(void* base, const RbkDims& d) {
   w.Vh = cv.take<C>(h * d.n2 * d.R);
   w.Sh = cv.take<C>(h * d.R);
   w.eig = cv.take<char>(eig_scratch_bytes(d.m, d.R, d.h));
+  w.Aop = nullptr;
+  w.E = nullptr;
+  w.tc_err = nullptr;
+  w.lda = w.lde = (2L * d.n2 + 7) / 8 * 8;
+  if (d.tc) {
+    const bool copy = d.tc == 2 || (2L * d.n2) % 4 != 0;
+    if (copy) w.Aop = cv.take<float>(h * d.n1 * w.lda);  // large enough for either element type
+    w.E = cv.take<float>(h * 2 * (size_t)d.b * w.lde);
+    w.tc_err = cv.take<int>(4);
+  }
   w.splitk_elems = 8 * h * (size_t)d.m * std::max(d.b, 64);
   w.splitk = cv.take<double2>(w.splitk_elems);
   w.bytes = cv.bytes();
@@ -206,13 +223,34 @@ static int to_orth(const RbkWs<T>& w, const RbkDims& d, int cols, cudaStream_t s
   return convert_c32_to_c64((const float2*)w.Wt, d.b, sW, (double2*)w.Wl, d.b, sW, d.n1, cols, d.h, s);
 }
 
+// W (n1 x nb, leading dim b) = X-hat Y for the thin Y (n2 x nb, leading dim ldy):
+// on tcgen05 in the mixed precisions (X-hat seen as real n1 x 2n2 rows, Y as
+// its expanded real form), else the FP32 / FP64 SIMT GEMM.
+template <typename T>
+static int basis_product(const RbkDims& d, RbkWs<T>& w, const cx_t<T>* Y, long ldy, long sy, int nb, cudaStream_t s) {
+  const int n1 = d.n1, n2 = d.n2, b = d.b, h = d.h;
+  const long sA = (long)n1 * n2, sW = (long)n1 * b;
+  if constexpr (std::is_same<T, float>::value) {
+    if (d.tc) {
+      const bool bf16 = d.tc == 2;
+      TSVD_TRY(expand_thin(Y, ldy, sy, n2, nb, w.E, w.lde, 2L * b * w.lde, h, 0, bf16, s));
+      const void* Aop = w.Aop ? w.Aop : (const void*)w.Ah;
+      const long lda = w.Aop ? w.lda : 2L * n2;
+      return tc_gemm(Aop, lda, (long)n1 * lda, n1, w.E, w.lde, 2L * b * w.lde, 2 * nb, 2 * n2, (float*)w.Wt, 2L * b,
+                     2L * sW, h, bf16, w.tc_err, s);
+    }
+  }
+  return cgemm<cx_t<T>>(gemm('N', 'N', n1, nb, n2, 1.0, w.Ah, n2, sA, Y, ldy, sy, 0.0, w.Wt, b, sW, h), w.splitk,
+                        w.splitk_elems * 2, s);
+}
+
 template <typename T, typename L>
 static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* Omega, T* U, T* S, T* V,
                    double* sig, void* ws, cudaStream_t s, tsvd_info* info) {
   using C = cx_t<T>;
   RbkWs<T> w = carve_rbk<T, L>(ws, d);
   const int n1 = d.n1, n2 = d.n2, n3 = d.n3, h = d.h, b = d.b, m = d.m, R = d.R;
-  const long sA = (long)n1 * n2, sQ = (long)n1 * m, sW = (long)n1 * b, sCH = (long)n2 * m, sO = (long)n2 * b;
+  const long sA = (long)n1 * n2, sQ = (long)n1 * m, sCH = (long)n2 * m, sO = (long)n2 * b;
   if (cudaMemsetAsync(w.counters, 0, 8 * sizeof(int), s) != cudaSuccess) return TSVD_ERR_CUDA;
 
   // test tensor and data in the Fourier domain
@@ -228,12 +266,17 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
     TSVD_TRY(launch_rfft3<T>(A, w.Ah, (long)n1 * n2, n3, s));
   }
 
+  if (d.tc) {  // tensor-core operand of X-hat (BF16, or FP32 rows padded to 16 bytes)
+    TSVD_STAGE("krylov_gemm_tc", s);
+    if (cudaMemsetAsync(w.tc_err, 0, sizeof(int), s) != cudaSuccess) return TSVD_ERR_CUDA;
+    if (w.Aop)
+      TSVD_TRY(copy_rows((const float*)w.Ah, 2L * n2, w.Aop, w.lda, 2 * n2, (long)h * n1, d.tc == 2, s));
+  }
   // block 0: W_0 = A Omega
   const int b0 = std::min(b, m);
   {
-    TSVD_STAGE("krylov_gemm", s);
-    TSVD_TRY(cgemm<C>(gemm('N', 'N', n1, b0, n2, 1.0, w.Ah, n2, sA, w.Omh, b, sO, 0.0, w.Wt, b, sW, h), w.splitk,
-                      w.splitk_elems * 2, s));
+    TSVD_STAGE(d.tc ? "krylov_gemm_tc" : "krylov_gemm", s);
+    TSVD_TRY(basis_product<T>(d, w, w.Omh, b, sO, b0, s));
   }
   TSVD_TRY((to_orth<T, L>(w, d, b0, s)));
   TSVD_TRY((orth_block<T, L>(d, w, 0, b0, 0, p.seed, s)));
@@ -246,9 +289,11 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
     TSVD_TRY(cgemm<C>(gemm('H', 'N', n2, pw, n1, 1.0, w.Ah, n2, sA, w.Qt + (c - pw), m, sQ, 0.0, w.CHt + (c - pw), m,
                            sCH, h),
                       w.splitk, w.splitk_elems * 2, s));
+    }
+    {
     // W_i = A Y_i (leading bi columns)
-    TSVD_TRY(cgemm<C>(gemm('N', 'N', n1, bi, n2, 1.0, w.Ah, n2, sA, w.CHt + (c - pw), m, sCH, 0.0, w.Wt, b, sW, h),
-                      w.splitk, w.splitk_elems * 2, s));
+    TSVD_STAGE(d.tc ? "krylov_gemm_tc" : "krylov_gemm", s);
+    TSVD_TRY(basis_product<T>(d, w, w.CHt + (c - pw), m, sCH, bi, s));
     }
     TSVD_TRY((to_orth<T, L>(w, d, bi, s)));
     TSVD_TRY((orth_block<T, L>(d, w, c, bi, i, p.seed, s)));
@@ -295,10 +340,12 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
   }
 
   if (info) {
-    int host[8];
+    int host[8], tcerr = 0;
     if (cudaMemcpyAsync(host, w.counters, sizeof(host), cudaMemcpyDeviceToHost, s) != cudaSuccess) return TSVD_ERR_CUDA;
+    if (w.tc_err && cudaMemcpyAsync(&tcerr, w.tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return TSVD_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return TSVD_ERR_CUDA;
-    info->status = host[0];
+    info->status = tcerr ? TSVD_ERR_CUDA : host[0];
     info->dead_columns = host[1];
     info->m_eff = m;
     info->reserved = 0;
@@ -320,7 +367,6 @@ extern "C" int tsvd_rbk_workspace_size(int n1, int n2, int n3, const tsvd_params
   if (!bytes) return TSVD_ERR_INVALID_ARG;
   RbkDims d;
   TSVD_TRY(rbk_dims(n1, n2, n3, params, &d));
-  if (params->precision == TSVD_MIXED_TF32 || params->precision == TSVD_MIXED_BF16) return TSVD_ERR_UNSUPPORTED;
   *bytes = rbk_bytes(d, params);
   return TSVD_OK;
 }
@@ -332,7 +378,6 @@ extern "C" int tsvd_rbk(const void* A, int n1, int n2, int n3, const tsvd_params
   TSVD_TRY(rbk_dims(n1, n2, n3, params, &d));
   if (!A || !U || !S || !V || !ws) return TSVD_ERR_INVALID_ARG;
   if (((uintptr_t)ws & 255) != 0) return TSVD_ERR_INVALID_ARG;
-  if (params->precision == TSVD_MIXED_TF32 || params->precision == TSVD_MIXED_BF16) return TSVD_ERR_UNSUPPORTED;
   if (ws_bytes < rbk_bytes(d, params)) return TSVD_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
   if (params->precision == TSVD_FP64)

@@ -11,7 +11,7 @@ torch = pytest.importorskip("torch")
 
 # tolerances (spec targets): sigma 1e-10 relative on the FP64 path,
 # 1e-4 on the FP32 path; reconstruction error within 1e-3 of the oracle's.
-SIG_TOL = {"fp64": 1e-10, "fp32": 1e-4}
+SIG_TOL = {"fp64": 1e-10, "fp32": 1e-4, "tf32": 1e-4, "bf16": 1e-4}
 ERR_TOL = 1e-3
 
 
@@ -85,6 +85,27 @@ def test_c1_fp32(api, orc, fp64_qr):
     X = wl.make_c1(0)
     om = wl.omega(64, 15, 16, seed=0)
     check_against_oracle(api, orc, X, 10, 5, 2, "fp32", omega=om, fp64_qr=fp64_qr)
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+def test_c1_mixed_tensor_core(api, orc, precision):
+    """Basis-building products X-hat Omega and X-hat Y_i on tcgen05 (TF32 /
+    BF16 operands, FP32 accumulation); C = Q^H X-hat and everything after it
+    as on the FP32 path.  Same sigma tolerance as the FP32 path."""
+    X = wl.make_c1(0)
+    om = wl.omega(64, 15, 16, seed=0)
+    with api.profile() as pr:
+        check_against_oracle(api, orc, X, 10, 5, 2, precision, omega=om)
+    assert "krylov_gemm_tc" in pr.stages  # the tcgen05 kernel ran
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+@pytest.mark.parametrize("n1,n2,n3,R,P,q", [(65, 129, 7, 6, 4, 3), (130, 63, 4, 12, 4, 2)])
+def test_mixed_ragged_shapes(api, orc, n1, n2, n3, R, P, q, precision):
+    """Odd n2 (padded tensor-core rows), M and N not multiples of the 128 tiles."""
+    X = wl.low_tubal_rank(n1, n2, n3, np.arange(1, min(n1, n2) + 1) ** -1.0, noise_std=1e-4, seed=n1 + n3)
+    om = wl.omega(n2, R + P, n3, seed=3)
+    check_against_oracle(api, orc, X, R, P, q, precision, omega=om, sig_floor=1e-6)
 
 
 @pytest.mark.parametrize("n1,n2,n3,R,P,q", [
