@@ -190,6 +190,42 @@ def job_value(steps, world, seconds):
     return world * steps / seconds
 
 
+def batched_bench(api, wl, dev, count, lanes, steps, flush, stream):
+    """Uneven batch (n1, n2 ~ U{32..512}, n3 ~ U{8,16,32,64}, tubal rank
+    r ~ U{5..40}, R = r, P = 5, q = 2, FP32): `count` tensors as one
+    tsvd_rbk_batched call over `lanes` streams, captured in a CUDA graph and
+    replayed; also one eager single-stream pass for comparison."""
+    import torch
+    items = wl.make_c4(0, count)
+    shapes = [(it["X"].shape[1], it["X"].shape[2], it["X"].shape[0]) for it in items]
+    Rs = [it["R"] for it in items]
+    xs = [torch.from_numpy(it["X"].astype(np.float32)).to(dev) for it in items]
+    del items
+
+    def timed(plan, k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            plan()
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        return sum(a.elapsed_time(b) for a, b in ev) / k
+
+    eager = api.RbkBatchPlan(shapes, Rs, P=5, q=2, seed=0, precision="fp32", lanes=1, device=dev)
+    eager(xs)
+    ms_eager = timed(eager, 1)
+    del eager
+    plan = api.RbkBatchPlan(shapes, Rs, P=5, q=2, seed=0, precision="fp32", lanes=lanes, device=dev, graph=True)
+    plan(xs)
+    torch.cuda.synchronize(dev)
+    timed(plan, 1)
+    ms = timed(plan, steps)
+    return {"workload": "uneven batch: n1, n2 ~ U{32..512}, n3 ~ U{8,16,32,64}, rank ~ U{5..40}, P=5, q=2, fp32",
+            "tensors": count, "lanes": lanes, "graph": True, "ms_per_batch": ms,
+            "tsvd_per_s": count * 1000.0 / ms, "eager_single_stream_ms": ms_eager}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -198,6 +234,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched-count", type=int, default=64,
+                    help="tensors of the uneven batch timed after the main workload (0: skip)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -377,6 +415,10 @@ def main():
             del A, B
         tprod_tflops[name] = row
 
+    batched = None
+    if args.batched_count > 0 and args.precision == "fp32":
+        batched = batched_bench(api, wl, dev, args.batched_count, 8, 3, flush, stream)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "T-SVD/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
@@ -392,7 +434,7 @@ def main():
                           **mixed,
                           "speedup_vs_fp64": fp64_ms / (1000 * total_s / args.steps),
                           "eckart_young_optimum_rel_error": opt},
-                "tprod_tflops": tprod_tflops}
+                "tprod_tflops": tprod_tflops, "batched": batched}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(X, d)
         print(json.dumps(line), flush=True)

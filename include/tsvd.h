@@ -113,6 +113,46 @@ TSVD_API int tsvd_rbk(const void* A, int n1, int n2, int n3, const tsvd_params* 
              tsvd_info* info);
 
 /*
+ * tsvd_rbk_batched -- Alg. 2 on a batch of independent tensors of different
+ * shapes, ranks and parameters (the slices of every tensor, and the tensors
+ * themselves, are independent problems: the remark opening Sec. 4).
+ *
+ *   descs  host array of `count` descriptors: each names one tsvd_rbk call
+ *          (A, n1, n2, n3, params, Omega, U, S, V, sigma_hat with tsvd_rbk's
+ *          meaning, layouts and limits; device pointers; sigma_hat and Omega
+ *          may be NULL).  The library reads the array during the call only.
+ *   lanes  number of concurrent CUDA streams (1..32; more than `count` is
+ *          clamped).  Tensors are ordered by an estimate of their work
+ *          (largest first) and each goes to the lane with the least work so
+ *          far; a lane runs its tensors in that order.
+ *   ws, ws_bytes  device workspace of tsvd_rbk_batched_workspace_size bytes
+ *          for the same descriptors and lanes (the sum over lanes of the
+ *          largest tsvd_rbk workspace among the lane's tensors).
+ *   stream the caller's stream: the lanes start after the work already
+ *          queued on it and it waits for all of them at the end, so the call
+ *          is asynchronous and can be captured into a CUDA graph (the first
+ *          call on a device creates the lane streams and events, so make one
+ *          call before capturing).
+ * The lane streams are shared by all calls on a device: calls whose work
+ * overlaps in time (different host threads or unordered streams) must not be
+ * issued concurrently.  Results equal those of separate tsvd_rbk calls.
+ */
+typedef struct {
+  const void* A;
+  int n1, n2, n3;
+  tsvd_params params;
+  const void* Omega;
+  void* U;
+  void* S;
+  void* V;
+  double* sigma_hat;
+} tsvd_rbk_desc;
+
+TSVD_API int tsvd_rbk_batched_workspace_size(const tsvd_rbk_desc* descs, int count, int lanes, size_t* bytes);
+TSVD_API int tsvd_rbk_batched(const tsvd_rbk_desc* descs, int count, int lanes, void* ws, size_t ws_bytes,
+                              void* stream);
+
+/*
  * tprod -- t-product C = A * B (Definition of the T-product, Sec. 2, computed
  * by Alg. TP: mode-3 FFT, one complex product per non-redundant Fourier slice,
  * conjugate mirror, inverse FFT).

@@ -27,6 +27,12 @@ class TsvdInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("m_eff", C.c_int), ("dead_columns", C.c_int), ("reserved", C.c_int)]
 
 
+class TsvdRbkDesc(C.Structure):
+    _fields_ = [("A", C.c_void_p), ("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int), ("params", TsvdParams),
+                ("Omega", C.c_void_p), ("U", C.c_void_p), ("S", C.c_void_p), ("V", C.c_void_p),
+                ("sigma_hat", C.c_void_p)]
+
+
 class TsvdStageTime(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("ms", C.c_double), ("count", C.c_int)]
 
@@ -37,6 +43,8 @@ SIGNATURES = {
     "tsvd_rbk_workspace_size": (_i, [_i, _i, _i, C.POINTER(TsvdParams), C.POINTER(_sz)]),
     "tsvd_rbk": (_i, [_vp, _i, _i, _i, C.POINTER(TsvdParams), _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp,
                       C.POINTER(TsvdInfo)]),
+    "tsvd_rbk_batched_workspace_size": (_i, [C.POINTER(TsvdRbkDesc), _i, _i, C.POINTER(_sz)]),
+    "tsvd_rbk_batched": (_i, [C.POINTER(TsvdRbkDesc), _i, _i, _vp, _sz, _vp]),
     "tprod_workspace_size": (_i, [_i, _i, _i, _i, _i, C.POINTER(_sz)]),
     "tprod": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _sz, _vp]),
     "tproj_workspace_size": (_i, [_i, _i, _i, _i, _i, C.POINTER(_sz)]),

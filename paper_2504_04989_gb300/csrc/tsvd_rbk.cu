@@ -23,6 +23,10 @@
 // Gram matrix G and its eigen-solve always run in FP64.
 #include <type_traits>
 
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -388,6 +392,154 @@ extern "C" int tsvd_rbk(const void* A, int n1, int n2, int n3, const tsvd_params
                                   sigma_hat, ws, s, info);
   return rbk_run<float, float>((const float*)A, d, *params, (const float*)Omega, (float*)U, (float*)S, (float*)V,
                                sigma_hat, ws, s, info);
+}
+
+// ---------------------------------------------------------------------------
+// Batched uneven T-SVDs (independent tensors of different shapes and ranks):
+// a host-side scheduler over a pool of CUDA streams.  Tensors are ordered by
+// an estimate of their work (largest first) and each goes to the lane with
+// the least work so far; a lane runs its tensors one after another in its
+// own region of the workspace (the largest its tensors need), lanes run
+// concurrently.  The lanes fork from and join back to the caller's stream
+// through events, so the whole batch can be captured into one CUDA graph.
+// ---------------------------------------------------------------------------
+namespace tsvd {
+
+constexpr int kMaxLanes = 32;
+constexpr int kMaxDevicesBatched = 64;
+
+struct LanePool {
+  cudaStream_t s[kMaxLanes];
+  cudaEvent_t done[kMaxLanes];
+  cudaEvent_t fork;
+  bool ready;
+};
+static LanePool g_lanes[kMaxDevicesBatched];
+static std::mutex g_lanes_mu;
+
+static int lane_pool(LanePool** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesBatched) return TSVD_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_lanes_mu);
+  LanePool& lp = g_lanes[dev];
+  if (!lp.ready) {
+    for (int l = 0; l < kMaxLanes; ++l) {
+      if (cudaStreamCreateWithFlags(&lp.s[l], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&lp.done[l], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return TSVD_ERR_CUDA;
+      }
+    }
+    if (cudaEventCreateWithFlags(&lp.fork, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return TSVD_ERR_CUDA;
+    }
+    lp.ready = true;
+  }
+  *out = &lp;
+  return TSVD_OK;
+}
+
+// work estimate of one T-SVD: Krylov products, orthonormalisation, eigen-solve
+static double rbk_cost(const RbkDims& d) {
+  const double n1 = d.n1, n2 = d.n2, m = d.m;
+  return d.h * (8.0 * n1 * n2 * 2.0 * m + 16.0 * n1 * m * m + (16.0 / 3.0) * m * m * m) + 2e6;
+}
+
+struct BatchPlan {
+  std::vector<int> order;    // tensors, largest first
+  std::vector<int> lane_of;  // lane of each tensor
+  size_t lane_off[kMaxLanes + 1];
+  int lanes;
+};
+
+static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+static int plan_batch(const tsvd_rbk_desc* descs, int count, int lanes, BatchPlan* bp) {
+  if (!descs || count < 0 || lanes < 1) return TSVD_ERR_INVALID_ARG;
+  bp->lanes = std::max(1, std::min({lanes, kMaxLanes, std::max(count, 1)}));
+  std::vector<double> cost(count);
+  std::vector<size_t> bytes(count);
+  for (int i = 0; i < count; ++i) {
+    RbkDims d;
+    TSVD_TRY(rbk_dims(descs[i].n1, descs[i].n2, descs[i].n3, &descs[i].params, &d));
+    cost[i] = rbk_cost(d);
+    bytes[i] = align256(rbk_bytes(d, &descs[i].params));
+  }
+  bp->order.resize(count);
+  for (int i = 0; i < count; ++i) bp->order[i] = i;
+  std::stable_sort(bp->order.begin(), bp->order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  bp->lane_of.assign(count, 0);
+  double load[kMaxLanes] = {0};
+  size_t lane_bytes[kMaxLanes] = {0};
+  for (int i : bp->order) {
+    int best = 0;
+    for (int l = 1; l < bp->lanes; ++l)
+      if (load[l] < load[best]) best = l;
+    bp->lane_of[i] = best;
+    load[best] += cost[i];
+    lane_bytes[best] = std::max(lane_bytes[best], bytes[i]);
+  }
+  bp->lane_off[0] = 0;
+  for (int l = 0; l < bp->lanes; ++l) bp->lane_off[l + 1] = bp->lane_off[l] + lane_bytes[l];
+  return TSVD_OK;
+}
+
+static int rbk_one(const tsvd_rbk_desc& t, void* ws, cudaStream_t s) {
+  RbkDims d;
+  TSVD_TRY(rbk_dims(t.n1, t.n2, t.n3, &t.params, &d));
+  if (!t.A || !t.U || !t.S || !t.V) return TSVD_ERR_INVALID_ARG;
+  const tsvd_params& p = t.params;
+  if (p.precision == TSVD_FP64)
+    return rbk_run<double, double>((const double*)t.A, d, p, (const double*)t.Omega, (double*)t.U, (double*)t.S,
+                                   (double*)t.V, t.sigma_hat, ws, s, nullptr);
+  if (p.flags & TSVD_FLAG_FP64_QR)
+    return rbk_run<float, double>((const float*)t.A, d, p, (const float*)t.Omega, (float*)t.U, (float*)t.S,
+                                  (float*)t.V, t.sigma_hat, ws, s, nullptr);
+  return rbk_run<float, float>((const float*)t.A, d, p, (const float*)t.Omega, (float*)t.U, (float*)t.S, (float*)t.V,
+                               t.sigma_hat, ws, s, nullptr);
+}
+
+}  // namespace tsvd
+
+extern "C" int tsvd_rbk_batched_workspace_size(const tsvd_rbk_desc* descs, int count, int lanes, size_t* bytes) {
+  if (!bytes) return TSVD_ERR_INVALID_ARG;
+  BatchPlan bp;
+  TSVD_TRY(plan_batch(descs, count, lanes, &bp));
+  *bytes = bp.lane_off[bp.lanes];
+  return TSVD_OK;
+}
+
+extern "C" int tsvd_rbk_batched(const tsvd_rbk_desc* descs, int count, int lanes, void* ws, size_t ws_bytes,
+                                void* stream) {
+  BatchPlan bp;
+  TSVD_TRY(plan_batch(descs, count, lanes, &bp));
+  if (count == 0) return TSVD_OK;
+  if (!ws || ((uintptr_t)ws & 255) != 0) return TSVD_ERR_INVALID_ARG;
+  if (ws_bytes < bp.lane_off[bp.lanes]) return TSVD_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = (char*)ws;
+  if (bp.lanes == 1) {
+    for (int i : bp.order) TSVD_TRY(rbk_one(descs[i], base, s));
+    return TSVD_OK;
+  }
+  LanePool* lp = nullptr;
+  TSVD_TRY(lane_pool(&lp));
+  if (cudaEventRecord(lp->fork, s) != cudaSuccess) return TSVD_ERR_CUDA;
+  for (int l = 0; l < bp.lanes; ++l)
+    if (cudaStreamWaitEvent(lp->s[l], lp->fork, 0) != cudaSuccess) return TSVD_ERR_CUDA;
+  int rc = TSVD_OK;
+  for (int i : bp.order) {
+    const int l = bp.lane_of[i];
+    rc = rbk_one(descs[i], base + bp.lane_off[l], lp->s[l]);
+    if (rc != TSVD_OK) break;
+  }
+  // join every lane back into the caller's stream, also after an error
+  for (int l = 0; l < bp.lanes; ++l) {
+    if (cudaEventRecord(lp->done[l], lp->s[l]) != cudaSuccess || cudaStreamWaitEvent(s, lp->done[l], 0) != cudaSuccess)
+      rc = (rc == TSVD_OK) ? TSVD_ERR_CUDA : rc;
+  }
+  return rc;
 }
 
 extern "C" const char* tsvd_strerror(int code) {
