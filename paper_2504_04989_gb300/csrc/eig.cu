@@ -1035,7 +1035,8 @@ __device__ __forceinline__ int sturm_count(const double* d, const double* f2, in
 // slice's scaled T); per step the 32 lanes count at 32 interior points of the
 // bracket, so the bracket shrinks 33-fold per step.
 constexpr int BIS_WARPS = 4;
-__global__ void __launch_bounds__(BIS_WARPS * 32) k_bisect(int m, int R, EigScratch e, double* __restrict__ lam_out) {
+__global__ void __launch_bounds__(BIS_WARPS * 32) k_bisect(int m, int R, EigScratch e, double* __restrict__ lam_out,
+                                                          double abs_tol) {
   extern __shared__ __align__(16) double bsm[];
   double* d = bsm;      // [m] scaled diagonal
   double* f2 = bsm + m; // [m] scaled squared off-diagonal
@@ -1078,7 +1079,8 @@ __global__ void __launch_bounds__(BIS_WARPS * 32) k_bisect(int m, int R, EigScra
   const int idx = m - 1 - r;  // ascending index of the wanted eigenvalue
   for (int it = 0; it < 64; ++it) {
     const double w = hi - lo;
-    if (w <= 2.0 * DBL_EPSILON * (fabs(lo) + fabs(hi)) + pivmin) break;
+    // relative to the eigenvalue (FP64 path), or absolute on the scaled T (abs_tol > 0)
+    if (w <= fmax(2.0 * DBL_EPSILON * (fabs(lo) + fabs(hi)), abs_tol) + pivmin) break;
     const double x = lo + w * ((double)(lane + 1) / 33.0);
     const unsigned above = __ballot_sync(0xffffffffu, sturm_count(d, f2, m, x, pivmin) > idx);
     const int first = above ? __ffs(above) - 1 : 32;  // lowest point with more than idx values below it
@@ -1401,7 +1403,10 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
   {
     TSVD_STAGE("eig_bisect", s);
     const size_t smem_b = 2 * (size_t)m * sizeof(double);
-    k_bisect<<<dim3(cdiv(R, BIS_WARPS), batch), BIS_WARPS * 32, smem_b, s>>>(m, R, e, lam);
+    // FP32 path: eigenvalues to 1e-13 of ||T|| (the vectors and the outputs are FP32; the
+    // smallest kept sigma^2 is far above that); FP64 path: to the eigenvalue's own precision
+    const double abs_tol = kDoubleFloat ? 1e-13 : 0.0;
+    k_bisect<<<dim3(cdiv(R, BIS_WARPS), batch), BIS_WARPS * 32, smem_b, s>>>(m, R, e, lam, abs_tol);
     TSVD_LAUNCHED();
   }
   {
