@@ -371,11 +371,14 @@ def main():
     err_fp64 = rel_err(plan64.U, plan64.S, plan64.V, X64)
     opt = float(np.sqrt(wl.optimal_error2(wl.c2_sigma(d["n1"]), d["R"])) / torch.linalg.vector_norm(X64).item())
 
-    # mixed paths: basis-building products on tcgen05 (TF32 / BF16), the rest as on the FP32 path
+    # mixed paths (basis-building products on tcgen05, TF32 / BF16, the rest as on the FP32 path)
+    # and Alg. 1 of the paper on the FP32 path
     mixed = {}
     if args.precision == "fp32":
-        for prec in ("tf32", "bf16"):
-            pl = api.RbkPlan(d["n1"], d["n2"], d["n3"], d["R"], d["P"], d["q"], seed=0, precision=prec, device=dev)
+        for prec in ("tf32", "bf16", "alg1"):
+            # "alg1": Alg. 1 of the paper (power iteration) on the FP32 path, same Omega
+            pl = api.RbkPlan(d["n1"], d["n2"], d["n3"], d["R"], d["P"], d["q"], seed=0,
+                             precision="fp32" if prec == "alg1" else prec, device=dev, alg1=prec == "alg1")
             pl(Xd)
             torch.cuda.synchronize(dev)
             evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]

@@ -64,10 +64,15 @@ typedef struct {
   int precision;  /* tsvd_precision */
   uint64_t seed;
   int flags;      /* bit 0 (TSVD_FLAG_FP64_QR): orthonormalise the Krylov blocks in FP64 on the
-                     FP32 / mixed paths too (they use FP32 by default; the FP64 path always uses FP64) */
+                     FP32 / mixed paths too (they use FP32 by default; the FP64 path always uses FP64);
+                     bit 1 (TSVD_FLAG_ALG1): Alg. 1 instead of Alg. 2 */
 } tsvd_params;
 
 #define TSVD_FLAG_FP64_QR 1
+/* bit 1 (TSVD_FLAG_ALG1): Alg. 1 of the paper (randomized subspace / power iteration):
+   Q = orth((A A^H)^q A B), orthonormalised after every step (same span), basis of
+   min(R+P, n1, n2) columns; the rest of the pipeline as for Alg. 2 */
+#define TSVD_FLAG_ALG1 2
 
 /* ---- device-side outcome, read back only when requested ---- */
 typedef struct {

@@ -43,14 +43,15 @@ def _workspace(nbytes, device):
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
-def rbk(A, R, P=10, q=2, seed=0, precision="fp32", omega=None, return_info=False, fp64_qr=False):
+def rbk(A, R, P=10, q=2, seed=0, precision="fp32", omega=None, return_info=False, fp64_qr=False, alg1=False):
     """Randomized block Krylov truncated T-SVD (Alg. 2): A ~ U * S * V^T.
 
     A: (n3, n1, n2) CUDA tensor.  Returns U (n3, n1, R), S (n3, R) singular
     tubes, V (n3, n2, R) and sigma_hat (n3 // 2 + 1, R) float64 Fourier-domain
     singular values (descending per slice).  omega (n3, n2, R + P) replaces the
     Philox-drawn test tensor when given.  fp64_qr=True orthonormalises the
-    Krylov blocks in FP64 on the FP32 path as well.
+    Krylov blocks in FP64 on the FP32 path as well; alg1=True runs Alg. 1
+    (power iteration, basis of R+P columns) instead of Alg. 2.
     """
     lib = _lib.load()
     pr = _prec(precision)
@@ -58,8 +59,8 @@ def rbk(A, R, P=10, q=2, seed=0, precision="fp32", omega=None, return_info=False
     A = A.contiguous()
     _need_cuda(A, omega, dtype=dt)
     n3, n1, n2 = A.shape
-    p = _lib.TsvdParams(R=int(R), P=int(P), q=int(q), precision=pr, seed=int(seed),
-                        flags=_lib.TSVD_FLAG_FP64_QR if fp64_qr else 0)
+    flags = (_lib.TSVD_FLAG_FP64_QR if fp64_qr else 0) | (_lib.TSVD_FLAG_ALG1 if alg1 else 0)
+    p = _lib.TsvdParams(R=int(R), P=int(P), q=int(q), precision=pr, seed=int(seed), flags=flags)
     nbytes = C.c_size_t()
     _lib.check(lib.tsvd_rbk_workspace_size(n1, n2, n3, C.byref(p), C.byref(nbytes)), "tsvd_rbk_workspace_size")
     dev = A.device
@@ -87,11 +88,13 @@ class RbkPlan:
     """Pre-allocated outputs and workspace for repeated T-SVDs of one shape
     (no allocation per call, so a loop of calls can be captured in a CUDA graph)."""
 
-    def __init__(self, n1, n2, n3, R, P=10, q=2, seed=0, precision="fp32", device="cuda", fp64_qr=False):
+    def __init__(self, n1, n2, n3, R, P=10, q=2, seed=0, precision="fp32", device="cuda", fp64_qr=False,
+                 alg1=False):
         self.lib = _lib.load()
         self.dt = _DT[precision]
+        flags = (_lib.TSVD_FLAG_FP64_QR if fp64_qr else 0) | (_lib.TSVD_FLAG_ALG1 if alg1 else 0)
         self.p = _lib.TsvdParams(R=int(R), P=int(P), q=int(q), precision=_prec(precision), seed=int(seed),
-                                 flags=_lib.TSVD_FLAG_FP64_QR if fp64_qr else 0)
+                                 flags=flags)
         self.shape = (n1, n2, n3)
         nbytes = C.c_size_t()
         _lib.check(self.lib.tsvd_rbk_workspace_size(n1, n2, n3, C.byref(self.p), C.byref(nbytes)), "workspace")

@@ -26,23 +26,27 @@ __device__ __forceinline__ int pidx(int i, int j, int n) { return i * n - (i * (
 // 1/sqrt(d_j) at the end.
 // ---------------------------------------------------------------------------
 template <typename GC>
-__global__ void __launch_bounds__(256) k_chol_upper(const GC* __restrict__ G, long ldg, long sG,
+__global__ void __launch_bounds__(512) k_chol_upper(const GC* __restrict__ G, long ldg, long sG,
                                                     double2* __restrict__ Rm, long ldr, long sR, int nb,
                                                     double shift_rel, double dead_rel,
                                                     uint32_t* __restrict__ dead_out) {
   using Rt = decltype(GC().x);
   extern __shared__ __align__(16) unsigned char chsm[];
-  GC* S = (GC*)chsm;          // packed upper triangle
+  const int np = nb * (nb + 1) / 2;
+  GC* S = (GC*)chsm;                                  // packed upper triangle
+  unsigned char* rowof = (unsigned char*)(S + np);    // row of each packed index (nb <= 128)
   __shared__ Rt dg[128];      // diagonal of G (pivot test of the plain passes)
   __shared__ Rt dj[128];      // pivots d_j (0 for a dead column)
   __shared__ double red[16];
   const int b = blockIdx.x, tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   G += (long)b * sG;
   Rm += (long)b * sR;
   for (int e = tid; e < nb * nb; e += blockDim.x) {
     const int i = e / nb, j = e - i * nb;
-    if (j >= i) S[pidx(i, j, nb)] = G[(long)i * ldg + j];
+    if (j >= i) {
+      S[pidx(i, j, nb)] = G[(long)i * ldg + j];
+      rowof[pidx(i, j, nb)] = (unsigned char)i;
+    }
   }
   if (tid < nb) dg[tid] = G[(long)tid * ldg + tid].x;
   __syncthreads();
@@ -51,26 +55,26 @@ __global__ void __launch_bounds__(256) k_chol_upper(const GC* __restrict__ G, lo
   if (tid < nb) S[pidx(tid, tid, nb)].x += sft;
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    const Rt d = S[pidx(j, j, nb)].x;
+    const int offj = pidx(j, j, nb);
+    const Rt d = S[offj].x;
     const bool dead = (shift_rel > 0.0) ? !(d > Rt(0)) : !(d > (Rt)dead_rel * dg[j]);
     if (tid == 0) dj[j] = dead ? Rt(0) : d;
-    if (!dead) {
+    if (!dead && j + 1 < nb) {
+      // trailing triangle (rows i > j) = the packed suffix from pidx(j+1, j+1), flattened over the CTA
       const Rt inv = Rt(1) / d;
-      const int offj = pidx(j, j, nb);
-      for (int i = j + 1 + warp; i < nb; i += nwarp) {
+      for (int p = pidx(j + 1, j + 1, nb) + tid; p < np; p += blockDim.x) {
+        const int i = rowof[p];
+        const int k = p - pidx(i, i, nb) + i;
         GC a = S[offj + (i - j)];  // S(j, i); the update uses conj(a) / d
+        const GC cjk = S[offj + (k - j)];
         a.x *= inv;
         a.y *= inv;
-        const int offi = pidx(i, i, nb);
-        for (int k = i + lane; k < nb; k += 32) {
-          const GC cjk = S[offj + (k - j)];
-          GC t = S[offi + (k - i)];
-          t.x = fma(-a.x, cjk.x, t.x);
-          t.x = fma(-a.y, cjk.y, t.x);
-          t.y = fma(-a.x, cjk.y, t.y);
-          t.y = fma(a.y, cjk.x, t.y);
-          S[offi + (k - i)] = t;
-        }
+        GC t = S[p];
+        t.x = fma(-a.x, cjk.x, t.x);
+        t.x = fma(-a.y, cjk.y, t.x);
+        t.y = fma(-a.x, cjk.y, t.y);
+        t.y = fma(a.y, cjk.x, t.y);
+        S[p] = t;
       }
     }
     __syncthreads();
@@ -103,9 +107,10 @@ int chol_upper(const GC* G, long ldg, long sG, double2* Rm, long ldr, long sR, i
                double dead_rel, uint32_t* dead, cudaStream_t s) {
   if (nb <= 0 || batch <= 0) return TSVD_OK;
   if (nb > 128) return TSVD_ERR_UNSUPPORTED;
-  const size_t smem = (size_t)nb * (nb + 1) / 2 * sizeof(GC);
+  const size_t np = (size_t)nb * (nb + 1) / 2;
+  const size_t smem = np * sizeof(GC) + np;  // packed triangle + row table
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_chol_upper<GC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_chol_upper<GC><<<batch, 256, smem, s>>>(G, ldg, sG, Rm, ldr, sR, nb, shift_rel, dead_rel, dead);
+  k_chol_upper<GC><<<batch, 512, smem, s>>>(G, ldg, sG, Rm, ldr, sR, nb, shift_rel, dead_rel, dead);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }
@@ -121,7 +126,9 @@ template int chol_upper<float2>(const float2*, long, long, double2*, long, long,
 // columns k > j with R(j, k) (R packed in shared memory, diagonal stored as
 // 1/R_jj, 0 for a dead column).
 // ---------------------------------------------------------------------------
-constexpr int TS_ROWS = 4;
+// rows per warp (more rows raise the registers past one wave of CTAs)
+template <typename C>
+constexpr int ts_rows() { return 4; }
 constexpr int TS_WARPS = 8;
 
 template <typename C>
@@ -153,6 +160,7 @@ __global__ void __launch_bounds__(TS_WARPS * 32) k_trsm_right_upper(C* __restric
     Rp[pidx(i, j, nb)] = out;
   }
   __syncthreads();
+  constexpr int TS_ROWS = ts_rows<C>();
   const int r0 = (blockIdx.x * TS_WARPS + warp) * TS_ROWS;
   if (r0 >= n1) return;
   C x[TS_ROWS][4];
@@ -212,7 +220,7 @@ int trsm_right_upper(C* W, long ldw, long sW, const double2* Rm, long ldr, long 
     cudaGetLastError();
     return TSVD_ERR_CUDA;
   }
-  dim3 grid(cdiv(n1, TS_ROWS * TS_WARPS), batch);
+  dim3 grid(cdiv(n1, ts_rows<C>() * TS_WARPS), batch);
   k_trsm_right_upper<C><<<grid, TS_WARPS * 32, smem, s>>>(W, ldw, sW, Rm, ldr, sR, n1, nb, dead);
   TSVD_LAUNCHED();
   return TSVD_OK;

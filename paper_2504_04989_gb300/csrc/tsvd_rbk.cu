@@ -34,7 +34,8 @@ namespace tsvd {
 
 struct RbkDims {
   int n1, n2, n3, h, R, P, q, b, m;
-  int tc;  // basis-building products on tcgen05: 0 none, 1 TF32, 2 BF16
+  int tc;    // basis-building products on tcgen05: 0 none, 1 TF32, 2 BF16
+  int alg1;  // Alg. 1 (power iteration, last block only) instead of Alg. 2
 };
 
 static int rbk_dims(int n1, int n2, int n3, const tsvd_params* p, RbkDims* d) {
@@ -50,7 +51,8 @@ static int rbk_dims(int n1, int n2, int n3, const tsvd_params* p, RbkDims* d) {
   d->q = p->q;
   d->b = p->R + p->P;
   d->tc = (p->precision == TSVD_MIXED_TF32) ? 1 : (p->precision == TSVD_MIXED_BF16) ? 2 : 0;
-  long m = (long)(p->q + 1) * d->b;
+  d->alg1 = (p->flags & TSVD_FLAG_ALG1) ? 1 : 0;
+  long m = (long)(d->alg1 ? 1 : p->q + 1) * d->b;
   m = std::min<long>(m, std::min(n1, n2));
   d->m = (int)m;
   if (d->b > 128 || d->m > 512) return TSVD_ERR_UNSUPPORTED;
@@ -285,7 +287,22 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
   TSVD_TRY((to_orth<T, L>(w, d, b0, s)));
   TSVD_TRY((orth_block<T, L>(d, w, 0, b0, 0, p.seed, s)));
   int c = b0, pw = b0;
-  for (int i = 1; i <= d.q && c < m; ++i) {
+  if (d.alg1) {  // Alg. 1: Q <- orth(A A^H Q), q times, in place
+    for (int i = 1; i <= d.q; ++i) {
+      {
+        TSVD_STAGE("krylov_gemm", s);
+        TSVD_TRY(cgemm<C>(gemm('H', 'N', n2, b0, n1, 1.0, w.Ah, n2, sA, w.Qt, m, sQ, 0.0, w.CHt, m, sCH, h), w.splitk,
+                          w.splitk_elems * 2, s));
+      }
+      {
+        TSVD_STAGE(d.tc ? "krylov_gemm_tc" : "krylov_gemm", s);
+        TSVD_TRY(basis_product<T>(d, w, w.CHt, m, sCH, b0, s));
+      }
+      TSVD_TRY((to_orth<T, L>(w, d, b0, s)));
+      TSVD_TRY((orth_block<T, L>(d, w, 0, b0, i, p.seed, s)));
+    }
+  }
+  for (int i = 1; !d.alg1 && i <= d.q && c < m; ++i) {
     const int bi = std::min(b, m - c);
     {
     TSVD_STAGE("krylov_gemm", s);

@@ -205,3 +205,31 @@ def test_c2_full_size_fp32_sampled_slices(api, orc):
     for j in range(len(slices)):
         g = np.linalg.norm(Xh[j] - (Uh[j] * sig[slices[j]]) @ Vh[j].conj().T) ** 2
         assert abs(g - ref["err2"][j]) <= ERR_TOL * ref["err2"][j], (slices[j], g, ref["err2"][j])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("n1,n2,n3,R,P,q", [(64, 64, 16, 10, 5, 2), (65, 129, 7, 6, 4, 3), (40, 33, 2, 4, 2, 1)])
+def test_alg1_against_oracle(api, orc, n1, n2, n3, R, P, q, precision):
+    """Alg. 1 (power iteration, orthonormalised after every step) with the
+    same kernels: sigma-hat against the oracle's Alg. 1 mode, and the
+    invariant err(Alg. 2) <= err(Alg. 1) for the same Omega (nested spans)."""
+    X = wl.make_c1(0) if (n1, n2, n3) == (64, 64, 16) else \
+        wl.low_tubal_rank(n1, n2, n3, np.arange(1, min(n1, n2) + 1) ** -1.0, noise_std=1e-4, seed=n1 + n3)
+    om = wl.omega(n2, R + P, n3, seed=5)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    Xin = X if precision == "fp64" else X.astype(np.float32).astype(np.float64)
+    omi = om if precision == "fp64" else om.astype(np.float32).astype(np.float64)
+    U1, S1, V1, s1, info = api.rbk(dev(Xin, dt), R, P, q, precision=precision, omega=dev(omi, dt), alg1=True,
+                                   return_info=True)
+    torch.cuda.synchronize()
+    assert info["status"] == 0 and info["m_eff"] == min(R + P, n1, n2)
+    ref = orc.rtsvd_fourier(Xin, R, P, q, mode="alg1", omega=omi)
+    s1 = s1.cpu().numpy()
+    mask = ref["sig"] > (1e-6 if precision == "fp32" else 0) * ref["sig"].max()
+    rel = np.abs(s1 - ref["sig"])[mask] / ref["sig"][mask]
+    assert rel.max() < SIG_TOL[precision], rel.max()
+    U2, S2, V2, s2 = api.rbk(dev(Xin, dt), R, P, q, precision=precision, omega=dev(omi, dt))
+    torch.cuda.synchronize()
+    e1 = api.tsvd_error(dev(Xin, dt), U1, S1, V1).item()
+    e2 = api.tsvd_error(dev(Xin, dt), U2, S2, V2).item()
+    assert e2 <= e1 * (1 + (1e-10 if precision == "fp64" else 1e-4)), (e1, e2)
