@@ -1031,6 +1031,35 @@ __device__ __forceinline__ int sturm_count(const double* d, const double* f2, in
   return cnt;
 }
 
+// The same count in FP32 (exponent kept within +-60 by powers of two).  A
+// computed count is the exact count of a tridiagonal whose entries moved by a
+// few units in the last place (backward stability of the recurrence), so a
+// bracket from FP32 counts holds the eigenvalue once widened by a margin far
+// above eps32 ||T||.
+__device__ __forceinline__ int sturm_count_f32(const float* d, const float* f2, int m, float x, float pivmin) {
+  float pm = 1.0f, p = d[0] - x;
+  if (p == 0.0f) p = -pivmin;
+  int cnt = (int)(__float_as_uint(p) >> 31);
+  for (int i = 1; i < m; ++i) {
+    float pn = fmaf(d[i] - x, p, -f2[i - 1] * pm);
+    unsigned bn = __float_as_uint(pn);
+    if ((bn << 1) == 0u) {
+      pn = -pivmin * p;
+      bn = __float_as_uint(pn);
+    }
+    cnt += (int)((bn ^ __float_as_uint(p)) >> 31);
+    pm = p;
+    p = pn;
+    const int ex = (int)((bn >> 23) & 0xffu) - 127;
+    if (ex > 60 || ex < -60) {
+      const float sc = __uint_as_float((unsigned)(127 - ex) << 23);
+      p *= sc;
+      pm *= sc;
+    }
+  }
+  return cnt;
+}
+
 // Multisection: one warp per wanted eigenvalue (the (r+1)-th largest of the
 // slice's scaled T); per step the 32 lanes count at 32 interior points of the
 // bracket, so the bracket shrinks 33-fold per step.
@@ -1040,6 +1069,8 @@ __global__ void __launch_bounds__(BIS_WARPS * 32) k_bisect(int m, int R, EigScra
   extern __shared__ __align__(16) double bsm[];
   double* d = bsm;      // [m] scaled diagonal
   double* f2 = bsm + m; // [m] scaled squared off-diagonal
+  float* d32 = (float*)(bsm + 2 * m);  // [m] the same in FP32 (coarse rounds)
+  float* f232 = d32 + m;
   __shared__ double s_scale, s_lo, s_hi;
   const int b = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r = blockIdx.x * BIS_WARPS + warp;
@@ -1053,6 +1084,8 @@ __global__ void __launch_bounds__(BIS_WARPS * 32) k_bisect(int m, int R, EigScra
     d[i] = e.d[(long)b * m + i] * sc;
     const double fi = (i < m - 1) ? e.f[(long)b * m + i] * sc : 0.0;
     f2[i] = fi * fi;
+    d32[i] = (float)d[i];
+    f232[i] = (float)(fi * fi);
   }
   if (threadIdx.x == 0) {  // Gershgorin bracket of the scaled T
     double lo = e.d[(long)b * m] * sc, hi = lo;
@@ -1077,6 +1110,22 @@ __global__ void __launch_bounds__(BIS_WARPS * 32) k_bisect(int m, int R, EigScra
   double lo = s_lo - (4.0 * DBL_EPSILON * tn + pivmin);
   double hi = s_hi + (4.0 * DBL_EPSILON * tn + pivmin);
   const int idx = m - 1 - r;  // ascending index of the wanted eigenvalue
+  if (abs_tol > 0.0) {
+    // coarse rounds on FP32 counts (64x the FP64 rate here), then widen by 4e-5 ||T||
+    const float pivmin32 = 1e-30f;
+    for (int it = 0; it < 3; ++it) {
+      const double w = hi - lo;
+      const float x = (float)(lo + w * ((double)(lane + 1) / 33.0));
+      const unsigned above = __ballot_sync(0xffffffffu, sturm_count_f32(d32, f232, m, x, pivmin32) > idx);
+      const int first = above ? __ffs(above) - 1 : 32;
+      const double nlo = (first == 0) ? lo : lo + w * ((double)first / 33.0);
+      const double nhi = (first == 32) ? hi : lo + w * ((double)(first + 1) / 33.0);
+      lo = nlo;
+      hi = nhi;
+    }
+    lo = fmax(lo - 4e-5 * tn, s_lo - (4.0 * DBL_EPSILON * tn + pivmin));
+    hi = fmin(hi + 4e-5 * tn, s_hi + (4.0 * DBL_EPSILON * tn + pivmin));
+  }
   for (int it = 0; it < 64; ++it) {
     const double w = hi - lo;
     // relative to the eigenvalue (FP64 path), or absolute on the scaled T (abs_tol > 0)
@@ -1094,14 +1143,14 @@ __global__ void __launch_bounds__(BIS_WARPS * 32) k_bisect(int m, int R, EigScra
 }
 
 // One thread per wanted eigenpair r (the (r+1)-th largest), TP_THREADS pairs
-// per CTA: inverse iteration (three solves) with a partially pivoted LU of
+// per CTA: inverse iteration (three solves, two on the FP32 path) with a partially pivoted LU of
 // T - lam I for the eigenvalue found by k_bisect.  The LU factors stream
 // from global memory (coalesced across the CTA's threads); the iterate lives
 // in shared memory, so the dependent chain of each solve never waits on L2.
 constexpr int TP_THREADS = 32;
 
 __global__ void __launch_bounds__(TP_THREADS) k_tridiag_pairs(int m, int R, EigScratch e,
-                                                              const double* __restrict__ lam_out) {
+                                                              const double* __restrict__ lam_out, int iters) {
   extern __shared__ __align__(16) double tsm[];
   double* d = tsm;      // [m] scaled diagonal
   double* f = tsm + m;  // [m] scaled off-diagonal
@@ -1145,9 +1194,10 @@ __global__ void __launch_bounds__(TP_THREADS) k_tridiag_pairs(int m, int R, EigS
     const double dn = d[i + 1] - lam, un = (i < m - 2) ? f[i + 1] : 0.0;
     if (fabs(dcur) >= fabs(sub)) {
       const double piv = (fabs(dcur) < tiny) ? copysign(tiny, dcur) : dcur;
-      const double l = sub / piv;
+      const double rp = 1.0 / piv;  // one division per step
+      const double l = sub * rp;
       LU(0, i) = l;
-      LU(1, i) = 1.0 / piv;
+      LU(1, i) = rp;
       LU(2, i) = ucur;
       LU(3, i) = 0.0;
       LU(4, i) = 0.0;
@@ -1156,9 +1206,10 @@ __global__ void __launch_bounds__(TP_THREADS) k_tridiag_pairs(int m, int R, EigS
     } else {
       // swap rows i and i+1: the new row i is (sub, dn, un); the old row i is eliminated
       const double sb = (fabs(sub) < tiny) ? copysign(tiny, sub) : sub;
-      const double l = dcur / sb;
+      const double rs = 1.0 / sb;
+      const double l = dcur * rs;
       LU(0, i) = l;
-      LU(1, i) = 1.0 / sb;
+      LU(1, i) = rs;
       LU(2, i) = dn;
       LU(3, i) = un;
       LU(4, i) = 1.0;
@@ -1174,7 +1225,7 @@ __global__ void __launch_bounds__(TP_THREADS) k_tridiag_pairs(int m, int R, EigS
     const uint4 w = philox10(make_uint4((uint32_t)i, (uint32_t)r, (uint32_t)b, 0x1e16u), 0x2504u, 0x4989u);
     X(i) = ((double)w.x + 0.5) * (2.0 / 4294967296.0) - 1.0;
   }
-  for (int iter = 0; iter < 3; ++iter) {
+  for (int iter = 0; iter < iters; ++iter) {
     double xi = X(0);
     for (int i = 0; i < m - 1; ++i) {  // row interchanges and multipliers: L^{-1} P
       double xn = X(i + 1);
@@ -1402,7 +1453,7 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
   }
   {
     TSVD_STAGE("eig_bisect", s);
-    const size_t smem_b = 2 * (size_t)m * sizeof(double);
+    const size_t smem_b = 2 * (size_t)m * (sizeof(double) + sizeof(float));
     // FP32 path: eigenvalues to 1e-13 of ||T|| (the vectors and the outputs are FP32; the
     // smallest kept sigma^2 is far above that); FP64 path: to the eigenvalue's own precision
     const double abs_tol = kDoubleFloat ? 1e-13 : 0.0;
@@ -1414,7 +1465,9 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
     const size_t smem_tp = (3 + (size_t)TP_THREADS) * m * sizeof(double);
     if (smem_tp > 48 * 1024)
       cudaFuncSetAttribute(k_tridiag_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tp);
-    k_tridiag_pairs<<<dim3(cdiv(R, TP_THREADS), batch), TP_THREADS, smem_tp, s>>>(m, R, e, lam);
+    // solves: 3 (FP64 path), 2 on the FP32 path (eigenvalues to 1e-13 ||T|| already make one solve
+    // amplify the wanted direction by gap / 1e-13; the vectors end in FP32)
+    k_tridiag_pairs<<<dim3(cdiv(R, TP_THREADS), batch), TP_THREADS, smem_tp, s>>>(m, R, e, lam, kDoubleFloat ? 2 : 3);
     TSVD_LAUNCHED();
   }
   {
