@@ -73,6 +73,11 @@ typedef struct {
    Q = orth((A A^H)^q A B), orthonormalised after every step (same span), basis of
    min(R+P, n1, n2) columns; the rest of the pipeline as for Alg. 2 */
 #define TSVD_FLAG_ALG1 2
+/* bit 2 (TSVD_FLAG_SIMT): FP32 / mixed paths: run the Krylov products on the FP32 SIMT units
+   instead of the tensor cores (by default the FP32 path runs them on tcgen05 as split TF32,
+   x = hi + lo with hi the nearest TF32, products hi*hi + hi*lo + lo*hi in FP32, about 22
+   significant bits) */
+#define TSVD_FLAG_SIMT 4
 
 /* ---- device-side outcome, read back only when requested ---- */
 typedef struct {

@@ -97,6 +97,16 @@ int expand_thin(const float2* Y, long ldy, long sy, int K, int N, void* E, long 
                 bool bf16, cudaStream_t s);
 // rows x cols FP32 rows (leading dim ldx) copied to BF16 or FP32 rows of leading dim ldy (zero padded)
 int copy_rows(const float* x, long ldx, void* y, long ldy, int cols, long rows, bool bf16, cudaStream_t s);
+// split TF32: C = A B^T with A = Ahi + Alo, B = Bhi + Blo (hi*hi + hi*lo + lo*hi), FP32-level accuracy
+int tc_gemm_split(const float* Ahi, const float* Alo, long lda, long sA, int M, const float* Bhi, const float* Blo,
+                  long ldb, long sB, int N, int K, float* C, long ldc, long sC, int batch, int* err, cudaStream_t s);
+// FP32 rows -> hi (nearest TF32) / lo rows of leading dim ldy, padding zeroed
+int split_rows(const float* x, long ldx, float* hi, float* lo, long ldy, int cols, long rows, cudaStream_t s);
+// per slice complex X (rows x cols) -> X^T as real rows of 2 rows floats (leading dim ldt), hi / lo
+int split_transpose(const float2* X, int rows, int cols, int batch, float* hi, float* lo, long ldt, cudaStream_t s);
+// expand_thin into FP32 hi / lo parts
+int expand_thin_split(const float2* Y, long ldy, long sy, int K, int N, float* Eh, float* El, long lde, long se,
+                      int batch, int mode, cudaStream_t s);
 // eig.cu
 // Eigen-decomposition of the m x m Hermitian G per slice (G is overwritten):
 // top-R eigenvalues (descending) in lam (batch x R) and eigenvectors in

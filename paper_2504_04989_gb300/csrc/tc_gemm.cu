@@ -11,6 +11,12 @@
 // tcgen05.ld and store it.  Every wait is bounded: on a timeout the kernel
 // records an error flag instead of hanging.
 //
+// A third mode keeps FP32 accuracy on the TF32 units ("split TF32"): each
+// operand is split as x = hi + lo with hi = x rounded to TF32 and lo = x - hi
+// (exact in FP32), and the tile product is hi*hi + hi*lo + lo*hi accumulated
+// in the same TMEM tile (about 22 significant bits per product; lo*lo, below
+// FP32 rounding, is dropped).  Four operand tiles per stage, three stages.
+//
 // Complex products use it without moving the big operand: an interleaved
 // complex matrix X (rows x cols) is the real matrix [Re Im Re Im ...] of
 // rows x 2cols, so X * Y = real(X) * E(Y)^T with a small expanded real form
@@ -26,9 +32,14 @@ namespace tsvd {
 
 constexpr int TC_BM = 128;
 constexpr int TC_BN = 128;
-constexpr int TC_STAGES = 4;
 constexpr int TC_TILE_BYTES = 128 * 128;  // 128 rows x 128 bytes of K
-constexpr int TC_SMEM = 2 * TC_STAGES * TC_TILE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+// MODE 0: TF32, 1: BF16, 2: split TF32
+template <int MODE>
+constexpr int tc_stages() { return MODE == 2 ? 3 : 4; }
+template <int MODE>
+constexpr int tc_ops() { return MODE == 2 ? 4 : 2; }  // operand tiles per stage
+template <int MODE>
+constexpr int tc_smem() { return tc_stages<MODE>() * tc_ops<MODE>() * TC_TILE_BYTES + 1024 + 256; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -102,25 +113,28 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-template <bool BF16>
+template <int MODE>
 __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
-                                                    const __grid_constant__ CUtensorMap tmB, float* __restrict__ C,
+                                                    const __grid_constant__ CUtensorMap tmB,
+                                                    const __grid_constant__ CUtensorMap tmA2,
+                                                    const __grid_constant__ CUtensorMap tmB2, float* __restrict__ C,
                                                     long ldc, long sC, int M, int N, int nk, int* __restrict__ err) {
+  constexpr bool BF16 = MODE == 1, SPLIT = MODE == 2;
+  constexpr int STAGES = tc_stages<MODE>(), NOPS = tc_ops<MODE>();
   extern __shared__ unsigned char tc_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* As = base;
-  unsigned char* Bs = base + TC_STAGES * TC_TILE_BYTES;
-  uint64_t* bars = (uint64_t*)(Bs + TC_STAGES * TC_TILE_BYTES);  // full[S], empty[S], done
-  uint32_t* tslot = (uint32_t*)(bars + 2 * TC_STAGES + 1);
+  auto tile = [&](int s, int o) { return base + (s * NOPS + o) * TC_TILE_BYTES; };  // o: A, B, A lo, B lo
+  uint64_t* bars = (uint64_t*)(base + STAGES * NOPS * TC_TILE_BYTES);  // full[S], empty[S], done
+  uint32_t* tslot = (uint32_t*)(bars + 2 * STAGES + 1);
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n0 = blockIdx.x * TC_BN, m0 = blockIdx.y * TC_BM, bz = blockIdx.z;
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_STAGES), done = smem_u32(bars + 2 * TC_STAGES);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
   constexpr int KE = BF16 ? 64 : 32;  // elements per 128 bytes of K
 
   if (tid == 0) {
     s_fail = 0;
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
@@ -140,30 +154,41 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
   int issued = 0;  // stages the producer loaded
   if (tid == 0) {  // TMA producer
     for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % TC_STAGES, round = kb / TC_STAGES;
+      const int s = kb % STAGES, round = kb / STAGES;
       if (round > 0 && !mbar_wait(empty0 + 8 * s, (round - 1) & 1)) {
         s_fail = 1;
         break;
       }
-      mbar_expect_tx(full0 + 8 * s, 2 * TC_TILE_BYTES);
-      tma_load_3d(smem_u32(As + s * TC_TILE_BYTES), &tmA, kb * KE, m0, bz, full0 + 8 * s);
-      tma_load_3d(smem_u32(Bs + s * TC_TILE_BYTES), &tmB, kb * KE, n0, bz, full0 + 8 * s);
+      mbar_expect_tx(full0 + 8 * s, NOPS * TC_TILE_BYTES);
+      tma_load_3d(smem_u32(tile(s, 0)), &tmA, kb * KE, m0, bz, full0 + 8 * s);
+      tma_load_3d(smem_u32(tile(s, 1)), &tmB, kb * KE, n0, bz, full0 + 8 * s);
+      if (SPLIT) {
+        tma_load_3d(smem_u32(tile(s, 2)), &tmA2, kb * KE, m0, bz, full0 + 8 * s);
+        tma_load_3d(smem_u32(tile(s, 3)), &tmB2, kb * KE, n0, bz, full0 + 8 * s);
+      }
       issued = kb + 1;
     }
   } else if (tid == 32) {  // MMA issuer
     const uint32_t idesc = instr_desc<BF16>();
     for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % TC_STAGES, round = kb / TC_STAGES;
+      const int s = kb % STAGES, round = kb / STAGES;
       if (!mbar_wait(full0 + 8 * s, round & 1)) {
         s_fail = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint64_t ad = smem_desc_sw128(smem_u32(As + s * TC_TILE_BYTES));
-      const uint64_t bd = smem_desc_sw128(smem_u32(Bs + s * TC_TILE_BYTES));
+      const uint64_t ad = smem_desc_sw128(smem_u32(tile(s, 0)));
+      const uint64_t bd = smem_desc_sw128(smem_u32(tile(s, 1)));
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk)  // 32 bytes of K per instruction: advance the start address by 2 x 16 B
+      for (int kk = 0; kk < 4; ++kk) {  // 32 bytes of K per instruction: advance the start address by 2 x 16 B
         mma_issue<BF16>(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0);
+        if (SPLIT) {
+          const uint64_t ad2 = smem_desc_sw128(smem_u32(tile(s, 2)));
+          const uint64_t bd2 = smem_desc_sw128(smem_u32(tile(s, 3)));
+          mma_issue<BF16>(tmem, ad + 2 * kk, bd2 + 2 * kk, idesc, 1);
+          mma_issue<BF16>(tmem, ad2 + 2 * kk, bd + 2 * kk, idesc, 1);
+        }
+      }
       mma_commit(empty0 + 8 * s);
     }
     mma_commit(done);
@@ -199,8 +224,8 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
     atomicExch(err, 1);
   }
   if (tid == 0) {  // make sure no copy of this CTA is still landing in shared memory
-    for (int kb = (issued > TC_STAGES ? issued - TC_STAGES : 0); kb < issued; ++kb)
-      mbar_wait(full0 + 8 * (kb % TC_STAGES), (kb / TC_STAGES) & 1);
+    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+      mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -252,6 +277,20 @@ bool tc_gemm_supported(const void* A, long lda, long sA, const void* B, long ldb
   return batch <= 65535;
 }
 
+template <int MODE>
+static int tc_launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& ta2, const CUtensorMap& tb2,
+                     float* C, long ldc, long sC, int M, int N, int nk, int batch, int* err, cudaStream_t s) {
+  dim3 grid(cdiv(N, TC_BN), cdiv(M, TC_BM), batch);
+  if (cudaFuncSetAttribute(k_tc_gemm<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<MODE>()) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return TSVD_ERR_CUDA;
+  }
+  k_tc_gemm<MODE><<<grid, 128, tc_smem<MODE>(), s>>>(ta, tb, ta2, tb2, C, ldc, sC, M, N, nk, err);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
 int tc_gemm(const void* A, long lda, long sA, int M, const void* B, long ldb, long sB, int N, int K, float* C, long ldc,
             long sC, int batch, bool bf16, int* err, cudaStream_t s) {
   if (M <= 0 || N <= 0 || batch <= 0) return TSVD_OK;
@@ -261,16 +300,22 @@ int tc_gemm(const void* A, long lda, long sA, int M, const void* B, long ldb, lo
   TSVD_TRY(make_map(&tb, B, N, K, ldb, sB, batch, bf16));
   const int kelem = bf16 ? 64 : 32;
   const int nk = (K + kelem - 1) / kelem;
-  dim3 grid(cdiv(N, TC_BN), cdiv(M, TC_BM), batch);
-  if (bf16) {
-    cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    k_tc_gemm<true><<<grid, 128, TC_SMEM, s>>>(ta, tb, C, ldc, sC, M, N, nk, err);
-  } else {
-    cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    k_tc_gemm<false><<<grid, 128, TC_SMEM, s>>>(ta, tb, C, ldc, sC, M, N, nk, err);
-  }
-  TSVD_LAUNCHED();
-  return TSVD_OK;
+  if (bf16) return tc_launch<1>(ta, tb, ta, tb, C, ldc, sC, M, N, nk, batch, err, s);
+  return tc_launch<0>(ta, tb, ta, tb, C, ldc, sC, M, N, nk, batch, err, s);
+}
+
+int tc_gemm_split(const float* Ahi, const float* Alo, long lda, long sA, int M, const float* Bhi, const float* Blo,
+                  long ldb, long sB, int N, int K, float* C, long ldc, long sC, int batch, int* err, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || batch <= 0) return TSVD_OK;
+  if (!tc_gemm_supported(Ahi, lda, sA, Bhi, ldb, sB, batch, false) ||
+      !tc_gemm_supported(Alo, lda, sA, Blo, ldb, sB, batch, false))
+    return TSVD_ERR_UNSUPPORTED;
+  CUtensorMap ta, tb, ta2, tb2;
+  TSVD_TRY(make_map(&ta, Ahi, M, K, lda, sA, batch, false));
+  TSVD_TRY(make_map(&tb, Bhi, N, K, ldb, sB, batch, false));
+  TSVD_TRY(make_map(&ta2, Alo, M, K, lda, sA, batch, false));
+  TSVD_TRY(make_map(&tb2, Blo, N, K, ldb, sB, batch, false));
+  return tc_launch<2>(ta, tb, ta2, tb2, C, ldc, sC, M, N, (K + 31) / 32, batch, err, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -349,6 +394,116 @@ int copy_rows(const float* x, long ldx, void* y, long ldy, int cols, long rows, 
   const unsigned grid = std::min<long>(cdiv(total, 256), 8192);
   if (bf16) k_copy_rows<__nv_bfloat16><<<grid, 256, 0, s>>>(x, ldx, (__nv_bfloat16*)y, ldy, cols, rows);
   else k_copy_rows<float><<<grid, 256, 0, s>>>(x, ldx, (float*)y, ldy, cols, rows);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Split operands for the split-TF32 mode: hi = x rounded to the nearest TF32
+// (cvt.rna.tf32.f32), lo = x - hi (exact in FP32).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// rows x cols FP32 (leading dim ldx) to hi / lo rows of leading dim ldy (padding zeroed)
+__global__ void k_split_rows(const float* __restrict__ x, long ldx, float* __restrict__ hi, float* __restrict__ lo,
+                             long ldy, int cols, long rows) {
+  const long total = rows * ldy;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const long r = i / ldy;
+    const long c = i % ldy;
+    const float v = c < cols ? x[r * ldx + c] : 0.0f;
+    const float h = tf32_hi(v);
+    hi[i] = h;
+    lo[i] = v - h;
+  }
+}
+
+int split_rows(const float* x, long ldx, float* hi, float* lo, long ldy, int cols, long rows, cudaStream_t s) {
+  const long total = rows * ldy;
+  if (total <= 0) return TSVD_OK;
+  k_split_rows<<<(unsigned)std::min<long>(cdiv(total, 256), 8192), 256, 0, s>>>(x, ldx, hi, lo, ldy, cols, rows);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
+// per slice: complex X (rows x cols, interleaved, leading dim cols) transposed
+// to XT (cols x rows complex = real rows of 2 rows floats, leading dim ldt),
+// split into hi / lo; 32 x 32 complex tiles through shared memory
+__global__ void k_split_transpose(const float2* __restrict__ X, int rows, int cols, float* __restrict__ hi,
+                                  float* __restrict__ lo, long ldt) {
+  __shared__ float2 t[32][33];
+  const int b = blockIdx.z;
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const float2* Xb = X + (long)b * rows * cols;
+  for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+    const int r = r0 + rr, c = c0 + threadIdx.x;
+    t[rr][threadIdx.x] = (r < rows && c < cols) ? Xb[(long)r * cols + c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float* hb = hi + (long)b * cols * ldt;
+  float* lb = lo + (long)b * cols * ldt;
+  for (int cc = threadIdx.y; cc < 32; cc += blockDim.y) {
+    const int c = c0 + cc, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) {
+      const float2 v = t[threadIdx.x][cc];
+      const float hx = tf32_hi(v.x), hy = tf32_hi(v.y);
+      hb[(long)c * ldt + 2 * r] = hx;
+      hb[(long)c * ldt + 2 * r + 1] = hy;
+      lb[(long)c * ldt + 2 * r] = v.x - hx;
+      lb[(long)c * ldt + 2 * r + 1] = v.y - hy;
+    }
+  }
+}
+
+int split_transpose(const float2* X, int rows, int cols, int batch, float* hi, float* lo, long ldt, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0 || batch <= 0) return TSVD_OK;
+  if (batch > 65535) return TSVD_ERR_UNSUPPORTED;
+  // zero the padding columns of every row once (2 rows .. ldt)
+  if (ldt > 2L * rows) {
+    if (cudaMemset2DAsync(hi + 2L * rows, ldt * sizeof(float), 0, (ldt - 2L * rows) * sizeof(float),
+                          (size_t)batch * cols, s) != cudaSuccess ||
+        cudaMemset2DAsync(lo + 2L * rows, ldt * sizeof(float), 0, (ldt - 2L * rows) * sizeof(float),
+                          (size_t)batch * cols, s) != cudaSuccess)
+      return TSVD_ERR_CUDA;
+  }
+  dim3 grid(cdiv(cols, 32), cdiv(rows, 32), batch), block(32, 8);
+  k_split_transpose<<<grid, block, 0, s>>>(X, rows, cols, hi, lo, ldt);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
+// expanded real form (as expand_thin, FP32) split into hi / lo
+__global__ void k_expand_split(const float2* __restrict__ Y, long ldy, long sy, int K, int N, float* __restrict__ Eh,
+                               float* __restrict__ El, long lde, long se, int batch, int mode) {
+  const long total = (long)batch * K * N;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int k = idx % K;
+    const long t = idx / K;
+    const int n = t % N;
+    const int b = t / N;
+    const float2 y = Y[(long)b * sy + (long)k * ldy + n];
+    const float v[4] = {y.x, mode == 0 ? -y.y : y.y, y.y, mode == 0 ? y.x : -y.x};
+    const long o0 = (long)b * se + (long)(2 * n) * lde + 2 * k;
+    const long off[4] = {o0, o0 + 1, o0 + lde, o0 + lde + 1};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float h = tf32_hi(v[q]);
+      Eh[off[q]] = h;
+      El[off[q]] = v[q] - h;
+    }
+  }
+}
+
+int expand_thin_split(const float2* Y, long ldy, long sy, int K, int N, float* Eh, float* El, long lde, long se,
+                      int batch, int mode, cudaStream_t s) {
+  const long total = (long)batch * K * N;
+  if (total <= 0) return TSVD_OK;
+  const unsigned grid = std::min<long>(cdiv(total, 256), 8192);
+  k_expand_split<<<grid, 256, 0, s>>>(Y, ldy, sy, K, N, Eh, El, lde, se, batch, mode);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }

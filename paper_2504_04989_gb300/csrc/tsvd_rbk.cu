@@ -34,7 +34,8 @@ namespace tsvd {
 
 struct RbkDims {
   int n1, n2, n3, h, R, P, q, b, m;
-  int tc;    // basis-building products on tcgen05: 0 none, 1 TF32, 2 BF16
+  int tc;    // basis-building products on tcgen05 in one pass: 0 none, 1 TF32, 2 BF16
+  int tc3;   // FP32-accurate products on tcgen05 (split TF32): FP32 data unless TSVD_FLAG_SIMT
   int alg1;  // Alg. 1 (power iteration, last block only) instead of Alg. 2
 };
 
@@ -52,6 +53,8 @@ static int rbk_dims(int n1, int n2, int n3, const tsvd_params* p, RbkDims* d) {
   d->b = p->R + p->P;
   d->tc = (p->precision == TSVD_MIXED_TF32) ? 1 : (p->precision == TSVD_MIXED_BF16) ? 2 : 0;
   d->alg1 = (p->flags & TSVD_FLAG_ALG1) ? 1 : 0;
+  d->tc3 = (p->precision != TSVD_FP64 && !(p->flags & TSVD_FLAG_SIMT)) ? 1 : 0;
+  if (p->flags & TSVD_FLAG_SIMT) d->tc = 0;
   long m = (long)(d->alg1 ? 1 : p->q + 1) * d->b;
   m = std::min<long>(m, std::min(n1, n2));
   d->m = (int)m;
@@ -86,9 +89,14 @@ struct RbkWs {
   C* Vh;
   C* Sh;
   void* eig;
-  void* Aop;      // tcgen05 operand: X-hat as real rows of 2 n2 (TF32 = FP32 storage, or BF16), padded
-  long lda;
-  void* E;        // expanded real form of the thin right factor (2b x 2 n2 per slice)
+  void* Aop;      // one-pass BF16 operand: X-hat as real rows of 2 n2, padded
+  float* Ahi;     // split TF32 operands: X-hat as real rows (leading dim lda) ...
+  float* Alo;
+  float* AThi;    // ... and X-hat^T (per slice n2 x n1 complex) as real rows (leading dim ldt)
+  float* ATlo;
+  long lda, ldt;
+  float* Eh;      // expanded real forms of the thin factor (2b rows per slice, leading dim lde)
+  float* El;
   long lde;
   int* tc_err;    // set by a tcgen05 pipeline wait that timed out
   double2* splitk;
@@ -129,14 +137,20 @@ static RbkWs<T> carve_rbk(void* base, const RbkDims& d) {
   w.Sh = cv.take<C>(h * d.R);
   w.eig = cv.take<char>(eig_scratch_bytes(d.m, d.R, d.h));
   w.Aop = nullptr;
-  w.E = nullptr;
+  w.Ahi = w.Alo = w.AThi = w.ATlo = w.Eh = w.El = nullptr;
   w.tc_err = nullptr;
-  w.lda = w.lde = (2L * d.n2 + 7) / 8 * 8;
-  if (d.tc) {
-    const bool copy = d.tc == 2 || (2L * d.n2) % 4 != 0;
-    if (copy) w.Aop = cv.take<float>(h * d.n1 * w.lda);  // large enough for either element type
-    w.E = cv.take<float>(h * 2 * (size_t)d.b * w.lde);
+  w.lda = (2L * d.n2 + 7) / 8 * 8;
+  w.ldt = (2L * d.n1 + 7) / 8 * 8;
+  w.lde = std::max(w.lda, w.ldt);
+  if (d.tc3) {
+    w.Ahi = cv.take<float>(h * d.n1 * w.lda);
+    w.Alo = cv.take<float>(h * d.n1 * w.lda);
+    w.AThi = cv.take<float>(h * d.n2 * w.ldt);
+    w.ATlo = cv.take<float>(h * d.n2 * w.ldt);
+    w.Eh = cv.take<float>(h * 2 * (size_t)d.b * w.lde);
+    w.El = cv.take<float>(h * 2 * (size_t)d.b * w.lde);
     w.tc_err = cv.take<int>(4);
+    if (d.tc == 2) w.Aop = cv.take<uint16_t>(h * d.n1 * w.lda);
   }
   w.splitk_elems = 8 * h * (size_t)d.m * std::max(d.b, 64);
   w.splitk = cv.take<double2>(w.splitk_elems);
@@ -230,24 +244,50 @@ static int to_orth(const RbkWs<T>& w, const RbkDims& d, int cols, cudaStream_t s
 }
 
 // W (n1 x nb, leading dim b) = X-hat Y for the thin Y (n2 x nb, leading dim ldy):
-// on tcgen05 in the mixed precisions (X-hat seen as real n1 x 2n2 rows, Y as
-// its expanded real form), else the FP32 / FP64 SIMT GEMM.
+// on tcgen05 (one TF32 / BF16 pass in the mixed precisions, split TF32 on the
+// FP32 path; X-hat seen as real n1 x 2n2 rows, Y as its expanded real form),
+// else the SIMT GEMM.
 template <typename T>
 static int basis_product(const RbkDims& d, RbkWs<T>& w, const cx_t<T>* Y, long ldy, long sy, int nb, cudaStream_t s) {
   const int n1 = d.n1, n2 = d.n2, b = d.b, h = d.h;
-  const long sA = (long)n1 * n2, sW = (long)n1 * b;
+  const long sA = (long)n1 * n2, sW = (long)n1 * b, se = 2L * b * w.lde;
   if constexpr (std::is_same<T, float>::value) {
-    if (d.tc) {
-      const bool bf16 = d.tc == 2;
-      TSVD_TRY(expand_thin(Y, ldy, sy, n2, nb, w.E, w.lde, 2L * b * w.lde, h, 0, bf16, s));
-      const void* Aop = w.Aop ? w.Aop : (const void*)w.Ah;
-      const long lda = w.Aop ? w.lda : 2L * n2;
-      return tc_gemm(Aop, lda, (long)n1 * lda, n1, w.E, w.lde, 2L * b * w.lde, 2 * nb, 2 * n2, (float*)w.Wt, 2L * b,
-                     2L * sW, h, bf16, w.tc_err, s);
+    if (d.tc == 2) {
+      TSVD_TRY(expand_thin(Y, ldy, sy, n2, nb, w.Eh, w.lde, se, h, 0, true, s));
+      return tc_gemm(w.Aop, w.lda, (long)n1 * w.lda, n1, w.Eh, w.lde, se, 2 * nb, 2 * n2, (float*)w.Wt, 2L * b,
+                     2L * sW, h, true, w.tc_err, s);
+    }
+    if (d.tc == 1) {  // one TF32 pass on the TF32-rounded X-hat
+      TSVD_TRY(expand_thin(Y, ldy, sy, n2, nb, w.Eh, w.lde, se, h, 0, false, s));
+      return tc_gemm(w.Ahi, w.lda, (long)n1 * w.lda, n1, w.Eh, w.lde, se, 2 * nb, 2 * n2, (float*)w.Wt, 2L * b,
+                     2L * sW, h, false, w.tc_err, s);
+    }
+    if (d.tc3) {
+      TSVD_TRY(expand_thin_split(Y, ldy, sy, n2, nb, w.Eh, w.El, w.lde, se, h, 0, s));
+      return tc_gemm_split(w.Ahi, w.Alo, w.lda, (long)n1 * w.lda, n1, w.Eh, w.El, w.lde, se, 2 * nb, 2 * n2,
+                           (float*)w.Wt, 2L * b, 2L * sW, h, w.tc_err, s);
     }
   }
   return cgemm<cx_t<T>>(gemm('N', 'N', n1, nb, n2, 1.0, w.Ah, n2, sA, Y, ldy, sy, 0.0, w.Wt, b, sW, h), w.splitk,
                         w.splitk_elems * 2, s);
+}
+
+// columns [col0, col0 + nb) of C^H (n2 x m) = X-hat^H Q(:, col0 : col0 + nb): the
+// products that form C, so FP32 accuracy (split TF32 on tcgen05, or SIMT)
+template <typename T>
+static int conj_product(const RbkDims& d, RbkWs<T>& w, int col0, int nb, cudaStream_t s) {
+  const int n1 = d.n1, n2 = d.n2, m = d.m, b = d.b, h = d.h;
+  const long sA = (long)n1 * n2, sQ = (long)n1 * m, sCH = (long)n2 * m, se = 2L * b * w.lde;
+  if constexpr (std::is_same<T, float>::value) {
+    if (d.tc3) {
+      TSVD_TRY(expand_thin_split(w.Qt + col0, m, sQ, n1, nb, w.Eh, w.El, w.lde, se, h, 1, s));
+      return tc_gemm_split(w.AThi, w.ATlo, w.ldt, (long)n2 * w.ldt, n2, w.Eh, w.El, w.lde, se, 2 * nb, 2 * n1,
+                           (float*)(w.CHt + col0), 2L * m, 2L * sCH, h, w.tc_err, s);
+    }
+  }
+  return cgemm<cx_t<T>>(gemm('H', 'N', n2, nb, n1, 1.0, w.Ah, n2, sA, w.Qt + col0, m, sQ, 0.0, w.CHt + col0, m, sCH,
+                             h),
+                        w.splitk, w.splitk_elems * 2, s);
 }
 
 template <typename T, typename L>
@@ -256,7 +296,7 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
   using C = cx_t<T>;
   RbkWs<T> w = carve_rbk<T, L>(ws, d);
   const int n1 = d.n1, n2 = d.n2, n3 = d.n3, h = d.h, b = d.b, m = d.m, R = d.R;
-  const long sA = (long)n1 * n2, sQ = (long)n1 * m, sCH = (long)n2 * m, sO = (long)n2 * b;
+  const long sQ = (long)n1 * m, sCH = (long)n2 * m, sO = (long)n2 * b;
   if (cudaMemsetAsync(w.counters, 0, 8 * sizeof(int), s) != cudaSuccess) return TSVD_ERR_CUDA;
 
   // test tensor and data in the Fourier domain
@@ -272,16 +312,19 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
     TSVD_TRY(launch_rfft3<T>(A, w.Ah, (long)n1 * n2, n3, s));
   }
 
-  if (d.tc) {  // tensor-core operand of X-hat (BF16, or FP32 rows padded to 16 bytes)
-    TSVD_STAGE("krylov_gemm_tc", s);
+  if (d.tc3) {  // tensor-core operands of X-hat and X-hat^T (split TF32; BF16 copy for the BF16 path)
+    TSVD_STAGE("krylov_split", s);
     if (cudaMemsetAsync(w.tc_err, 0, sizeof(int), s) != cudaSuccess) return TSVD_ERR_CUDA;
-    if (w.Aop)
-      TSVD_TRY(copy_rows((const float*)w.Ah, 2L * n2, w.Aop, w.lda, 2 * n2, (long)h * n1, d.tc == 2, s));
+    if constexpr (std::is_same<T, float>::value) {
+      TSVD_TRY(split_rows((const float*)w.Ah, 2L * n2, w.Ahi, w.Alo, w.lda, 2 * n2, (long)h * n1, s));
+      TSVD_TRY(split_transpose((const float2*)w.Ah, n1, n2, h, w.AThi, w.ATlo, w.ldt, s));
+      if (d.tc == 2) TSVD_TRY(copy_rows((const float*)w.Ah, 2L * n2, w.Aop, w.lda, 2 * n2, (long)h * n1, true, s));
+    }
   }
   // block 0: W_0 = A Omega
   const int b0 = std::min(b, m);
   {
-    TSVD_STAGE(d.tc ? "krylov_gemm_tc" : "krylov_gemm", s);
+    TSVD_STAGE((d.tc || d.tc3) ? "krylov_gemm_tc" : "krylov_gemm", s);
     TSVD_TRY(basis_product<T>(d, w, w.Omh, b, sO, b0, s));
   }
   TSVD_TRY((to_orth<T, L>(w, d, b0, s)));
@@ -290,12 +333,11 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
   if (d.alg1) {  // Alg. 1: Q <- orth(A A^H Q), q times, in place
     for (int i = 1; i <= d.q; ++i) {
       {
-        TSVD_STAGE("krylov_gemm", s);
-        TSVD_TRY(cgemm<C>(gemm('H', 'N', n2, b0, n1, 1.0, w.Ah, n2, sA, w.Qt, m, sQ, 0.0, w.CHt, m, sCH, h), w.splitk,
-                          w.splitk_elems * 2, s));
+        TSVD_STAGE(d.tc3 ? "krylov_gemm_tc" : "krylov_gemm", s);
+        TSVD_TRY(conj_product<T>(d, w, 0, b0, s));
       }
       {
-        TSVD_STAGE(d.tc ? "krylov_gemm_tc" : "krylov_gemm", s);
+        TSVD_STAGE((d.tc || d.tc3) ? "krylov_gemm_tc" : "krylov_gemm", s);
         TSVD_TRY(basis_product<T>(d, w, w.CHt, m, sCH, b0, s));
       }
       TSVD_TRY((to_orth<T, L>(w, d, b0, s)));
@@ -305,15 +347,13 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
   for (int i = 1; !d.alg1 && i <= d.q && c < m; ++i) {
     const int bi = std::min(b, m - c);
     {
-    TSVD_STAGE("krylov_gemm", s);
+    TSVD_STAGE(d.tc3 ? "krylov_gemm_tc" : "krylov_gemm", s);
     // Y_i = A^H Q_{i-1}: the block of C^H that belongs to Q_{i-1}
-    TSVD_TRY(cgemm<C>(gemm('H', 'N', n2, pw, n1, 1.0, w.Ah, n2, sA, w.Qt + (c - pw), m, sQ, 0.0, w.CHt + (c - pw), m,
-                           sCH, h),
-                      w.splitk, w.splitk_elems * 2, s));
+    TSVD_TRY(conj_product<T>(d, w, c - pw, pw, s));
     }
     {
     // W_i = A Y_i (leading bi columns)
-    TSVD_STAGE(d.tc ? "krylov_gemm_tc" : "krylov_gemm", s);
+    TSVD_STAGE((d.tc || d.tc3) ? "krylov_gemm_tc" : "krylov_gemm", s);
     TSVD_TRY(basis_product<T>(d, w, w.CHt + (c - pw), m, sCH, bi, s));
     }
     TSVD_TRY((to_orth<T, L>(w, d, bi, s)));
@@ -323,10 +363,8 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
   }
   // last block of C^H = A^H Q_last
   {
-  TSVD_STAGE("krylov_gemm", s);
-  TSVD_TRY(cgemm<C>(gemm('H', 'N', n2, pw, n1, 1.0, w.Ah, n2, sA, w.Qt + (c - pw), m, sQ, 0.0, w.CHt + (c - pw), m,
-                         sCH, h),
-                    w.splitk, w.splitk_elems * 2, s));
+  TSVD_STAGE(d.tc3 ? "krylov_gemm_tc" : "krylov_gemm", s);
+  TSVD_TRY(conj_product<T>(d, w, c - pw, pw, s));
   }
 
   // G = C C^H in FP64 (FP64 path) or exactly in integers from the FP32 C^H, and its top-R eigenpairs

@@ -75,4 +75,7 @@ def test_error_of_rbk_output(api, orc, precision):
     s = sig.cpu().numpy()
     ident = np.sum(Xin ** 2) - np.sum(w[:, None] * s ** 2) / n3
     nx = np.sum(Xin ** 2)
-    assert abs(got - ident) <= (1e-12 if precision == "fp64" else 1e-6) * nx, (got, ident)
+    # FP32 path: the products forming C carry about 22 significant bits (split TF32 on the
+    # tensor cores), so the identity holds to ~2^-22 sqrt(n) relative; the sigma tolerance
+    # of the path (1e-4) would allow 2e-4
+    assert abs(got - ident) <= (1e-12 if precision == "fp64" else 1e-5) * nx, (got, ident)
