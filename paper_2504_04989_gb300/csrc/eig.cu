@@ -254,12 +254,12 @@ static size_t hetrd_smem_bytes(int m, int CL, int nt = HS_THREADS) {
 }
 
 // A pass of E elements is cut into contiguous segments of L elements (the
-// last one shorter), one per thread: L is odd and at least 9, so the
+// last one shorter), one per thread: L is odd and at least 5, so the
 // addresses of neighbouring lanes inside a row differ by an odd multiple of
 // 16 bytes and fall in different shared-memory bank groups.
 template <int NT>
 __device__ __forceinline__ int hs_seglen(int E) {
-  int L = max(9, E / NT) | 1;
+  int L = max(5, E / NT) | 1;
   while ((E + L - 1) / L > NT) L += 2;
   return L;
 }
@@ -625,35 +625,43 @@ __device__ __forceinline__ double2 cdf_to(cdf a) { return make_double2(df_to(cre
 __device__ __forceinline__ cdf cdf_zero() { return cdf{0.f, 0.f, 0.f, 0.f}; }
 __device__ __forceinline__ cdf cdf_add(cdf a, cdf b) { return cdf_make(df_add(cre(a), cre(b)), df_add(cim(a), cim(b))); }
 // acc += a b
+// a + sum_i x_i y_i with one renormalisation at the end: each exact product
+// (TwoProduct by FMA plus the two cross terms) is added to the running high
+// part by TwoSum and every rounding error goes to one low accumulator (the
+// compensated dot product of Ogita, Rump and Oishi in double-float form).
+template <int N>
+__device__ __forceinline__ dfl df_dot(dfl a, const dfl (&x)[N], const dfl (&y)[N]) {
+  float s = a.hi, e = a.lo;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const float p = x[i].hi * y[i].hi;
+    float pe = fmaf(x[i].hi, y[i].hi, -p);
+    pe = fmaf(x[i].hi, y[i].lo, fmaf(x[i].lo, y[i].hi, pe));
+    const float t = s + p, bb = t - s;
+    e += ((s - (t - bb)) + (p - bb)) + pe;
+    s = t;
+  }
+  return df_fast_two_sum(s, e);
+}
+// acc += a b
 __device__ __forceinline__ void cdf_fma(cdf& acc, cdf a, cdf b) {
-  dfl r = cre(acc), i = cim(acc);
-  r = df_fma(r, cre(a), cre(b));
-  r = df_fma(r, df_neg(cim(a)), cim(b));
-  i = df_fma(i, cre(a), cim(b));
-  i = df_fma(i, cim(a), cre(b));
-  acc = cdf_make(r, i);
+  const dfl xr[2] = {cre(a), df_neg(cim(a))}, yr[2] = {cre(b), cim(b)};
+  const dfl xi[2] = {cre(a), cim(a)}, yi[2] = {cim(b), cre(b)};
+  acc = cdf_make(df_dot<2>(cre(acc), xr, yr), df_dot<2>(cim(acc), xi, yi));
 }
 // acc += conj(a) b
 __device__ __forceinline__ void cdf_fmac(cdf& acc, cdf a, cdf b) {
-  dfl r = cre(acc), i = cim(acc);
-  r = df_fma(r, cre(a), cre(b));
-  r = df_fma(r, cim(a), cim(b));
-  i = df_fma(i, cre(a), cim(b));
-  i = df_fma(i, df_neg(cim(a)), cre(b));
-  acc = cdf_make(r, i);
+  const dfl xr[2] = {cre(a), cim(a)}, yr[2] = {cre(b), cim(b)};
+  const dfl xi[2] = {cre(a), df_neg(cim(a))}, yi[2] = {cim(b), cre(b)};
+  acc = cdf_make(df_dot<2>(cre(acc), xr, yr), df_dot<2>(cim(acc), xi, yi));
 }
 // a - vg conj(wk) - wg conj(vk)
 __device__ __forceinline__ cdf cdf_lag(cdf a, cdf vg, cdf wg, cdf vk, cdf wk) {
-  dfl r = cre(a), i = cim(a);
-  r = df_fma(r, df_neg(cre(vg)), cre(wk));
-  r = df_fma(r, df_neg(cim(vg)), cim(wk));
-  r = df_fma(r, df_neg(cre(wg)), cre(vk));
-  r = df_fma(r, df_neg(cim(wg)), cim(vk));
-  i = df_fma(i, df_neg(cim(vg)), cre(wk));
-  i = df_fma(i, cre(vg), cim(wk));
-  i = df_fma(i, df_neg(cim(wg)), cre(vk));
-  i = df_fma(i, cre(wg), cim(vk));
-  return cdf_make(r, i);
+  const dfl xr[4] = {df_neg(cre(vg)), df_neg(cim(vg)), df_neg(cre(wg)), df_neg(cim(wg))};
+  const dfl yr[4] = {cre(wk), cim(wk), cre(vk), cim(vk)};
+  const dfl xi[4] = {df_neg(cim(vg)), cre(vg), df_neg(cim(wg)), cre(wg)};
+  const dfl yi[4] = {cre(wk), cim(wk), cre(vk), cim(vk)};
+  return cdf_make(df_dot<4>(cre(a), xr, yr), df_dot<4>(cim(a), xi, yi));
 }
 // x * s for a real double-float s
 __device__ __forceinline__ cdf cdf_scale(cdf x, dfl s) {
