@@ -131,7 +131,7 @@ template <typename C>
 constexpr int ts_rows() { return 4; }
 constexpr int TS_WARPS = 8;
 
-template <typename C>
+template <typename C, int NU>  // NU = ceil(nb / 32) column slots per lane
 __global__ void __launch_bounds__(TS_WARPS * 32) k_trsm_right_upper(C* __restrict__ W, long ldw, long sW,
                                                                    const double2* __restrict__ Rm, long ldr, long sR,
                                                                    int n1, int nb, const uint32_t* __restrict__ dead) {
@@ -163,16 +163,16 @@ __global__ void __launch_bounds__(TS_WARPS * 32) k_trsm_right_upper(C* __restric
   constexpr int TS_ROWS = ts_rows<C>();
   const int r0 = (blockIdx.x * TS_WARPS + warp) * TS_ROWS;
   if (r0 >= n1) return;
-  C x[TS_ROWS][4];
+  C x[TS_ROWS][NU];
 #pragma unroll
   for (int r = 0; r < TS_ROWS; ++r)
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < NU; ++u) {
       const int k = lane + 32 * u;
       x[r][u] = (r0 + r < n1 && k < nb) ? W[(long)(r0 + r) * ldw + k] : C{R(0), R(0)};
     }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < NU; ++u) {
     for (int jj = 0; jj < 32; ++jj) {
       const int j = 32 * u + jj;
       if (j >= nb) break;
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(TS_WARPS * 32) k_trsm_right_upper(C* __restric
         if (lane == jj) x[r][u] = xj[r];
       }
 #pragma unroll
-      for (int v = u; v < 4; ++v) {
+      for (int v = u; v < NU; ++v) {
         const int k = lane + 32 * v;
         if (k > j && k < nb) {
           const C rjk = Rp[offj + (k - j)];
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(TS_WARPS * 32) k_trsm_right_upper(C* __restric
 #pragma unroll
   for (int r = 0; r < TS_ROWS; ++r)
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < NU; ++u) {
       const int k = lane + 32 * u;
       if (r0 + r < n1 && k < nb) W[(long)(r0 + r) * ldw + k] = x[r][u];
     }
@@ -214,16 +214,23 @@ int trsm_right_upper(C* W, long ldw, long sW, const double2* Rm, long ldr, long 
   if (nb <= 0 || n1 <= 0 || batch <= 0) return TSVD_OK;
   if (nb > 128) return TSVD_ERR_UNSUPPORTED;
   const size_t smem = (size_t)nb * (nb + 1) / 2 * sizeof(C);
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(k_trsm_right_upper<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess) {
-    cudaGetLastError();
-    return TSVD_ERR_CUDA;
-  }
   dim3 grid(cdiv(n1, ts_rows<C>() * TS_WARPS), batch);
-  k_trsm_right_upper<C><<<grid, TS_WARPS * 32, smem, s>>>(W, ldw, sW, Rm, ldr, sR, n1, nb, dead);
-  TSVD_LAUNCHED();
-  return TSVD_OK;
+  auto go = [&](auto kern) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return TSVD_ERR_CUDA;
+    }
+    kern<<<grid, TS_WARPS * 32, smem, s>>>(W, ldw, sW, Rm, ldr, sR, n1, nb, dead);
+    TSVD_LAUNCHED();
+    return TSVD_OK;
+  };
+  switch ((nb + 31) / 32) {
+    case 1: return go(k_trsm_right_upper<C, 1>);
+    case 2: return go(k_trsm_right_upper<C, 2>);
+    case 3: return go(k_trsm_right_upper<C, 3>);
+    default: return go(k_trsm_right_upper<C, 4>);
+  }
 }
 template int trsm_right_upper<double2>(double2*, long, long, const double2*, long, long, int, int, int,
                                        const uint32_t*, cudaStream_t);
