@@ -1273,42 +1273,61 @@ __global__ void __launch_bounds__(TP_THREADS) k_tridiag_pairs(int m, int R, EigS
 // Inside clusters of close eigenvalues (gap < 1e-3 ||T||) the vectors are
 // made orthonormal: two classical Gram-Schmidt passes against the earlier
 // members of the cluster, then normalisation.
-__global__ void __launch_bounds__(256) k_cluster_orth(int m, int R, EigScratch e, const double* __restrict__ lam) {
+// CT: arithmetic of the two Gram-Schmidt passes (FP32 on the FP32 path, whose
+// vectors are rounded to FP32 right after; FP64 otherwise).  The slice's R
+// vectors are staged in shared memory for the whole kernel (the passes are a
+// chain of short dependent steps, so every operand should be one shared-memory
+// access away); one warp per dot product.
+constexpr int CO_THREADS = 1024;
+template <typename CT, bool STAGED>  // !STAGED (vectors too large for shared memory): CT = double, in place in Z
+__global__ void __launch_bounds__(CO_THREADS) k_cluster_orth(int m, int R, EigScratch e, const double* __restrict__ lam) {
+  extern __shared__ __align__(16) unsigned char cosm[];
   __shared__ double red[32];
-  __shared__ double dots[128];
+  __shared__ CT dots[128];
   const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   double* Z = e.Z + (long)b * R * m;  // vector r at Z + r*m
   const double* l = lam + (long)b * R;
   const double tol = 1e-3 * e.tnorm[b];
+  // only vectors inside a cluster change; find whether there is any
+  bool any = false;
+  for (int r = 1; r < R; ++r) any |= !(l[r - 1] - l[r] > tol);
+  if (!any) return;
+  CT* zsm = STAGED ? (CT*)cosm : (CT*)Z;  // [R][m]
+  if (STAGED) {
+    for (int q = tid; q < R * m; q += blockDim.x) zsm[q] = (CT)Z[q];
+    __syncthreads();
+  }
   int c0 = 0;
   for (int r = 1; r < R; ++r) {
     if (l[r - 1] - l[r] > tol) {
       c0 = r;
       continue;
     }
-    double* zr = Z + (long)r * m;
+    CT* zr = zsm + (long)r * m;
     for (int pass = 0; pass < 2; ++pass) {
       for (int s = c0 + warp; s < r; s += nwarp) {
-        const double* zs = Z + (long)s * m;
-        double acc = 0;
+        const CT* zs = zsm + (long)s * m;
+        CT acc = 0;
         for (int i = lane; i < m; i += 32) acc += zs[i] * zr[i];
         acc = warp_sum(acc);
         if (lane == 0) dots[s - c0] = acc;
       }
       __syncthreads();
       for (int i = tid; i < m; i += blockDim.x) {
-        double acc = zr[i];
-        for (int s = c0; s < r; ++s) acc -= dots[s - c0] * Z[(long)s * m + i];
+        CT acc = zr[i];
+        for (int s = c0; s < r; ++s) acc -= dots[s - c0] * zsm[(long)s * m + i];
         zr[i] = acc;
       }
       __syncthreads();
     }
     double part = 0;
-    for (int i = tid; i < m; i += blockDim.x) part += zr[i] * zr[i];
-    const double nrm = sqrt(block_sum(part, red));
-    for (int i = tid; i < m; i += blockDim.x) zr[i] /= nrm;
+    for (int i = tid; i < m; i += blockDim.x) part += (double)zr[i] * (double)zr[i];
+    const CT inv = (CT)(1.0 / sqrt(block_sum(part, red)));
+    for (int i = tid; i < m; i += blockDim.x) zr[i] *= inv;
     __syncthreads();
   }
+  if (STAGED)
+    for (int q = tid; q < R * m; q += blockDim.x) Z[q] = (double)zsm[q];
 }
 
 // u_r = H_0 H_1 .. H_{m-2} D z_r, one warp per eigenvector, in the precision
@@ -1480,7 +1499,19 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
   }
   {
     TSVD_STAGE("eig_cluster", s);
-    k_cluster_orth<<<batch, 256, 0, s>>>(m, R, e, lam);
+    size_t smem_co = (size_t)R * m * (kDoubleFloat ? sizeof(float) : sizeof(double));
+    using CoKernel = void (*)(int, int, EigScratch, const double*);
+    CoKernel co = kDoubleFloat ? (CoKernel)k_cluster_orth<float, true> : (CoKernel)k_cluster_orth<double, true>;
+    if (smem_co > 200 * 1024) {  // vectors stay in global memory
+      co = k_cluster_orth<double, false>;
+      smem_co = 0;
+    }
+    if (smem_co > 48 * 1024 && cudaFuncSetAttribute(co, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_co) !=
+                                   cudaSuccess) {
+      cudaGetLastError();
+      return TSVD_ERR_CUDA;
+    }
+    co<<<batch, CO_THREADS, smem_co, s>>>(m, R, e, lam);
     TSVD_LAUNCHED();
   }
   TSVD_STAGE("eig_backtransform", s);
