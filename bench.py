@@ -37,7 +37,7 @@ DF_PEAK_TFLOPS = FP32_ISSUE_TINST / DF_FMA_INSTR * 2         # 5.37 (FP64-accura
 # DRAM bytes per launch of the dominant kernel from the committed ncu capture of
 # the same kernel and workload (profiles/k_hetrd_df_512x512x64_fp32.md); None
 # once the kernel changes.
-NCU_TRAFFIC = {"eig_hetrd": None}
+NCU_TRAFFIC = {"eig_hetrd": 24.80e6}
 
 
 def peaks():
