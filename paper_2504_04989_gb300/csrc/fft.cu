@@ -131,12 +131,14 @@ constexpr int FFT_LOADS = 8;
 constexpr int FFT_MAXR = 24;
 struct FftPlan {
   int n, nr, tubes;
+  int seqs;  // sequences a warp transforms together (every pass has seqs * n / R independent butterflies)
   int radix[FFT_MAXR];
 };
 
 static bool make_plan(int n, FftPlan* p) {
   p->n = n;
   p->nr = 0;
+  p->seqs = std::max(1, std::min(4, 256 / std::max(n, 1)));
   int m = n;
   while (m % 4 == 0) { p->radix[p->nr++] = 4; m /= 4; }
   while (m % 2 == 0) { p->radix[p->nr++] = 2; m /= 2; }
@@ -152,10 +154,13 @@ static bool make_plan(int n, FftPlan* p) {
 
 // one Stockham pass of radix R (sign of the exponent in tw): in -> out
 template <typename C, int R>
-__device__ __forceinline__ void fft_pass_fixed(const C* __restrict__ in, C* __restrict__ out, const C* __restrict__ tw,
-                                               int n, int Ns, int lane) {
+__device__ __forceinline__ void fft_pass_fixed(const C* __restrict__ in0, C* __restrict__ out0,
+                                               const C* __restrict__ tw, int n, int Ns, int lane, int nseq) {
   const int nR = n / R, tstep = n / (Ns * R);
-  for (int j = lane; j < nR; j += 32) {
+  for (int jj = lane; jj < nseq * nR; jj += 32) {
+    const int sq = jj / nR, j = jj - sq * nR;
+    const C* __restrict__ in = in0 + sq * n;
+    C* __restrict__ out = out0 + sq * n;
     const int k = j % Ns;
     C v[R];
 #pragma unroll
@@ -192,10 +197,13 @@ __device__ __forceinline__ void fft_pass_fixed(const C* __restrict__ in, C* __re
 }
 
 template <typename C>
-__device__ void fft_pass_generic(const C* __restrict__ in, C* __restrict__ out, const C* __restrict__ tw, int n, int Ns,
-                                 int R, int lane) {
+__device__ void fft_pass_generic(const C* __restrict__ in0, C* __restrict__ out0, const C* __restrict__ tw, int n,
+                                 int Ns, int R, int lane, int nseq) {
   const int nR = n / R, tstep = n / (Ns * R);
-  for (int j = lane; j < nR; j += 32) {
+  for (int jj = lane; jj < nseq * nR; jj += 32) {
+    const int sq = jj / nR, j = jj - sq * nR;
+    const C* __restrict__ in = in0 + sq * n;
+    C* __restrict__ out = out0 + sq * n;
     const int k = j % Ns;
     const int idxD = (j / Ns) * Ns * R + k;
     for (int q = 0; q < R; ++q) {
@@ -209,17 +217,18 @@ __device__ void fft_pass_generic(const C* __restrict__ in, C* __restrict__ out, 
   }
 }
 
-// in-place (ping-pong) FFT of a length-n sequence in a / b; returns the buffer holding the result
+// in-place (ping-pong) FFT of nseq length-n sequences (stride n) in a / b;
+// returns the buffer holding the result
 template <typename C>
-__device__ C* fft_run(C* a, C* b, const C* tw, const FftPlan& P, int lane) {
+__device__ C* fft_run(C* a, C* b, const C* tw, const FftPlan& P, int lane, int nseq) {
   int Ns = 1;
   for (int s = 0; s < P.nr; ++s) {
     const int R = P.radix[s];
-    if (R == 4) fft_pass_fixed<C, 4>(a, b, tw, P.n, Ns, lane);
-    else if (R == 2) fft_pass_fixed<C, 2>(a, b, tw, P.n, Ns, lane);
-    else if (R == 3) fft_pass_fixed<C, 3>(a, b, tw, P.n, Ns, lane);
-    else if (R == 5) fft_pass_fixed<C, 5>(a, b, tw, P.n, Ns, lane);
-    else fft_pass_generic<C>(a, b, tw, P.n, Ns, R, lane);
+    if (R == 4) fft_pass_fixed<C, 4>(a, b, tw, P.n, Ns, lane, nseq);
+    else if (R == 2) fft_pass_fixed<C, 2>(a, b, tw, P.n, Ns, lane, nseq);
+    else if (R == 3) fft_pass_fixed<C, 3>(a, b, tw, P.n, Ns, lane, nseq);
+    else if (R == 5) fft_pass_fixed<C, 5>(a, b, tw, P.n, Ns, lane, nseq);
+    else fft_pass_generic<C>(a, b, tw, P.n, Ns, R, lane, nseq);
     __syncwarp();
     C* t = a;
     a = b;
@@ -236,9 +245,9 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_rfft3_fft(const T* __restric
   extern __shared__ __align__(16) unsigned char fsm[];
   const int n = P.n, h = n / 2 + 1, TT = P.tubes;
   C* tw = (C*)fsm;                                  // [n]
-  C* zb = tw + n;                                   // [FFT_WARPS][2][n]
+  C* zb = tw + n;                                   // [FFT_WARPS][2][seqs][n]
   const int LD = TT + 1;                            // padded row stride: conflict-free column walks
-  C* otile = zb + (size_t)FFT_WARPS * 2 * n;        // [h][LD] complex
+  C* otile = zb + (size_t)FFT_WARPS * 2 * P.seqs * n;  // [h][LD] complex
   T* itile = (T*)(otile + (size_t)h * LD);          // [n][LD] real
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long e0 = (long)blockIdx.x * TT;
@@ -263,15 +272,21 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_rfft3_fft(const T* __restric
     }
   }
   __syncthreads();
-  C* za = zb + (size_t)warp * 2 * n;
-  C* zc = za + n;
+  const int B = P.seqs;
+  C* za = zb + (size_t)warp * 2 * B * n;
+  C* zc = za + (size_t)B * n;
   const T hf = T(0.5);
-  for (int s = warp; s < TT / 2; s += FFT_WARPS) {
-    for (int t = lane; t < n; t += 32) za[t] = mkc(itile[t * LD + 2 * s], itile[t * LD + 2 * s + 1]);
+  for (int s0 = warp * B; s0 < TT / 2; s0 += FFT_WARPS * B) {
+    const int nseq = min(B, TT / 2 - s0);
+    for (int q = lane; q < nseq * n; q += 32) {
+      const int sq = q / n, t = q - sq * n, s = s0 + sq;
+      za[q] = mkc(itile[t * LD + 2 * s], itile[t * LD + 2 * s + 1]);
+    }
     __syncwarp();
-    const C* Z = fft_run<C>(za, zc, tw, P, lane);
-    for (int k = lane; k < h; k += 32) {
-      const C zk = Z[k], zn = Z[(n - k) % n];
+    const C* Z = fft_run<C>(za, zc, tw, P, lane, nseq);
+    for (int q = lane; q < nseq * h; q += 32) {
+      const int sq = q / h, k = q - sq * h, s = s0 + sq;
+      const C zk = Z[sq * n + k], zn = Z[sq * n + (n - k) % n];
       otile[k * LD + 2 * s] = mkc(hf * (zk.x + zn.x), hf * (zk.y - zn.y));      // X_k
       otile[k * LD + 2 * s + 1] = mkc(hf * (zk.y + zn.y), hf * (zn.x - zk.x));  // Y_k
     }
@@ -292,9 +307,9 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_irfft3_fft(const cx_t<T>* __
   extern __shared__ __align__(16) unsigned char fsm[];
   const int n = P.n, h = n / 2 + 1, TT = P.tubes;
   C* tw = (C*)fsm;                                  // [n]
-  C* zb = tw + n;                                   // [FFT_WARPS][2][n]
+  C* zb = tw + n;                                   // [FFT_WARPS][2][seqs][n]
   const int LD = TT + 1;                            // padded row stride: conflict-free column walks
-  C* itile = zb + (size_t)FFT_WARPS * 2 * n;        // [h][LD] complex
+  C* itile = zb + (size_t)FFT_WARPS * 2 * P.seqs * n;  // [h][LD] complex
   T* otile = (T*)(itile + (size_t)h * LD);          // [n][LD] real
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long e0 = (long)blockIdx.x * TT;
@@ -320,11 +335,14 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_irfft3_fft(const cx_t<T>* __
     }
   }
   __syncthreads();
-  C* za = zb + (size_t)warp * 2 * n;
-  C* zc = za + n;
+  const int B = P.seqs;
+  C* za = zb + (size_t)warp * 2 * B * n;
+  C* zc = za + (size_t)B * n;
   const T inv = T(1) / T(n);
-  for (int s = warp; s < TT / 2; s += FFT_WARPS) {
-    for (int k = lane; k < n; k += 32) {
+  for (int s0 = warp * B; s0 < TT / 2; s0 += FFT_WARPS * B) {
+    const int nseq = min(B, TT / 2 - s0);
+    for (int q = lane; q < nseq * n; q += 32) {
+      const int sq = q / n, k = q - sq * n, s = s0 + sq;
       C x, y;
       if (k < h) {
         x = itile[k * LD + 2 * s];
@@ -333,13 +351,14 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_irfft3_fft(const cx_t<T>* __
         x = cconj(itile[(n - k) * LD + 2 * s]);
         y = cconj(itile[(n - k) * LD + 2 * s + 1]);
       }
-      za[k] = mkc(x.x - y.y, x.y + y.x);  // Z = X + i Y
+      za[q] = mkc(x.x - y.y, x.y + y.x);  // Z = X + i Y
     }
     __syncwarp();
-    const C* z = fft_run<C>(za, zc, tw, P, lane);
-    for (int t = lane; t < n; t += 32) {
-      otile[t * LD + 2 * s] = z[t].x * inv;
-      otile[t * LD + 2 * s + 1] = z[t].y * inv;
+    const C* z = fft_run<C>(za, zc, tw, P, lane, nseq);
+    for (int q = lane; q < nseq * n; q += 32) {
+      const int sq = q / n, t = q - sq * n, s = s0 + sq;
+      otile[t * LD + 2 * s] = z[q].x * inv;
+      otile[t * LD + 2 * s + 1] = z[q].y * inv;
     }
     __syncwarp();
   }
@@ -353,9 +372,9 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_irfft3_fft(const cx_t<T>* __
 
 // shared bytes of the FFT kernels for tile width tt (0 when the plan does not exist)
 template <typename T>
-static size_t fft_smem(int n, int tt) {
+static size_t fft_smem(int n, int tt, int seqs) {
   const int h = n / 2 + 1;
-  return sizeof(cx_t<T>) * ((size_t)n + (size_t)FFT_WARPS * 2 * n + (size_t)h * (tt + 1)) +
+  return sizeof(cx_t<T>) * ((size_t)n + (size_t)FFT_WARPS * 2 * seqs * n + (size_t)h * (tt + 1)) +
          sizeof(T) * (size_t)n * (tt + 1);
 }
 
@@ -363,7 +382,7 @@ template <typename T>
 static bool fft_setup(int n, FftPlan* P, size_t* smem) {
   if (!make_plan(n, P)) return false;
   for (int tt = 64; tt >= 16; tt >>= 1) {
-    const size_t b = fft_smem<T>(n, tt);
+    const size_t b = fft_smem<T>(n, tt, P->seqs);
     if (b <= 110 * 1024) {
       P->tubes = tt;
       *smem = b;

@@ -337,17 +337,25 @@ __device__ __forceinline__ __nv_bfloat16 cvt_out<__nv_bfloat16>(float v) {
   return __float2bfloat16_rn(v);
 }
 
+// 32 x 32 tiles of Y (k rows x n columns) through shared memory: reads
+// coalesced along n (Y's rows), writes coalesced along k (E's rows).
 template <typename O>
-__global__ void k_expand(const float2* __restrict__ Y, long ldy, long sy, int K, int N, O* __restrict__ E, long lde,
-                         long se, int batch, int mode) {
-  const long total = (long)batch * K * N;
-  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-    const int k = idx % K;  // k fastest: consecutive threads write consecutive columns of E
-    const long t = idx / K;
-    const int n = t % N;
-    const int b = t / N;
-    const float2 y = Y[(long)b * sy + (long)k * ldy + n];
-    O* e0 = E + (long)b * se + (long)(2 * n) * lde + 2 * k;
+__global__ void __launch_bounds__(256) k_expand(const float2* __restrict__ Y, long ldy, long sy, int K, int N,
+                                                O* __restrict__ E, long lde, long se, int mode) {
+  __shared__ float2 t[32][33];
+  const int b = blockIdx.z, k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  const float2* Yb = Y + (long)b * sy;
+  for (int kk = threadIdx.y; kk < 32; kk += blockDim.y) {
+    const int k = k0 + kk, n = n0 + threadIdx.x;
+    t[kk][threadIdx.x] = (k < K && n < N) ? Yb[(long)k * ldy + n] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  O* Eb = E + (long)b * se;
+  for (int nn = threadIdx.y; nn < 32; nn += blockDim.y) {
+    const int n = n0 + nn, k = k0 + threadIdx.x;
+    if (n >= N || k >= K) continue;
+    const float2 y = t[threadIdx.x][nn];
+    O* e0 = Eb + (long)(2 * n) * lde + 2 * k;
     O* e1 = e0 + lde;
     if (mode == 0) {
       e0[0] = cvt_out<O>(y.x);
@@ -365,13 +373,13 @@ __global__ void k_expand(const float2* __restrict__ Y, long ldy, long sy, int K,
 
 int expand_thin(const float2* Y, long ldy, long sy, int K, int N, void* E, long lde, long se, int batch, int mode,
                 bool bf16, cudaStream_t s) {
-  const long total = (long)batch * K * N;
-  if (total <= 0) return TSVD_OK;
-  const unsigned grid = std::min<long>(cdiv(total, 256), 8192);
+  if ((long)batch * K * N <= 0) return TSVD_OK;
+  if (batch > 65535 || cdiv(K, 32) > 65535) return TSVD_ERR_UNSUPPORTED;
+  dim3 grid(cdiv(N, 32), cdiv(K, 32), batch), block(32, 8);
   if (bf16)
-    k_expand<__nv_bfloat16><<<grid, 256, 0, s>>>(Y, ldy, sy, K, N, (__nv_bfloat16*)E, lde, se, batch, mode);
+    k_expand<__nv_bfloat16><<<grid, block, 0, s>>>(Y, ldy, sy, K, N, (__nv_bfloat16*)E, lde, se, mode);
   else
-    k_expand<float><<<grid, 256, 0, s>>>(Y, ldy, sy, K, N, (float*)E, lde, se, batch, mode);
+    k_expand<float><<<grid, block, 0, s>>>(Y, ldy, sy, K, N, (float*)E, lde, se, mode);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }
@@ -476,16 +484,22 @@ int split_transpose(const float2* X, int rows, int cols, int batch, float* hi, f
   return TSVD_OK;
 }
 
-// expanded real form (as expand_thin, FP32) split into hi / lo
-__global__ void k_expand_split(const float2* __restrict__ Y, long ldy, long sy, int K, int N, float* __restrict__ Eh,
-                               float* __restrict__ El, long lde, long se, int batch, int mode) {
-  const long total = (long)batch * K * N;
-  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-    const int k = idx % K;
-    const long t = idx / K;
-    const int n = t % N;
-    const int b = t / N;
-    const float2 y = Y[(long)b * sy + (long)k * ldy + n];
+// expanded real form (as expand_thin, FP32) split into hi / lo; same tiling
+__global__ void __launch_bounds__(256) k_expand_split(const float2* __restrict__ Y, long ldy, long sy, int K, int N,
+                                                      float* __restrict__ Eh, float* __restrict__ El, long lde,
+                                                      long se, int mode) {
+  __shared__ float2 t[32][33];
+  const int b = blockIdx.z, k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  const float2* Yb = Y + (long)b * sy;
+  for (int kk = threadIdx.y; kk < 32; kk += blockDim.y) {
+    const int k = k0 + kk, n = n0 + threadIdx.x;
+    t[kk][threadIdx.x] = (k < K && n < N) ? Yb[(long)k * ldy + n] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int nn = threadIdx.y; nn < 32; nn += blockDim.y) {
+    const int n = n0 + nn, k = k0 + threadIdx.x;
+    if (n >= N || k >= K) continue;
+    const float2 y = t[threadIdx.x][nn];
     const float v[4] = {y.x, mode == 0 ? -y.y : y.y, y.y, mode == 0 ? y.x : -y.x};
     const long o0 = (long)b * se + (long)(2 * n) * lde + 2 * k;
     const long off[4] = {o0, o0 + 1, o0 + lde, o0 + lde + 1};
@@ -500,10 +514,10 @@ __global__ void k_expand_split(const float2* __restrict__ Y, long ldy, long sy, 
 
 int expand_thin_split(const float2* Y, long ldy, long sy, int K, int N, float* Eh, float* El, long lde, long se,
                       int batch, int mode, cudaStream_t s) {
-  const long total = (long)batch * K * N;
-  if (total <= 0) return TSVD_OK;
-  const unsigned grid = std::min<long>(cdiv(total, 256), 8192);
-  k_expand_split<<<grid, 256, 0, s>>>(Y, ldy, sy, K, N, Eh, El, lde, se, batch, mode);
+  if ((long)batch * K * N <= 0) return TSVD_OK;
+  if (batch > 65535 || cdiv(K, 32) > 65535) return TSVD_ERR_UNSUPPORTED;
+  dim3 grid(cdiv(N, 32), cdiv(K, 32), batch), block(32, 8);
+  k_expand_split<<<grid, block, 0, s>>>(Y, ldy, sy, K, N, Eh, El, lde, se, mode);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }
