@@ -129,6 +129,8 @@ static int tile_e(int n3, size_t elem, size_t celem, bool inverse) {
 constexpr int FFT_WARPS = 8;
 constexpr int FFT_LOADS = 8;
 constexpr int FFT_MAXR = 24;
+// sequences a warp transforms together
+constexpr int fft_seqs(int n) { return n < 1 ? 1 : (256 / n < 1 ? 1 : (256 / n > 4 ? 4 : 256 / n)); }
 struct FftPlan {
   int n, nr, tubes;
   int seqs;  // sequences a warp transforms together (every pass has seqs * n / R independent butterflies)
@@ -138,7 +140,7 @@ struct FftPlan {
 static bool make_plan(int n, FftPlan* p) {
   p->n = n;
   p->nr = 0;
-  p->seqs = std::max(1, std::min(4, 256 / std::max(n, 1)));
+  p->seqs = fft_seqs(n);
   int m = n;
   while (m % 4 == 0) { p->radix[p->nr++] = 4; m /= 4; }
   while (m % 2 == 0) { p->radix[p->nr++] = 2; m /= 2; }
@@ -238,16 +240,42 @@ __device__ C* fft_run(C* a, C* b, const C* tw, const FftPlan& P, int lane, int n
   return a;
 }
 
+// The same transform for a length known at compile time (powers of two up to
+// 128): the pass sequence (radix 4 while possible, then 2, as make_plan) is
+// unrolled and every index division and modulus becomes a shift or a mask.
+template <typename C, int N, int NS>
+__device__ __forceinline__ C* fft_run_c(C* a, C* b, const C* tw, int lane, int nseq) {
+  if constexpr (NS >= N) {
+    return a;
+  } else {
+    constexpr int R = ((N / NS) % 4 == 0) ? 4 : 2;
+    fft_pass_fixed<C, R>(a, b, tw, N, NS, lane, nseq);
+    __syncwarp();
+    return fft_run_c<C, N, NS * R>(b, a, tw, lane, nseq);
+  }
+}
+
 template <typename T>
+constexpr size_t fft_smem_c(int n, int tt) {
+  return sizeof(cx_t<T>) * ((size_t)n + (size_t)FFT_WARPS * 2 * fft_seqs(n) * n + (size_t)(n / 2 + 1) * (tt + 1)) +
+         sizeof(T) * (size_t)n * (tt + 1);
+}
+// tubes per CTA: the widest tile that fits (the choice fft_setup makes at run time)
+template <typename T>
+constexpr int fft_tt(int n) {
+  return fft_smem_c<T>(n, 64) <= 110 * 1024 ? 64 : (fft_smem_c<T>(n, 32) <= 110 * 1024 ? 32 : 16);
+}
+
+template <typename T, int NC>  // NC: compile-time length (0: the plan's)
 __global__ void __launch_bounds__(FFT_WARPS * 32) k_rfft3_fft(const T* __restrict__ X, cx_t<T>* __restrict__ Xh,
                                                               long plane, FftPlan P) {
   using C = cx_t<T>;
   extern __shared__ __align__(16) unsigned char fsm[];
-  const int n = P.n, h = n / 2 + 1, TT = P.tubes;
+  const int n = NC ? NC : P.n, h = n / 2 + 1, TT = NC ? fft_tt<T>(NC) : P.tubes;
   C* tw = (C*)fsm;                                  // [n]
   C* zb = tw + n;                                   // [FFT_WARPS][2][seqs][n]
   const int LD = TT + 1;                            // padded row stride: conflict-free column walks
-  C* otile = zb + (size_t)FFT_WARPS * 2 * P.seqs * n;  // [h][LD] complex
+  C* otile = zb + (size_t)FFT_WARPS * 2 * (NC ? fft_seqs(NC) : P.seqs) * n;  // [h][LD] complex
   T* itile = (T*)(otile + (size_t)h * LD);          // [n][LD] real
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long e0 = (long)blockIdx.x * TT;
@@ -272,7 +300,7 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_rfft3_fft(const T* __restric
     }
   }
   __syncthreads();
-  const int B = P.seqs;
+  const int B = NC ? fft_seqs(NC) : P.seqs;
   C* za = zb + (size_t)warp * 2 * B * n;
   C* zc = za + (size_t)B * n;
   const T hf = T(0.5);
@@ -283,7 +311,9 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_rfft3_fft(const T* __restric
       za[q] = mkc(itile[t * LD + 2 * s], itile[t * LD + 2 * s + 1]);
     }
     __syncwarp();
-    const C* Z = fft_run<C>(za, zc, tw, P, lane, nseq);
+    const C* Z;
+    if constexpr (NC > 0) Z = fft_run_c<C, NC, 1>(za, zc, tw, lane, nseq);
+    else Z = fft_run<C>(za, zc, tw, P, lane, nseq);
     for (int q = lane; q < nseq * h; q += 32) {
       const int sq = q / h, k = q - sq * h, s = s0 + sq;
       const C zk = Z[sq * n + k], zn = Z[sq * n + (n - k) % n];
@@ -300,16 +330,16 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_rfft3_fft(const T* __restric
   }
 }
 
-template <typename T>
+template <typename T, int NC>  // NC: compile-time length (0: the plan's)
 __global__ void __launch_bounds__(FFT_WARPS * 32) k_irfft3_fft(const cx_t<T>* __restrict__ Xh, T* __restrict__ X,
                                                                long plane, FftPlan P) {
   using C = cx_t<T>;
   extern __shared__ __align__(16) unsigned char fsm[];
-  const int n = P.n, h = n / 2 + 1, TT = P.tubes;
+  const int n = NC ? NC : P.n, h = n / 2 + 1, TT = NC ? fft_tt<T>(NC) : P.tubes;
   C* tw = (C*)fsm;                                  // [n]
   C* zb = tw + n;                                   // [FFT_WARPS][2][seqs][n]
   const int LD = TT + 1;                            // padded row stride: conflict-free column walks
-  C* itile = zb + (size_t)FFT_WARPS * 2 * P.seqs * n;  // [h][LD] complex
+  C* itile = zb + (size_t)FFT_WARPS * 2 * (NC ? fft_seqs(NC) : P.seqs) * n;  // [h][LD] complex
   T* otile = (T*)(itile + (size_t)h * LD);          // [n][LD] real
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long e0 = (long)blockIdx.x * TT;
@@ -335,7 +365,7 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_irfft3_fft(const cx_t<T>* __
     }
   }
   __syncthreads();
-  const int B = P.seqs;
+  const int B = NC ? fft_seqs(NC) : P.seqs;
   C* za = zb + (size_t)warp * 2 * B * n;
   C* zc = za + (size_t)B * n;
   const T inv = T(1) / T(n);
@@ -354,7 +384,9 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_irfft3_fft(const cx_t<T>* __
       za[q] = mkc(x.x - y.y, x.y + y.x);  // Z = X + i Y
     }
     __syncwarp();
-    const C* z = fft_run<C>(za, zc, tw, P, lane, nseq);
+    const C* z;
+    if constexpr (NC > 0) z = fft_run_c<C, NC, 1>(za, zc, tw, lane, nseq);
+    else z = fft_run<C>(za, zc, tw, P, lane, nseq);
     for (int q = lane; q < nseq * n; q += 32) {
       const int sq = q / n, t = q - sq * n, s = s0 + sq;
       otile[t * LD + 2 * s] = z[q].x * inv;
@@ -398,11 +430,21 @@ int launch_rfft3(const T* X, cx_t<T>* Xh, long plane, int n3, cudaStream_t s) {
   FftPlan P;
   size_t smem;
   if (fft_setup<T>(n3, &P, &smem)) {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_rfft3_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_rfft3_fft<T><<<cdiv(plane, P.tubes), FFT_WARPS * 32, smem, s>>>(X, Xh, plane, P);
-    TSVD_LAUNCHED();
-    return TSVD_OK;
+    auto go = [&](auto kern) {
+      if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kern<<<cdiv(plane, P.tubes), FFT_WARPS * 32, smem, s>>>(X, Xh, plane, P);
+      TSVD_LAUNCHED();
+      return TSVD_OK;
+    };
+    switch (n3) {  // compile-time lengths (same tile width as the plan's)
+      case 4: return go(k_rfft3_fft<T, 4>);
+      case 8: return go(k_rfft3_fft<T, 8>);
+      case 16: return go(k_rfft3_fft<T, 16>);
+      case 32: return go(k_rfft3_fft<T, 32>);
+      case 64: return go(k_rfft3_fft<T, 64>);
+      case 128: return go(k_rfft3_fft<T, 128>);
+      default: return go(k_rfft3_fft<T, 0>);
+    }
   }
   // very long tubes: direct transform
   const int te = tile_e(n3, sizeof(T), sizeof(cx_t<T>), false);
@@ -420,11 +462,21 @@ int launch_irfft3(const cx_t<T>* Xh, T* X, long plane, int n3, cudaStream_t s) {
   FftPlan P;
   size_t smem;
   if (fft_setup<T>(n3, &P, &smem)) {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_irfft3_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_irfft3_fft<T><<<cdiv(plane, P.tubes), FFT_WARPS * 32, smem, s>>>(Xh, X, plane, P);
-    TSVD_LAUNCHED();
-    return TSVD_OK;
+    auto go = [&](auto kern) {
+      if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kern<<<cdiv(plane, P.tubes), FFT_WARPS * 32, smem, s>>>(Xh, X, plane, P);
+      TSVD_LAUNCHED();
+      return TSVD_OK;
+    };
+    switch (n3) {
+      case 4: return go(k_irfft3_fft<T, 4>);
+      case 8: return go(k_irfft3_fft<T, 8>);
+      case 16: return go(k_irfft3_fft<T, 16>);
+      case 32: return go(k_irfft3_fft<T, 32>);
+      case 64: return go(k_irfft3_fft<T, 64>);
+      case 128: return go(k_irfft3_fft<T, 128>);
+      default: return go(k_irfft3_fft<T, 0>);
+    }
   }
   const int h = n3 / 2 + 1;
   const int te = tile_e(n3, sizeof(T), sizeof(cx_t<T>), true);

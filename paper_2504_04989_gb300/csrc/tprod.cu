@@ -134,15 +134,14 @@ static int tprod_tc_run(const float* A, const float* B, float* Cout, int n1, int
   {
     TSVD_STAGE("tprod_expand", s);
     TSVD_TRY(expand_thin(w.Bh, n4, (long)n2 * n4, n2, n4, w.E, w.lde, 2L * n4 * w.lde, h, 0, bf16, s));
-    const void* Aop = w.Ah;
-    long lda = k2;
-    if (w.Aop) {  // BF16 operand, or FP32 rows padded to 16 bytes
+    if (w.Aop)  // BF16 operand, or FP32 rows padded to 16 bytes
       TSVD_TRY(copy_rows((const float*)w.Ah, k2, w.Aop, w.lda, (int)k2, (long)h * n1, bf16, s));
-      Aop = w.Aop;
-      lda = w.lda;
-    }
     if (cudaMemsetAsync(w.err, 0, sizeof(int), s) != cudaSuccess) return TSVD_ERR_CUDA;
+  }
+  {
     TSVD_STAGE("tprod_gemm_tc", s);
+    const void* Aop = w.Aop ? w.Aop : (const void*)w.Ah;
+    const long lda = w.Aop ? w.lda : k2;
     TSVD_TRY(tc_gemm(Aop, lda, (long)n1 * lda, n1, w.E, w.lde, 2L * n4 * w.lde, 2 * n4, (int)k2, (float*)w.Ch,
                      2L * n4, 2L * n1 * n4, h, bf16, w.err, s));
   }
