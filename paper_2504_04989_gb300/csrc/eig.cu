@@ -1039,27 +1039,32 @@ __device__ __forceinline__ int sturm_count(const double* d, const double* f2, in
   return cnt;
 }
 
-// The same count in FP32 (exponent kept within +-60 by powers of two).  A
-// computed count is the exact count of a tridiagonal whose entries moved by a
-// few units in the last place (backward stability of the recurrence), so a
-// bracket from FP32 counts holds the eigenvalue once widened by a margin far
-// above eps32 ||T||.
-__device__ __forceinline__ int sturm_count_f32(const float* d, const float* f2, int m, float x, float pivmin) {
-  float pm = 1.0f, p = d[0] - x;
-  if (p == 0.0f) p = -pivmin;
-  int cnt = (int)(__float_as_uint(p) >> 31);
-  for (int i = 1; i < m; ++i) {
-    float pn = fmaf(d[i] - x, p, -f2[i - 1] * pm);
-    unsigned bn = __float_as_uint(pn);
-    if ((bn << 1) == 0u) {
-      pn = -pivmin * p;
-      bn = __float_as_uint(pn);
-    }
-    cnt += (int)((bn ^ __float_as_uint(p)) >> 31);
+// The reduced-precision counts below clamp every ratio q_i of magnitude
+// below 2^-64 to -2^-64 (a perturbation of d_{i-1} by at most 2^-63 ||T||)
+// and rescale the pair by a power of two whenever |P_i| leaves
+// [2^-32, 2^32].  The clamp bounds |P_{i-1} / P_i| by 2^64, so neither member
+// of the pair can overflow or become subnormal.
+constexpr float kSturmPiv = 0x1p-64f;
+
+// FP32 count.  df[i] = (d_i, f_{i-1}^2) with f_{-1} = 0.  A computed count is
+// the exact count of a tridiagonal whose d_i - x and f^2 moved by a few units
+// in the last place (the recurrence is backward stable), i.e. of one within
+// about 5e-7 ||T|| of the given one, so a bracket from FP32 counts holds the
+// eigenvalue once widened by a margin above that.
+__device__ __forceinline__ int sturm_count_f32(const float2* __restrict__ df, int m, float x) {
+  float p = 1.0f, pm = 0.0f;
+  int cnt = 0;
+#pragma unroll 4
+  for (int i = 0; i < m; ++i) {
+    const float2 v = df[i];
+    float pn = fmaf(v.x - x, p, -v.y * pm);
+    if (fabsf(pn) < kSturmPiv * fabsf(p)) pn = -kSturmPiv * p;
+    cnt += (int)((__float_as_uint(pn) ^ __float_as_uint(p)) >> 31);
     pm = p;
     p = pn;
-    const int ex = (int)((bn >> 23) & 0xffu) - 127;
-    if (ex > 60 || ex < -60) {
+    const float an = fabsf(pn);
+    if (an > 0x1p32f || an < 0x1p-32f) {
+      const int ex = (int)((__float_as_uint(pn) >> 23) & 0xffu) - 127;
       const float sc = __uint_as_float((unsigned)(127 - ex) << 23);
       p *= sc;
       pm *= sc;
@@ -1068,18 +1073,76 @@ __device__ __forceinline__ int sturm_count_f32(const float* d, const float* f2, 
   return cnt;
 }
 
+// The same count in double-float arithmetic (each value hi + lo, two FP32
+// numbers, about 48 significant bits) on the FP32 pipe, which on GB300 issues
+// 64 times the FP64 rate.  v[i] = (d_i hi, d_i lo, f_{i-1}^2 hi, f_{i-1}^2 lo).
+// Per step: d_i - x by TwoSum of the high parts plus the low parts; the two
+// products by TwoProduct (FMA) of the high parts plus the cross terms; their
+// difference by TwoSum and one renormalisation.  Every operation is exact up
+// to about 2^-47 of its operands, so a computed count is the exact count of a
+// tridiagonal within about 1e-14 ||T|| of the given one.
+__device__ __forceinline__ int sturm_count_df(const float4* __restrict__ v, int m, dfl x) {
+  float ph = 1.0f, pl = 0.0f, qh = 0.0f, ql = 0.0f;  // P_i, P_{i-1}
+  int cnt = 0;
+#pragma unroll 2
+  for (int i = 0; i < m; ++i) {
+    const float4 c = v[i];
+    const float th = c.x - x.hi;  // t = d_i - x, not renormalised
+    const float tb = th - c.x;
+    const float tl = ((c.x - (th - tb)) + (-x.hi - tb)) + (c.y - x.lo);
+    const float a = th * ph;  // t P_i
+    const float ae = fmaf(tl, ph, fmaf(th, pl, fmaf(th, ph, -a)));
+    const float b = c.z * qh;  // f^2 P_{i-1}
+    const float be = fmaf(c.w, qh, fmaf(c.z, ql, fmaf(c.z, qh, -b)));
+    const float sh = a - b;
+    const float sb = sh - a;
+    const float sl = ((a - (sh - sb)) + (-b - sb)) + (ae - be);
+    float nh = sh + sl;
+    float nl = sl - (nh - sh);
+    if (fabsf(nh) < kSturmPiv * fabsf(ph)) {
+      nh = -kSturmPiv * ph;
+      nl = -kSturmPiv * pl;
+    }
+    cnt += (int)((__float_as_uint(nh) ^ __float_as_uint(ph)) >> 31);
+    qh = ph;
+    ql = pl;
+    ph = nh;
+    pl = nl;
+    const float an = fabsf(nh);
+    if (an > 0x1p32f || an < 0x1p-32f) {
+      const int ex = (int)((__float_as_uint(nh) >> 23) & 0xffu) - 127;
+      const float sc = __uint_as_float((unsigned)(127 - ex) << 23);
+      ph *= sc;
+      pl *= sc;
+      qh *= sc;
+      ql *= sc;
+    }
+  }
+  return cnt;
+}
+
 // Multisection: one warp per wanted eigenvalue (the (r+1)-th largest of the
 // slice's scaled T); per step the 32 lanes count at 32 interior points of the
 // bracket, so the bracket shrinks 33-fold per step.
+//
+// abs_tol = 0 (FP64 path): FP64 counts until the bracket is within two units
+// in the last place of the eigenvalue.  abs_tol > 0 (FP32 path): BIS_F32_ROUNDS
+// rounds of FP32 counts, the bracket widened by BIS_F32_MARGIN on both sides
+// (about seven times the FP32 count's backward error bound), then
+// double-float counts until the bracket is at most abs_tol wide.  Each round
+// moves an end only to a point whose count was taken, at that point's value
+// in the precision of the count.
 constexpr int BIS_WARPS = 4;
+constexpr int BIS_F32_ROUNDS = 4;
+constexpr double BIS_F32_MARGIN = 0x1p-18;
 __global__ void __launch_bounds__(BIS_WARPS * 32) k_bisect(int m, int R, EigScratch e, double* __restrict__ lam_out,
                                                           double abs_tol) {
   extern __shared__ __align__(16) double bsm[];
-  double* d = bsm;      // [m] scaled diagonal
-  double* f2 = bsm + m; // [m] scaled squared off-diagonal
-  float* d32 = (float*)(bsm + 2 * m);  // [m] the same in FP32 (coarse rounds)
-  float* f232 = d32 + m;
-  __shared__ double s_scale, s_lo, s_hi;
+  double* d = bsm;                        // [m] scaled diagonal
+  double* f2 = bsm + m;                   // [m] scaled squared off-diagonal
+  float4* v4 = (float4*)(bsm + 2 * m);    // [m] double-float (d_i, f_{i-1}^2)
+  float2* v2 = (float2*)(v4 + m);         // [m] FP32 (d_i, f_{i-1}^2)
+  __shared__ double s_scale, s_lo[BIS_WARPS], s_hi[BIS_WARPS];
   const int b = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r = blockIdx.x * BIS_WARPS + warp;
   if (threadIdx.x == 0) {
@@ -1088,24 +1151,29 @@ __global__ void __launch_bounds__(BIS_WARPS * 32) k_bisect(int m, int R, EigScra
   }
   __syncthreads();
   const double sc = s_scale;
+  const double* ed = e.d + (long)b * m;
+  const double* ef = e.f + (long)b * m;
+  double glo = DBL_MAX, ghi = -DBL_MAX;  // Gershgorin bracket of the scaled T
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    d[i] = e.d[(long)b * m + i] * sc;
-    const double fi = (i < m - 1) ? e.f[(long)b * m + i] * sc : 0.0;
-    f2[i] = fi * fi;
-    d32[i] = (float)d[i];
-    f232[i] = (float)(fi * fi);
+    const double di = ed[i] * sc;
+    const double fr = (i < m - 1) ? ef[i] * sc : 0.0;
+    const double fl = (i > 0) ? ef[i - 1] * sc : 0.0;
+    d[i] = di;
+    f2[i] = fr * fr;
+    const double fl2 = fl * fl;
+    const dfl dh = df_from(di), fh = df_from(fl2);
+    v4[i] = make_float4(dh.hi, dh.lo, fh.hi, fh.lo);
+    v2[i] = make_float2((float)di, (float)fl2);
+    glo = fmin(glo, di - fabs(fl) - fabs(fr));
+    ghi = fmax(ghi, di + fabs(fl) + fabs(fr));
   }
-  if (threadIdx.x == 0) {  // Gershgorin bracket of the scaled T
-    double lo = e.d[(long)b * m] * sc, hi = lo;
-    for (int i = 0; i < m; ++i) {
-      const double fl = (i > 0) ? e.f[(long)b * m + i - 1] * sc : 0.0;
-      const double fr = (i < m - 1) ? e.f[(long)b * m + i] * sc : 0.0;
-      const double di = e.d[(long)b * m + i] * sc;
-      lo = fmin(lo, di - fl - fr);
-      hi = fmax(hi, di + fl + fr);
-    }
-    s_lo = lo;
-    s_hi = hi;
+  for (int o = 16; o > 0; o >>= 1) {
+    glo = fmin(glo, __shfl_xor_sync(0xffffffffu, glo, o));
+    ghi = fmax(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
+  }
+  if (lane == 0) {
+    s_lo[warp] = glo;
+    s_hi[warp] = ghi;
   }
   __syncthreads();
   if (r >= R) return;
@@ -1113,39 +1181,55 @@ __global__ void __launch_bounds__(BIS_WARPS * 32) k_bisect(int m, int R, EigScra
     if (lane == 0) lam_out[(long)b * R + r] = 0.0;
     return;
   }
-  const double tn = fmax(fabs(s_lo), fabs(s_hi));
+  double g_lo = s_lo[0], g_hi = s_hi[0];
+  for (int w = 1; w < BIS_WARPS; ++w) {
+    g_lo = fmin(g_lo, s_lo[w]);
+    g_hi = fmax(g_hi, s_hi[w]);
+  }
+  const double tn = fmax(fabs(g_lo), fabs(g_hi));
   const double pivmin = DBL_MIN * 0x1p+64;
-  double lo = s_lo - (4.0 * DBL_EPSILON * tn + pivmin);
-  double hi = s_hi + (4.0 * DBL_EPSILON * tn + pivmin);
+  double lo = g_lo - (4.0 * DBL_EPSILON * tn + pivmin);
+  double hi = g_hi + (4.0 * DBL_EPSILON * tn + pivmin);
   const int idx = m - 1 - r;  // ascending index of the wanted eigenvalue
   if (abs_tol > 0.0) {
-    // coarse rounds on FP32 counts (64x the FP64 rate here), then widen by 4e-5 ||T||
-    const float pivmin32 = 1e-30f;
-    for (int it = 0; it < 3; ++it) {
+    for (int it = 0; it < BIS_F32_ROUNDS; ++it) {
       const double w = hi - lo;
       const float x = (float)(lo + w * ((double)(lane + 1) / 33.0));
-      const unsigned above = __ballot_sync(0xffffffffu, sturm_count_f32(d32, f232, m, x, pivmin32) > idx);
+      const unsigned above = __ballot_sync(0xffffffffu, sturm_count_f32(v2, m, x) > idx);
       const int first = above ? __ffs(above) - 1 : 32;
-      const double nlo = (first == 0) ? lo : lo + w * ((double)first / 33.0);
-      const double nhi = (first == 32) ? hi : lo + w * ((double)(first + 1) / 33.0);
+      const double nlo = (first == 0) ? lo : (double)(float)(lo + w * ((double)first / 33.0));
+      const double nhi = (first == 32) ? hi : (double)(float)(lo + w * ((double)(first + 1) / 33.0));
       lo = nlo;
       hi = nhi;
     }
-    lo = fmax(lo - 4e-5 * tn, s_lo - (4.0 * DBL_EPSILON * tn + pivmin));
-    hi = fmin(hi + 4e-5 * tn, s_hi + (4.0 * DBL_EPSILON * tn + pivmin));
-  }
-  for (int it = 0; it < 64; ++it) {
-    const double w = hi - lo;
-    // relative to the eigenvalue (FP64 path), or absolute on the scaled T (abs_tol > 0)
-    if (w <= fmax(2.0 * DBL_EPSILON * (fabs(lo) + fabs(hi)), abs_tol) + pivmin) break;
-    const double x = lo + w * ((double)(lane + 1) / 33.0);
-    const unsigned above = __ballot_sync(0xffffffffu, sturm_count(d, f2, m, x, pivmin) > idx);
-    const int first = above ? __ffs(above) - 1 : 32;  // lowest point with more than idx values below it
-    const double nlo = (first == 0) ? lo : lo + w * ((double)first / 33.0);
-    const double nhi = (first == 32) ? hi : lo + w * ((double)(first + 1) / 33.0);
-    if (nlo == lo && nhi == hi) break;
-    lo = nlo;
-    hi = nhi;
+    lo = fmax(lo - BIS_F32_MARGIN * tn, g_lo - (4.0 * DBL_EPSILON * tn + pivmin));
+    hi = fmin(hi + BIS_F32_MARGIN * tn, g_hi + (4.0 * DBL_EPSILON * tn + pivmin));
+    for (int it = 0; it < 16; ++it) {
+      const double w = hi - lo;
+      if (w <= abs_tol) break;
+      const dfl x = df_from(lo + w * ((double)(lane + 1) / 33.0));
+      const unsigned above = __ballot_sync(0xffffffffu, sturm_count_df(v4, m, x) > idx);
+      const int first = above ? __ffs(above) - 1 : 32;
+      const double nlo = (first == 0) ? lo : df_to(df_from(lo + w * ((double)first / 33.0)));
+      const double nhi = (first == 32) ? hi : df_to(df_from(lo + w * ((double)(first + 1) / 33.0)));
+      if (nlo == lo && nhi == hi) break;
+      lo = nlo;
+      hi = nhi;
+    }
+  } else {
+    for (int it = 0; it < 64; ++it) {
+      const double w = hi - lo;
+      // relative to the eigenvalue
+      if (w <= 2.0 * DBL_EPSILON * (fabs(lo) + fabs(hi)) + pivmin) break;
+      const double x = lo + w * ((double)(lane + 1) / 33.0);
+      const unsigned above = __ballot_sync(0xffffffffu, sturm_count(d, f2, m, x, pivmin) > idx);
+      const int first = above ? __ffs(above) - 1 : 32;  // lowest point with more than idx values below it
+      const double nlo = (first == 0) ? lo : lo + w * ((double)first / 33.0);
+      const double nhi = (first == 32) ? hi : lo + w * ((double)(first + 1) / 33.0);
+      if (nlo == lo && nhi == hi) break;
+      lo = nlo;
+      hi = nhi;
+    }
   }
   if (lane == 0) lam_out[(long)b * R + r] = 0.5 * (lo + hi) / sc;
 }
@@ -1480,10 +1564,10 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
   }
   {
     TSVD_STAGE("eig_bisect", s);
-    const size_t smem_b = 2 * (size_t)m * (sizeof(double) + sizeof(float));
-    // FP32 path: eigenvalues to 1e-13 of ||T|| (the vectors and the outputs are FP32; the
+    const size_t smem_b = (size_t)m * (2 * sizeof(double) + sizeof(float4) + sizeof(float2));
+    // FP32 path: eigenvalues to 3e-13 of ||T|| (the vectors and the outputs are FP32; the
     // smallest kept sigma^2 is far above that); FP64 path: to the eigenvalue's own precision
-    const double abs_tol = kDoubleFloat ? 1e-13 : 0.0;
+    const double abs_tol = kDoubleFloat ? 3e-13 : 0.0;
     k_bisect<<<dim3(cdiv(R, BIS_WARPS), batch), BIS_WARPS * 32, smem_b, s>>>(m, R, e, lam, abs_tol);
     TSVD_LAUNCHED();
   }
@@ -1492,8 +1576,8 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
     const size_t smem_tp = (3 + (size_t)TP_THREADS) * m * sizeof(double);
     if (smem_tp > 48 * 1024)
       cudaFuncSetAttribute(k_tridiag_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tp);
-    // solves: 3 (FP64 path), 2 on the FP32 path (eigenvalues to 1e-13 ||T|| already make one solve
-    // amplify the wanted direction by gap / 1e-13; the vectors end in FP32)
+    // solves: 3 (FP64 path), 2 on the FP32 path (eigenvalues to 3e-13 ||T|| already make one solve
+    // amplify the wanted direction by gap / 3e-13; the vectors end in FP32)
     k_tridiag_pairs<<<dim3(cdiv(R, TP_THREADS), batch), TP_THREADS, smem_tp, s>>>(m, R, e, lam, kDoubleFloat ? 2 : 3);
     TSVD_LAUNCHED();
   }
