@@ -14,83 +14,155 @@
 
 namespace tsvd {
 
-__device__ __forceinline__ int pidx(int i, int j, int n) { return i * n - (i * (i - 1)) / 2 + (j - i); }
-
 // ---------------------------------------------------------------------------
 // Cholesky (upper, right-looking) R^H R = G + s I of one nb x nb Gram matrix
-// per CTA, in the Gram's own precision.  s = shift_rel * trace(G).
-// Pivot test: shifted pass -> dead iff d_j <= 0; plain pass -> dead iff
-// d_j <= dead_rel * G_jj.  Dead columns get R_jj = 1 and R_jk = 0.
-// One barrier per column: the scaling of row j is folded into the trailing
-// update S(i,k) -= conj(S(j,i)) S(j,k) / d_j, and row j is scaled by
-// 1/sqrt(d_j) at the end.
+// per CTA, in the Gram's own precision, s = shift_rel * trace(G), followed by
+// the inverse M of R-tilde, written dense (zeros below the diagonal):
+//   pivot test: shifted pass -> dead iff d_j <= 0; plain pass -> dead iff
+//   d_j <= dead_rel * G_jj;
+//   R-tilde: R with every dead row and every dead column replaced by the unit
+//   vector (so R-tilde = diag(R_live, I) up to a permutation);
+//   M: R-tilde^{-1} with the dead columns set to zero, so that W M is
+//   W_live R_live^{-1} on the live columns and zero on the dead ones.
+// Thread t keeps the entries p = t, t + CI_THREADS, ... of the packed upper
+// triangle (row-major) in registers, so each step is one round of independent
+// register updates between two barriers:
+//   factorisation, step j: S(i,k) -= conj(S(j,i)) S(j,k) / d_j for
+//   j < i <= k, with row j read from shared memory, where its owners
+//   published it when it became final (end of step j-1); the published rows
+//   are R unscaled (row j is divided by sqrt(d_j) when read);
+//   inverse, step l = nb-1 .. 1 (backward substitution R X = I for all
+//   columns at once, B = I initially): B(i,k) -= R(i,l) X(l,k) for
+//   i < l <= k, where X(l,k) = B(l,k) / R_ll, final after step l+1, is
+//   published in a double-buffered row.
 // ---------------------------------------------------------------------------
-template <typename GC>
-__global__ void __launch_bounds__(512) k_chol_upper(const GC* __restrict__ G, long ldg, long sG,
-                                                    double2* __restrict__ Rm, long ldr, long sR, int nb,
-                                                    double shift_rel, double dead_rel,
-                                                    uint32_t* __restrict__ dead_out) {
+constexpr int CI_THREADS = 512;
+template <typename GC, int EPT>  // EPT >= nb (nb+1) / 2 / CI_THREADS entries per thread
+__global__ void __launch_bounds__(CI_THREADS) k_chol_inv(const GC* __restrict__ G, long ldg, long sG,
+                                                       GC* __restrict__ Mo, long ldm, long sM, int nb,
+                                                       double shift_rel, double dead_rel,
+                                                       uint32_t* __restrict__ dead_out) {
   using Rt = decltype(GC().x);
   extern __shared__ __align__(16) unsigned char chsm[];
-  const int np = nb * (nb + 1) / 2;
-  GC* S = (GC*)chsm;                                  // packed upper triangle
-  unsigned char* rowof = (unsigned char*)(S + np);    // row of each packed index (nb <= 128)
-  __shared__ Rt dg[128];      // diagonal of G (pivot test of the plain passes)
-  __shared__ Rt dj[128];      // pivots d_j (0 for a dead column)
-  __shared__ double red[16];
+  GC* S = (GC*)chsm;            // published rows of the packed triangle: S(i, k) = S[rb(i) + k]
+  GC* Xr = S + nb * (nb + 1) / 2;  // [2][nb] published rows of X
+  __shared__ Rt dg[128];        // diagonal of G (pivot test of the plain passes)
+  __shared__ Rt dj[128];        // pivots d_j (0 for a dead column)
+  __shared__ Rt ri[128];        // 1 / R-tilde_jj
+  __shared__ double red[CI_THREADS / 32];
   const int b = blockIdx.x, tid = threadIdx.x;
+  const int np = nb * (nb + 1) / 2;
+  auto rb = [nb](int i) { return i * nb - (i * (i + 1)) / 2; };  // packed offset of row i, minus i
   G += (long)b * sG;
-  Rm += (long)b * sR;
-  for (int e = tid; e < nb * nb; e += blockDim.x) {
-    const int i = e / nb, j = e - i * nb;
-    if (j >= i) {
-      S[pidx(i, j, nb)] = G[(long)i * ldg + j];
-      rowof[pidx(i, j, nb)] = (unsigned char)i;
+  Mo += (long)b * sM;
+  // owned entries: (row, column) and value
+  int ei[EPT], ek[EPT];
+  GC v[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int p = tid + e * CI_THREADS;
+    int i = -1, k = -1;
+    if (p < np) {
+      // row i: largest i with rb(i) + i <= p (closed form, then corrected)
+      const double q = 2.0 * nb + 1.0;
+      i = (int)((q - sqrt(q * q - 8.0 * p)) * 0.5);
+      i = max(0, min(i, nb - 1));
+      while (i > 0 && rb(i) + i > p) --i;
+      while (i + 1 < nb && rb(i + 1) + i + 1 <= p) ++i;
+      k = p - rb(i);
     }
+    ei[e] = i;
+    ek[e] = k;
+    v[e] = (p < np) ? G[(long)i * ldg + k] : GC{Rt(0), Rt(0)};
   }
   if (tid < nb) dg[tid] = G[(long)tid * ldg + tid].x;
   __syncthreads();
   const double trace = block_sum(tid < nb ? (double)dg[tid] : 0.0, red);
   const Rt sft = (shift_rel > 0.0) ? (Rt)(shift_rel * trace) : Rt(0);
-  if (tid < nb) S[pidx(tid, tid, nb)].x += sft;
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    if (ei[e] >= 0 && ei[e] == ek[e]) v[e].x += sft;
+    if (ei[e] == 0) S[ek[e]] = v[e];  // row 0 is final
+  }
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    const int offj = pidx(j, j, nb);
-    const Rt d = S[offj].x;
+    const GC* Sj = S + rb(j);
+    const Rt d = Sj[j].x;
     const bool dead = (shift_rel > 0.0) ? !(d > Rt(0)) : !(d > (Rt)dead_rel * dg[j]);
     if (tid == 0) dj[j] = dead ? Rt(0) : d;
-    if (!dead && j + 1 < nb) {
-      // trailing triangle (rows i > j) = the packed suffix from pidx(j+1, j+1), flattened over the CTA
-      const Rt inv = Rt(1) / d;
-      for (int p = pidx(j + 1, j + 1, nb) + tid; p < np; p += blockDim.x) {
-        const int i = rowof[p];
-        const int k = p - pidx(i, i, nb) + i;
-        GC a = S[offj + (i - j)];  // S(j, i); the update uses conj(a) / d
-        const GC cjk = S[offj + (k - j)];
-        a.x *= inv;
-        a.y *= inv;
-        GC t = S[p];
-        t.x = fma(-a.x, cjk.x, t.x);
-        t.x = fma(-a.y, cjk.y, t.x);
-        t.y = fma(-a.x, cjk.y, t.y);
-        t.y = fma(a.y, cjk.x, t.y);
-        S[p] = t;
+    const Rt inv = dead ? Rt(0) : Rt(1) / d;  // a dead column leaves the trailing rows unchanged
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int i = ei[e], k = ek[e];
+      if (i > j) {
+        const GC a = Sj[i];
+        const GC c = Sj[k];
+        const Rt ax = a.x * inv, ay = a.y * inv;  // conj(a) / d times c
+        v[e].x = fma(-ax, c.x, v[e].x);
+        v[e].x = fma(-ay, c.y, v[e].x);
+        v[e].y = fma(-ax, c.y, v[e].y);
+        v[e].y = fma(ay, c.x, v[e].y);
+        if (i == j + 1) S[rb(i) + k] = v[e];  // row j+1 is final
       }
     }
     __syncthreads();
   }
-  for (int e = tid; e < nb * nb; e += blockDim.x) {
-    const int i = e / nb, k = e - i * nb;
-    double2 r = make_double2(0, 0);
-    const Rt d = dj[i];
-    if (k == i) {
-      r.x = (d > Rt(0)) ? sqrt((double)d) : 1.0;
-    } else if (k > i && d > Rt(0)) {
-      const double sc = 1.0 / sqrt((double)d);
-      const GC v = S[pidx(i, k, nb)];
-      r = make_double2((double)v.x * sc, (double)v.y * sc);
+  if (tid < nb) ri[tid] = (dj[tid] > Rt(0)) ? Rt(1) / sqrt(dj[tid]) : Rt(1);
+  __syncthreads();
+  // inverse: B in the registers (0 above the diagonal, 1 on it), R-tilde(i, l) = R(i, l) / sqrt(d_i)
+  // read from the published rows (0 where row i or column l is dead)
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) v[e] = GC{Rt(0), Rt(0)};
+  for (int l = nb - 1; l >= 1; --l) {
+    const GC* xl = Xr + (l & 1) * nb;  // X(l, k), k > l
+    const Rt rl = ri[l];
+    const bool live_l = dj[l] > Rt(0);
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int i = ei[e], k = ek[e];
+      if (i >= 0 && i < l && k >= l) {
+        GC c = S[rb(i) + l];
+        const Rt sc = (live_l && dj[i] > Rt(0)) ? ri[i] : Rt(0);
+        c.x *= sc;
+        c.y *= sc;
+        GC x;
+        if (k == l) {
+          x.x = rl;
+          x.y = Rt(0);
+        } else {
+          x = xl[k];
+        }
+        v[e].x = fma(-c.x, x.x, v[e].x);
+        v[e].x = fma(c.y, x.y, v[e].x);
+        v[e].y = fma(-c.x, x.y, v[e].y);
+        v[e].y = fma(-c.y, x.x, v[e].y);
+      }
+      if (i == l - 1 && k > i) {  // row l-1 of B is final: publish X(l-1, k)
+        const Rt s = ri[i];
+        Xr[((l - 1) & 1) * nb + k] = GC{v[e].x * s, v[e].y * s};
+      }
     }
-    Rm[(long)i * ldr + k] = r;
+    __syncthreads();
+  }
+  // M(i, k) = B(i, k) / R_ii (M(i, i) = 1 / R_ii); dead columns and the lower triangle zero
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = ei[e], k = ek[e];
+    if (i < 0) continue;
+    GC mv = GC{Rt(0), Rt(0)};
+    if (dj[k] > Rt(0)) {
+      if (k == i) {
+        mv.x = ri[i];
+      } else {
+        mv.x = v[e].x * ri[i];
+        mv.y = v[e].y * ri[i];
+      }
+    }
+    Mo[(long)i * ldm + k] = mv;
+  }
+  for (int e = tid; e < nb * nb; e += CI_THREADS) {
+    const int i = e / nb, k = e - i * nb;
+    if (k < i) Mo[(long)i * ldm + k] = GC{Rt(0), Rt(0)};
   }
   if (tid < 4) {
     uint32_t msk = 0;
@@ -103,139 +175,138 @@ __global__ void __launch_bounds__(512) k_chol_upper(const GC* __restrict__ G, lo
 }
 
 template <typename GC>
-int chol_upper(const GC* G, long ldg, long sG, double2* Rm, long ldr, long sR, int nb, int batch, double shift_rel,
-               double dead_rel, uint32_t* dead, cudaStream_t s) {
+int chol_inv(const GC* G, long ldg, long sG, GC* M, long ldm, long sM, int nb, int batch, double shift_rel,
+             double dead_rel, uint32_t* dead, cudaStream_t s) {
   if (nb <= 0 || batch <= 0) return TSVD_OK;
   if (nb > 128) return TSVD_ERR_UNSUPPORTED;
-  const size_t np = (size_t)nb * (nb + 1) / 2;
-  const size_t smem = np * sizeof(GC) + np;  // packed triangle + row table
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_chol_upper<GC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_chol_upper<GC><<<batch, 512, smem, s>>>(G, ldg, sG, Rm, ldr, sR, nb, shift_rel, dead_rel, dead);
-  TSVD_LAUNCHED();
-  return TSVD_OK;
-}
-template int chol_upper<double2>(const double2*, long, long, double2*, long, long, int, int, double, double,
-                                 uint32_t*, cudaStream_t);
-template int chol_upper<float2>(const float2*, long, long, double2*, long, long, int, int, double, double, uint32_t*,
-                                cudaStream_t);
-
-// ---------------------------------------------------------------------------
-// W <- W R^{-1} by forward substitution x R = w, one warp per TS_ROWS rows of
-// W: lane l keeps columns l, l+32, l+64, l+96 of its rows in registers; for
-// each j the solved x_j is broadcast by a shuffle and every lane updates its
-// columns k > j with R(j, k) (R packed in shared memory, diagonal stored as
-// 1/R_jj, 0 for a dead column).
-// ---------------------------------------------------------------------------
-// rows per warp (more rows raise the registers past one wave of CTAs)
-template <typename C>
-constexpr int ts_rows() { return 4; }
-constexpr int TS_WARPS = 8;
-
-template <typename C, int NU>  // NU = ceil(nb / 32) column slots per lane
-__global__ void __launch_bounds__(TS_WARPS * 32) k_trsm_right_upper(C* __restrict__ W, long ldw, long sW,
-                                                                   const double2* __restrict__ Rm, long ldr, long sR,
-                                                                   int n1, int nb, const uint32_t* __restrict__ dead) {
-  using R = decltype(C().x);
-  extern __shared__ __align__(16) unsigned char smraw[];
-  C* Rp = (C*)smraw;  // packed upper, nb(nb+1)/2
-  const int b = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  W += (long)b * sW;
-  Rm += (long)b * sR;
-  uint32_t dm[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) dm[q] = dead[b * 4 + q];
-  for (int e = tid; e < nb * nb; e += blockDim.x) {
-    const int i = e / nb, j = e - i * nb;
-    if (j < i) continue;
-    const double2 v = Rm[(long)i * ldr + j];
-    C out;
-    if (j == i) {
-      const bool isdead = (dm[j >> 5] >> (j & 31)) & 1u;
-      out.x = isdead ? R(0) : (R)(1.0 / v.x);
-      out.y = R(0);
-    } else {
-      out.x = (R)v.x;
-      out.y = (R)v.y;
-    }
-    Rp[pidx(i, j, nb)] = out;
-  }
-  __syncthreads();
-  constexpr int TS_ROWS = ts_rows<C>();
-  const int r0 = (blockIdx.x * TS_WARPS + warp) * TS_ROWS;
-  if (r0 >= n1) return;
-  C x[TS_ROWS][NU];
-#pragma unroll
-  for (int r = 0; r < TS_ROWS; ++r)
-#pragma unroll
-    for (int u = 0; u < NU; ++u) {
-      const int k = lane + 32 * u;
-      x[r][u] = (r0 + r < n1 && k < nb) ? W[(long)(r0 + r) * ldw + k] : C{R(0), R(0)};
-    }
-#pragma unroll
-  for (int u = 0; u < NU; ++u) {
-    for (int jj = 0; jj < 32; ++jj) {
-      const int j = 32 * u + jj;
-      if (j >= nb) break;
-      const int offj = pidx(j, j, nb);
-      const R rinv = Rp[offj].x;
-      C xj[TS_ROWS];
-#pragma unroll
-      for (int r = 0; r < TS_ROWS; ++r) {
-        xj[r].x = __shfl_sync(0xffffffffu, x[r][u].x, jj) * rinv;
-        xj[r].y = __shfl_sync(0xffffffffu, x[r][u].y, jj) * rinv;
-        if (lane == jj) x[r][u] = xj[r];
-      }
-#pragma unroll
-      for (int v = u; v < NU; ++v) {
-        const int k = lane + 32 * v;
-        if (k > j && k < nb) {
-          const C rjk = Rp[offj + (k - j)];
-#pragma unroll
-          for (int r = 0; r < TS_ROWS; ++r) {
-            x[r][v].x -= xj[r].x * rjk.x - xj[r].y * rjk.y;
-            x[r][v].y -= xj[r].x * rjk.y + xj[r].y * rjk.x;
-          }
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < TS_ROWS; ++r)
-#pragma unroll
-    for (int u = 0; u < NU; ++u) {
-      const int k = lane + 32 * u;
-      if (r0 + r < n1 && k < nb) W[(long)(r0 + r) * ldw + k] = x[r][u];
-    }
-}
-
-template <typename C>
-int trsm_right_upper(C* W, long ldw, long sW, const double2* Rm, long ldr, long sR, int n1, int nb, int batch,
-                     const uint32_t* dead, cudaStream_t s) {
-  if (nb <= 0 || n1 <= 0 || batch <= 0) return TSVD_OK;
-  if (nb > 128) return TSVD_ERR_UNSUPPORTED;
-  const size_t smem = (size_t)nb * (nb + 1) / 2 * sizeof(C);
-  dim3 grid(cdiv(n1, ts_rows<C>() * TS_WARPS), batch);
+  const int np = nb * (nb + 1) / 2;
+  const size_t smem = ((size_t)np + 2 * (size_t)nb) * sizeof(GC);  // published rows + X rows
   auto go = [&](auto kern) {
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
       cudaGetLastError();
       return TSVD_ERR_CUDA;
     }
-    kern<<<grid, TS_WARPS * 32, smem, s>>>(W, ldw, sW, Rm, ldr, sR, n1, nb, dead);
+    kern<<<batch, CI_THREADS, smem, s>>>(G, ldg, sG, M, ldm, sM, nb, shift_rel, dead_rel, dead);
     TSVD_LAUNCHED();
     return TSVD_OK;
   };
-  switch ((nb + 31) / 32) {
-    case 1: return go(k_trsm_right_upper<C, 1>);
-    case 2: return go(k_trsm_right_upper<C, 2>);
-    case 3: return go(k_trsm_right_upper<C, 3>);
-    default: return go(k_trsm_right_upper<C, 4>);
+  if (np <= 2 * CI_THREADS) return go(k_chol_inv<GC, 2>);
+  if (np <= 4 * CI_THREADS) return go(k_chol_inv<GC, 4>);
+  if (np <= 8 * CI_THREADS) return go(k_chol_inv<GC, 8>);
+  return go(k_chol_inv<GC, 17>);
+}
+template int chol_inv<double2>(const double2*, long, long, double2*, long, long, int, int, double, double, uint32_t*,
+                               cudaStream_t);
+template int chol_inv<float2>(const float2*, long, long, float2*, long, long, int, int, double, double, uint32_t*,
+                              cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// W <- W M in place for the n1 x nb block of every slice (M nb x nb, upper
+// triangular, dense): a CTA stages TM_ROWS full rows of W and, kchunk rows at
+// a time, M in shared memory (all of M at once when it fits); thread
+// (ty, tx) accumulates rows ty + 16a (a < 4) and columns tx + 16u in
+// registers; column group u takes no terms from rows k >= 16 (u + 1).
+// ---------------------------------------------------------------------------
+constexpr int TM_ROWS = 64;
+template <typename C, int NU>  // NU = ceil(nb / 16) column groups per thread
+__global__ void __launch_bounds__(256) k_rmul_block(C* __restrict__ W, long ldw, long sW, const C* __restrict__ M,
+                                                  long ldm, long sM, int n1, int nb, int kchunk) {
+  using R = decltype(C().x);
+  extern __shared__ __align__(16) unsigned char rmsm[];
+  constexpr int MC = 16 * NU;
+  C* Ws = (C*)rmsm;                  // [TM_ROWS][nb + 1]
+  const int lw = nb + 1;
+  C* Ms = Ws + TM_ROWS * lw;         // [kchunk][MC]
+  const int b = blockIdx.y, tid = threadIdx.x;
+  const int r0 = blockIdx.x * TM_ROWS;
+  W += (long)b * sW;
+  M += (long)b * sM;
+  for (int r = tid >> 5; r < TM_ROWS; r += 8)
+    for (int k = tid & 31; k < nb; k += 32)
+      Ws[r * lw + k] = (r0 + r < n1) ? W[(long)(r0 + r) * ldw + k] : C{R(0), R(0)};
+  const int ty = tid >> 4, tx = tid & 15;
+  C acc[4][NU];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int u = 0; u < NU; ++u) acc[a][u] = C{R(0), R(0)};
+  for (int k0 = 0; k0 < nb; k0 += kchunk) {
+    const int kc = min(kchunk, nb - k0);
+    if (k0 > 0) __syncthreads();  // the previous chunk of M consumed
+    for (int e = tid; e < kc * MC; e += 256) {
+      const int kk = e / MC, c = e - kk * MC;
+      Ms[e] = (c < nb) ? M[(long)(k0 + kk) * ldm + c] : C{R(0), R(0)};
+    }
+    __syncthreads();
+    for (int kk = 0; kk < kc; ++kk) {
+      const int k = k0 + kk;
+      C a[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a[q] = Ws[(ty + 16 * q) * lw + k];
+      const int u0 = k >> 4;  // M(k, c) = 0 for c < k
+#pragma unroll
+      for (int u = 0; u < NU; ++u) {
+        if (u >= u0) {
+          const C mv = Ms[kk * MC + tx + 16 * u];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            acc[q][u].x = fma(a[q].x, mv.x, acc[q][u].x);
+            acc[q][u].x = fma(-a[q].y, mv.y, acc[q][u].x);
+            acc[q][u].y = fma(a[q].x, mv.y, acc[q][u].y);
+            acc[q][u].y = fma(a[q].y, mv.x, acc[q][u].y);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = r0 + ty + 16 * q;
+    if (r < n1) {
+#pragma unroll
+      for (int u = 0; u < NU; ++u) {
+        const int c = tx + 16 * u;
+        if (c < nb) W[(long)r * ldw + c] = acc[q][u];
+      }
+    }
   }
 }
-template int trsm_right_upper<double2>(double2*, long, long, const double2*, long, long, int, int, int,
-                                       const uint32_t*, cudaStream_t);
-template int trsm_right_upper<float2>(float2*, long, long, const double2*, long, long, int, int, int,
-                                      const uint32_t*, cudaStream_t);
+
+template <typename C>
+int rmul_block(C* W, long ldw, long sW, const C* M, long ldm, long sM, int n1, int nb, int batch, cudaStream_t s) {
+  if (nb <= 0 || n1 <= 0 || batch <= 0) return TSVD_OK;
+  if (nb > 128) return TSVD_ERR_UNSUPPORTED;
+  if (batch > 65535) return TSVD_ERR_UNSUPPORTED;
+  const int nu = (nb + 15) / 16;
+  const size_t wbytes = (size_t)TM_ROWS * (nb + 1) * sizeof(C), mrow = (size_t)16 * nu * sizeof(C);
+  int kchunk = nb;
+  while (wbytes + kchunk * mrow > 200 * 1024) kchunk = (kchunk + 1) / 2;
+  const size_t smem = wbytes + kchunk * mrow;
+  const dim3 grid(cdiv(n1, TM_ROWS), batch);
+  auto go = [&](auto kern) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return TSVD_ERR_CUDA;
+    }
+    kern<<<grid, 256, smem, s>>>(W, ldw, sW, M, ldm, sM, n1, nb, kchunk);
+    TSVD_LAUNCHED();
+    return TSVD_OK;
+  };
+  switch (nu) {
+    case 1: return go(k_rmul_block<C, 1>);
+    case 2: return go(k_rmul_block<C, 2>);
+    case 3: return go(k_rmul_block<C, 3>);
+    case 4: return go(k_rmul_block<C, 4>);
+    case 5: return go(k_rmul_block<C, 5>);
+    case 6: return go(k_rmul_block<C, 6>);
+    case 7: return go(k_rmul_block<C, 7>);
+    default: return go(k_rmul_block<C, 8>);
+  }
+}
+template int rmul_block<double2>(double2*, long, long, const double2*, long, long, int, int, int, cudaStream_t);
+template int rmul_block<float2>(float2*, long, long, const float2*, long, long, int, int, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Dependent Krylov columns (exact low rank, zero data): replace column c+j by

@@ -1354,6 +1354,185 @@ __global__ void __launch_bounds__(TP_THREADS) k_tridiag_pairs(int m, int R, EigS
 #undef LU
 }
 
+// Reciprocal: correctly rounded FP32 reciprocal, then one Newton correction
+// with the residual 1 - b r formed exactly (FMA) plus the low part's term.
+__device__ __forceinline__ dfl df_rcp(dfl b) {
+  const float r = __frcp_rn(b.hi);
+  const float p = b.hi * r, pe = fmaf(b.hi, r, -p);
+  const float res = ((1.0f - p) - pe) - b.lo * r;
+  return df_fast_two_sum(r, r * res);
+}
+
+// The inverse iteration of k_tridiag_pairs in double-float arithmetic (FP32
+// path): the LU of T - lam I, the solves and the normalisation carry hi + lo
+// pairs (about 48 significant bits, far below the FP32 accuracy this path
+// returns) on the FP32 pipe, so each step's dependent chain is a few FP32
+// operations rather than FP64 ones at 1/64 of the rate.  Pivots below 2^-47
+// ||T|| are raised to that size.  Factors per step (coalesced over r):
+// multiplier, reciprocal pivot and the two U super-diagonals as (hi, lo)
+// pairs, the row swaps as bits of one word per 32 steps.  The solves fetch
+// the factors TP_CHUNK steps at a time, ahead of the dependent chain.
+constexpr int TP_CHUNK = 8;
+__global__ void __launch_bounds__(TP_THREADS) k_tridiag_pairs_df(int m, int R, EigScratch e,
+                                                                 const double* __restrict__ lam_out, int iters) {
+  extern __shared__ __align__(16) double tsm[];
+  float4* T4 = (float4*)tsm;         // [m] (d_i hi, lo, f_i hi, lo), f_{m-1} = 0
+  float2* xs = (float2*)(T4 + m);    // [m][TP_THREADS] iterates
+  __shared__ double s_scale;
+  const int b = blockIdx.y, t = threadIdx.x, r = blockIdx.x * TP_THREADS + t;
+  if (t == 0) {
+    const double tn = e.tnorm[b];
+    s_scale = (tn > 0.0 && isfinite(tn)) ? 1.0 / tn : 1.0;
+  }
+  __syncthreads();
+  const double sc = s_scale;
+  for (int i = t; i < m; i += blockDim.x) {
+    const dfl dd = df_from(e.d[(long)b * m + i] * sc);
+    const dfl ff = df_from((i < m - 1) ? e.f[(long)b * m + i] * sc : 0.0);
+    T4[i] = make_float4(dd.hi, dd.lo, ff.hi, ff.lo);
+  }
+  __syncthreads();
+  if (r >= R) return;
+  double* Z = e.Z + ((long)b * R + r) * m;  // vector r, contiguous
+  if (!(e.tnorm[b] > 0.0)) {  // T = 0 (zero data): vectors e_r
+    for (int i = 0; i < m; ++i) Z[i] = (i == r) ? 1.0 : 0.0;
+    return;
+  }
+  const dfl nlam = df_neg(df_from(lam_out[(long)b * R + r] * sc));
+  // factor arrays of this slice, element i of thread r at [i * R + r]
+  float2* L0 = (float2*)(e.lu + (long)b * 5 * m * R);  // multiplier
+  float2* L1 = L0 + (long)m * R;                       // reciprocal pivot
+  float2* L2 = L1 + (long)m * R;                       // U first super-diagonal
+  float2* L3 = L2 + (long)m * R;                       // U second super-diagonal
+  unsigned* FL = (unsigned*)(L3 + (long)m * R);        // row swaps, [cdiv(m, 32)][R]
+  float2* x = xs + t;
+#define X(i) x[(long)(i) * TP_THREADS]
+  const float tiny = 0x1p-47f;
+  dfl dcur = df_add(dfl{T4[0].x, T4[0].y}, nlam), ucur = dfl{T4[0].z, T4[0].w};
+  unsigned flags = 0;
+  for (int i = 0; i < m - 1; ++i) {
+    const float4 c0 = T4[i], c1 = T4[i + 1];
+    const dfl sub = dfl{c0.z, c0.w};
+    const dfl dn = df_add(dfl{c1.x, c1.y}, nlam), un = dfl{c1.z, c1.w};
+    dfl l, rp, u1, u2;
+    if (fabsf(dcur.hi) >= fabsf(sub.hi)) {
+      const dfl piv = (fabsf(dcur.hi) < tiny) ? dfl{copysignf(tiny, dcur.hi), 0.0f} : dcur;
+      rp = df_rcp(piv);
+      l = df_mul(sub, rp);
+      u1 = ucur;
+      u2 = dfl{0.0f, 0.0f};
+      dcur = df_fma(dn, df_neg(l), ucur);
+      ucur = un;
+    } else {
+      // swap rows i and i+1: the new row i is (sub, dn, un); the old row i is eliminated
+      const dfl sb = (fabsf(sub.hi) < tiny) ? dfl{copysignf(tiny, sub.hi), 0.0f} : sub;
+      rp = df_rcp(sb);
+      l = df_mul(dcur, rp);
+      u1 = dn;
+      u2 = un;
+      const dfl nd = df_fma(ucur, df_neg(l), dn);
+      ucur = df_mul(df_neg(l), un);
+      dcur = nd;
+      flags |= 1u << (i & 31);
+    }
+    const long o = (long)i * R + r;
+    L0[o] = make_float2(l.hi, l.lo);
+    L1[o] = make_float2(rp.hi, rp.lo);
+    L2[o] = make_float2(u1.hi, u1.lo);
+    L3[o] = make_float2(u2.hi, u2.lo);
+    if ((i & 31) == 31 || i == m - 2) {
+      FL[(long)(i >> 5) * R + r] = flags;
+      flags = 0;
+    }
+  }
+  {
+    const dfl rp = df_rcp((fabsf(dcur.hi) < tiny) ? dfl{copysignf(tiny, dcur.hi), 0.0f} : dcur);
+    const long o = (long)(m - 1) * R + r;
+    L1[o] = make_float2(rp.hi, rp.lo);
+    L2[o] = make_float2(0.0f, 0.0f);
+    L3[o] = make_float2(0.0f, 0.0f);
+  }
+  for (int i = 0; i < m; ++i) {  // starting vector: Philox uniforms in (-1, 1)
+    const uint4 w = philox10(make_uint4((uint32_t)i, (uint32_t)r, (uint32_t)b, 0x1e16u), 0x2504u, 0x4989u);
+    const dfl v = df_from(((double)w.x + 0.5) * (2.0 / 4294967296.0) - 1.0);
+    X(i) = make_float2(v.hi, v.lo);
+  }
+  for (int iter = 0; iter < iters; ++iter) {
+    // row interchanges and multipliers: L^{-1} P
+    dfl xi = dfl{X(0).x, X(0).y};
+    unsigned fw = 0;
+    for (int i0 = 0; i0 < m - 1; i0 += TP_CHUNK) {
+      float2 lc[TP_CHUNK];
+#pragma unroll
+      for (int k = 0; k < TP_CHUNK; ++k)
+        lc[k] = (i0 + k < m - 1) ? __ldcg(L0 + (long)(i0 + k) * R + r) : make_float2(0.0f, 0.0f);
+      if ((i0 & 31) == 0) fw = __ldcg(FL + (long)(i0 >> 5) * R + r);
+#pragma unroll
+      for (int k = 0; k < TP_CHUNK; ++k) {
+        const int i = i0 + k;
+        if (i < m - 1) {
+          const float2 xv = X(i + 1);
+          dfl xn = dfl{xv.x, xv.y};
+          if ((fw >> (i & 31)) & 1u) {
+            const dfl tmp = xi;
+            xi = xn;
+            xn = tmp;
+          }
+          X(i) = make_float2(xi.hi, xi.lo);
+          xi = df_fma(xn, dfl{-lc[k].x, -lc[k].y}, xi);
+        }
+      }
+    }
+    X(m - 1) = make_float2(xi.hi, xi.lo);
+    // back substitution with U
+    dfl x1 = dfl{0.0f, 0.0f}, x2 = dfl{0.0f, 0.0f};
+    float mx = 0.0f;
+    for (int i0 = m - 1; i0 >= 0; i0 -= TP_CHUNK) {
+      float2 pc[TP_CHUNK], ac[TP_CHUNK], bc[TP_CHUNK];
+#pragma unroll
+      for (int k = 0; k < TP_CHUNK; ++k) {
+        const int i = i0 - k;
+        const bool ok = i >= 0;
+        const long o = (long)(ok ? i : 0) * R + r;
+        pc[k] = ok ? __ldcg(L1 + o) : make_float2(0.0f, 0.0f);
+        ac[k] = ok ? __ldcg(L2 + o) : make_float2(0.0f, 0.0f);
+        bc[k] = ok ? __ldcg(L3 + o) : make_float2(0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int k = 0; k < TP_CHUNK; ++k) {
+        const int i = i0 - k;
+        if (i >= 0) {
+          const float2 xv = X(i);
+          dfl s = df_fma(dfl{xv.x, xv.y}, dfl{-ac[k].x, -ac[k].y}, x1);
+          s = df_fma(s, dfl{-bc[k].x, -bc[k].y}, x2);
+          s = df_mul(s, dfl{pc[k].x, pc[k].y});
+          X(i) = make_float2(s.hi, s.lo);
+          x2 = x1;
+          x1 = s;
+          mx = fmaxf(mx, fabsf(s.hi));
+        }
+      }
+    }
+    // rescale by a power of two (exact) so that the largest component is in [1, 2)
+    if (mx > 0.0f && mx <= FLT_MAX) {
+      const int ex = (int)((__float_as_uint(mx) >> 23) & 0xffu) - 127;
+      const float s2 = ldexpf(1.0f, -ex);
+      for (int i = 0; i < m; ++i) {
+        const float2 v = X(i);
+        X(i) = make_float2(v.x * s2, v.y * s2);
+      }
+    }
+  }
+  dfl nrm2 = dfl{0.0f, 0.0f};
+  for (int i = 0; i < m; ++i) {
+    const dfl v = dfl{X(i).x, X(i).y};
+    nrm2 = df_fma(nrm2, v, v);
+  }
+  const dfl inv = df_rcp(df_sqrt(nrm2));
+  for (int i = 0; i < m; ++i) Z[i] = df_to(df_mul(dfl{X(i).x, X(i).y}, inv));
+#undef X
+}
+
 // Inside clusters of close eigenvalues (gap < 1e-3 ||T||) the vectors are
 // made orthonormal: two classical Gram-Schmidt passes against the earlier
 // members of the cluster, then normalisation.
@@ -1578,7 +1757,14 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
       cudaFuncSetAttribute(k_tridiag_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tp);
     // solves: 3 (FP64 path), 2 on the FP32 path (eigenvalues to 3e-13 ||T|| already make one solve
     // amplify the wanted direction by gap / 3e-13; the vectors end in FP32)
-    k_tridiag_pairs<<<dim3(cdiv(R, TP_THREADS), batch), TP_THREADS, smem_tp, s>>>(m, R, e, lam, kDoubleFloat ? 2 : 3);
+    if (kDoubleFloat) {
+      const size_t smem_df = (size_t)m * (sizeof(float4) + TP_THREADS * sizeof(float2));
+      if (smem_df > 48 * 1024)
+        cudaFuncSetAttribute(k_tridiag_pairs_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df);
+      k_tridiag_pairs_df<<<dim3(cdiv(R, TP_THREADS), batch), TP_THREADS, smem_df, s>>>(m, R, e, lam, 2);
+    } else {
+      k_tridiag_pairs<<<dim3(cdiv(R, TP_THREADS), batch), TP_THREADS, smem_tp, s>>>(m, R, e, lam, 3);
+    }
     TSVD_LAUNCHED();
   }
   {

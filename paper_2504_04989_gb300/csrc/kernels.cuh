@@ -66,19 +66,19 @@ int copy_cx(const C* src, long lds, long ss, C* dst, long ldd, long sd, int rows
             cudaStream_t s);
 
 // cholqr.cu -- block orthonormalisation pieces (one problem per Fourier slice)
-// Cholesky R^H R = G + s I (FP64) of the nb x nb Hermitian Gram G of precision
-// GC (s = shift_rel * trace(G) when shift_rel > 0).  R is written dense upper
-// triangular (zeros below).  Pivots: shifted pass -> dead iff d_j <= 0; plain
-// pass -> dead iff d_j <= dead_rel * G_jj.  Dead columns are marked in `dead`
-// (4 words per slice) and get R_jj = 1, R_jk = 0.
+// Cholesky R^H R = G + s I of the nb x nb Hermitian Gram G (s = shift_rel *
+// trace(G) when shift_rel > 0) in G's precision, then M = R-tilde^{-1} written
+// dense (zeros below the diagonal) in the same precision.  Pivots: shifted
+// pass -> dead iff d_j <= 0; plain pass -> dead iff d_j <= dead_rel * G_jj.
+// Dead columns are marked in `dead` (4 words per slice); R-tilde has unit
+// rows and columns there and M zero columns, so W M = W_live R_live^{-1} on
+// the live columns and 0 on the dead ones.
 template <typename GC>
-int chol_upper(const GC* G, long ldg, long sG, double2* Rm, long ldr, long sR, int nb, int batch, double shift_rel,
-               double dead_rel, uint32_t* dead, cudaStream_t s);
-// W <- W R^{-1} in place (W's precision) for the n1 x nb blocks of every
-// slice; dead columns come out zero.
+int chol_inv(const GC* G, long ldg, long sG, GC* M, long ldm, long sM, int nb, int batch, double shift_rel,
+             double dead_rel, uint32_t* dead, cudaStream_t s);
+// W <- W M in place for the n1 x nb blocks of every slice (M nb x nb dense).
 template <typename C>
-int trsm_right_upper(C* W, long ldw, long sW, const double2* Rm, long ldr, long sR, int n1, int nb, int batch,
-                     const uint32_t* dead, cudaStream_t s);
+int rmul_block(C* W, long ldw, long sW, const C* M, long ldm, long sM, int n1, int nb, int batch, cudaStream_t s);
 // Replace dead columns [c, c+nb) of Q (n1 x ldq per slice) by unit vectors
 // orthogonal to columns [0, c+nb): Philox directions projected twice.
 template <typename C>

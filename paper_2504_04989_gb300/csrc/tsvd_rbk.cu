@@ -213,13 +213,14 @@ static int orth_block(const RbkDims& d, RbkWs<T>& w, int c, int nb, int block_id
       TSVD_STAGE("orth_gram", s);
       TSVD_TRY(cgemm<CL>(gemm('H', 'N', nb, nb, n1, 1.0, W, b, sW, W, b, sW, 0.0, Gs, b, sG, h), w.splitk, sk, s));
     }
+    CL* Mi = (CL*)w.Rs;  // R-tilde^{-1}, nb x nb per slice (leading dimension b)
     {
       TSVD_STAGE("orth_chol", s);
-      TSVD_TRY(chol_upper<CL>(Gs, b, sG, w.Rs, b, sG, nb, h, pass == 0 ? shift : 0.0, dead_rel, w.dead, s));
+      TSVD_TRY(chol_inv<CL>(Gs, b, sG, Mi, b, sG, nb, h, pass == 0 ? shift : 0.0, dead_rel, w.dead, s));
     }
     {
       TSVD_STAGE("orth_trsm", s);
-      TSVD_TRY(trsm_right_upper<CL>(W, b, sW, w.Rs, b, sG, n1, nb, h, w.dead, s));
+      TSVD_TRY(rmul_block<CL>(W, b, sW, Mi, b, sG, n1, nb, h, s));
     }
   }
   {
