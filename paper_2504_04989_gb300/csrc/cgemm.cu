@@ -3,8 +3,10 @@
 // One CTA computes a 64 x 64 tile of one slice's product with 256 threads,
 // each holding a 4 x 4 complex register tile (rows ty + 16 i, columns
 // tx + 16 j, so a warp's shared-memory reads are contiguous).  op(A) and op(B)
-// tiles are staged in shared memory k-major; the conjugate transpose is taken
-// while staging, reading the stored matrix along its contiguous dimension.
+// tiles are staged in shared memory k-major, in two stages: the next k-tile is
+// loaded into registers while the current one is multiplied; the conjugate
+// transpose is taken while staging, reading the stored matrix along its
+// contiguous dimension.
 // Thin products (long K, small M x N) split K across CTAs and reduce the
 // partial tiles in a fixed order (deterministic, no atomics).
 #include "common.cuh"
@@ -31,9 +33,11 @@ template <typename C, bool AH, bool BH>
 __global__ void __launch_bounds__(256) k_cgemm(GemmArgs g, C* __restrict__ ws, int ksplit, int kchunk, int tiles_m,
                                                int herm_upper) {
   constexpr int BK = GemmCfg<C>::BK;
+  constexpr int NA = GBM * BK / 256, NB = GBN * BK / 256;  // staged elements per thread
   using R = typename GemmCfg<C>::R;
-  __shared__ __align__(16) C As[BK][GBM];
-  __shared__ __align__(16) C Bs[BK][GBN];
+  // two stages; rows padded by one element so the transposed stores hit distinct banks
+  __shared__ __align__(16) C As[2][BK][GBM + 1];
+  __shared__ __align__(16) C Bs[2][BK][GBN + 1];
   const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
   if (herm_upper && tm > tn) return;  // Hermitian product: the lower tiles are mirrored afterwards
   const int bi = blockIdx.z / ksplit, kz = blockIdx.z % ksplit;
@@ -48,39 +52,65 @@ __global__ void __launch_bounds__(256) k_cgemm(GemmArgs g, C* __restrict__ ws, i
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = mkc(R(0), R(0));
 
-  for (int k0 = kb; k0 < ke; k0 += BK) {
-    for (int idx = tid; idx < GBM * BK; idx += 256) {
+  // the next k-tile is fetched into registers while the current one is multiplied
+  C ra[NA], rb[NB];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int t = 0; t < NA; ++t) {
+      const int idx = tid + 256 * t;
       int mm, kk;
       if (!AH) { kk = idx % BK; mm = idx / BK; }
       else { mm = idx % GBM; kk = idx / GBM; }
       const int gm = m0 + mm, gk = k0 + kk;
       C v = mkc(R(0), R(0));
       if (gm < g.M && gk < ke) v = AH ? cconj(A[(long)gk * g.lda + gm]) : A[(long)gm * g.lda + gk];
-      As[kk][mm] = v;
+      ra[t] = v;
     }
-    for (int idx = tid; idx < GBN * BK; idx += 256) {
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const int idx = tid + 256 * t;
       int nn, kk;
       if (!BH) { nn = idx % GBN; kk = idx / GBN; }
       else { kk = idx % BK; nn = idx / BK; }
       const int gn = n0 + nn, gk = k0 + kk;
       C v = mkc(R(0), R(0));
       if (gn < g.N && gk < ke) v = BH ? cconj(B[(long)gn * g.ldb + gk]) : B[(long)gk * g.ldb + gn];
-      Bs[kk][nn] = v;
+      rb[t] = v;
     }
-    __syncthreads();
+  };
+  auto stash = [&](int st) {
+#pragma unroll
+    for (int t = 0; t < NA; ++t) {
+      const int idx = tid + 256 * t;
+      if (!AH) As[st][idx % BK][idx / BK] = ra[t];
+      else As[st][idx / GBM][idx % GBM] = ra[t];
+    }
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const int idx = tid + 256 * t;
+      if (!BH) Bs[st][idx / GBN][idx % GBN] = rb[t];
+      else Bs[st][idx % BK][idx / BK] = rb[t];
+    }
+  };
+  if (kb < ke) fetch(kb);
+  int st = 0;
+  for (int k0 = kb; k0 < ke; k0 += BK) {
+    stash(st);
+    __syncthreads();  // stage st complete; the stage written next was last read before this barrier
+    if (k0 + BK < ke) fetch(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       C a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < 4; ++i) a[i] = As[st][kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < 4; ++j) b[j] = Bs[st][kk][tx + 16 * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
     }
-    __syncthreads();
+    st ^= 1;
   }
   C* __restrict__ Cm = (C*)g.C + (long)bi * g.sC;
 #pragma unroll

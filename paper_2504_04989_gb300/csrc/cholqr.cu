@@ -44,19 +44,21 @@ __global__ void __launch_bounds__(CI_THREADS) k_chol_inv(const GC* __restrict__ 
                                                        uint32_t* __restrict__ dead_out) {
   using Rt = decltype(GC().x);
   extern __shared__ __align__(16) unsigned char chsm[];
-  GC* S = (GC*)chsm;            // published rows of the packed triangle: S(i, k) = S[rb(i) + k]
+  GC* S = (GC*)chsm;               // published rows of the packed triangle: S(i, k) = S[rb(i) + k]
   GC* Xr = S + nb * (nb + 1) / 2;  // [2][nb] published rows of X
-  __shared__ Rt dg[128];        // diagonal of G (pivot test of the plain passes)
-  __shared__ Rt dj[128];        // pivots d_j (0 for a dead column)
-  __shared__ Rt ri[128];        // 1 / R-tilde_jj
+  __shared__ Rt dg[128];           // diagonal of G (pivot test of the plain passes)
+  __shared__ Rt dj[128];           // pivots d_j (0 for a dead column)
+  __shared__ Rt pinv[128];         // 1 / d_j (0 for a dead column)
+  __shared__ Rt ri[128];           // 1 / R-tilde_jj
   __shared__ double red[CI_THREADS / 32];
   const int b = blockIdx.x, tid = threadIdx.x;
   const int np = nb * (nb + 1) / 2;
   auto rb = [nb](int i) { return i * nb - (i * (i + 1)) / 2; };  // packed offset of row i, minus i
   G += (long)b * sG;
   Mo += (long)b * sM;
-  // owned entries: (row, column) and value
-  int ei[EPT], ek[EPT];
+  if (tid < nb) dg[tid] = G[(long)tid * ldg + tid].x;
+  // owned entries: (row, column) (-1 if none), packed offset and value
+  int ei[EPT], ek[EPT], eo[EPT];
   GC v[EPT];
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
@@ -73,46 +75,62 @@ __global__ void __launch_bounds__(CI_THREADS) k_chol_inv(const GC* __restrict__ 
     }
     ei[e] = i;
     ek[e] = k;
+    eo[e] = (p < np) ? p : 0;
     v[e] = (p < np) ? G[(long)i * ldg + k] : GC{Rt(0), Rt(0)};
   }
-  if (tid < nb) dg[tid] = G[(long)tid * ldg + tid].x;
   __syncthreads();
   const double trace = block_sum(tid < nb ? (double)dg[tid] : 0.0, red);
   const Rt sft = (shift_rel > 0.0) ? (Rt)(shift_rel * trace) : Rt(0);
+  // a final diagonal entry d_i: pivot test, published with its row
+  auto pivot = [&](int i, Rt d) {
+    const bool dead = (shift_rel > 0.0) ? !(d > Rt(0)) : !(d > (Rt)dead_rel * dg[i]);
+    dj[i] = dead ? Rt(0) : d;
+    pinv[i] = dead ? Rt(0) : Rt(1) / d;
+  };
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
     if (ei[e] >= 0 && ei[e] == ek[e]) v[e].x += sft;
-    if (ei[e] == 0) S[ek[e]] = v[e];  // row 0 is final
+    if (ei[e] == 0) {  // row 0 is final
+      S[eo[e]] = v[e];
+      if (ek[e] == 0) pivot(0, v[e].x);
+    }
   }
   __syncthreads();
+  // every step is branch-free: the operands of each entry are loaded whether or not it is
+  // active (in-range addresses), and the update is selected
   for (int j = 0; j < nb; ++j) {
     const GC* Sj = S + rb(j);
-    const Rt d = Sj[j].x;
-    const bool dead = (shift_rel > 0.0) ? !(d > Rt(0)) : !(d > (Rt)dead_rel * dg[j]);
-    if (tid == 0) dj[j] = dead ? Rt(0) : d;
-    const Rt inv = dead ? Rt(0) : Rt(1) / d;  // a dead column leaves the trailing rows unchanged
+    const Rt inv = pinv[j];
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
       const int i = ei[e], k = ek[e];
-      if (i > j) {
-        const GC a = Sj[i];
-        const GC c = Sj[k];
-        const Rt ax = a.x * inv, ay = a.y * inv;  // conj(a) / d times c
-        v[e].x = fma(-ax, c.x, v[e].x);
-        v[e].x = fma(-ay, c.y, v[e].x);
-        v[e].y = fma(-ax, c.y, v[e].y);
-        v[e].y = fma(ay, c.x, v[e].y);
-        if (i == j + 1) S[rb(i) + k] = v[e];  // row j+1 is final
+      const GC a = Sj[max(i, 0)];
+      const GC c = Sj[max(k, 0)];
+      const Rt ax = a.x * inv, ay = a.y * inv;  // conj(a) / d times c
+      GC t = v[e];
+      t.x = fma(-ax, c.x, t.x);
+      t.x = fma(-ay, c.y, t.x);
+      t.y = fma(-ax, c.y, t.y);
+      t.y = fma(ay, c.x, t.y);
+      if (i > j) v[e] = t;
+      if (i == j + 1) {  // row j+1 is final
+        S[eo[e]] = v[e];
+        if (k == i) pivot(i, v[e].x);
       }
     }
     __syncthreads();
   }
   if (tid < nb) ri[tid] = (dj[tid] > Rt(0)) ? Rt(1) / sqrt(dj[tid]) : Rt(1);
   __syncthreads();
-  // inverse: B in the registers (0 above the diagonal, 1 on it), R-tilde(i, l) = R(i, l) / sqrt(d_i)
+  // inverse: B in the registers (0 above the diagonal, 1 on it); R-tilde(i, l) = R(i, l) / sqrt(d_i)
   // read from the published rows (0 where row i or column l is dead)
+  Rt er[EPT];  // 1 / R-tilde_ii of the entry's row, 0 for a dead row
 #pragma unroll
-  for (int e = 0; e < EPT; ++e) v[e] = GC{Rt(0), Rt(0)};
+  for (int e = 0; e < EPT; ++e) {
+    const int i = max(ei[e], 0);
+    er[e] = (dj[i] > Rt(0)) ? ri[i] : Rt(0);
+    v[e] = GC{Rt(0), Rt(0)};
+  }
   for (int l = nb - 1; l >= 1; --l) {
     const GC* xl = Xr + (l & 1) * nb;  // X(l, k), k > l
     const Rt rl = ri[l];
@@ -120,26 +138,21 @@ __global__ void __launch_bounds__(CI_THREADS) k_chol_inv(const GC* __restrict__ 
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
       const int i = ei[e], k = ek[e];
-      if (i >= 0 && i < l && k >= l) {
-        GC c = S[rb(i) + l];
-        const Rt sc = (live_l && dj[i] > Rt(0)) ? ri[i] : Rt(0);
-        c.x *= sc;
-        c.y *= sc;
-        GC x;
-        if (k == l) {
-          x.x = rl;
-          x.y = Rt(0);
-        } else {
-          x = xl[k];
-        }
-        v[e].x = fma(-c.x, x.x, v[e].x);
-        v[e].x = fma(c.y, x.y, v[e].x);
-        v[e].y = fma(-c.x, x.y, v[e].y);
-        v[e].y = fma(-c.y, x.x, v[e].y);
-      }
+      const int ic = max(i, 0), kc = max(k, 0);
+      const GC cr = S[rb(ic) + l];
+      const GC xv = xl[kc];
+      const Rt sc = live_l ? er[e] : Rt(0);
+      const Rt cx = cr.x * sc, cy = cr.y * sc;
+      const GC x = (k == l) ? GC{rl, Rt(0)} : xv;
+      GC t = v[e];
+      t.x = fma(-cx, x.x, t.x);
+      t.x = fma(cy, x.y, t.x);
+      t.y = fma(-cx, x.y, t.y);
+      t.y = fma(-cy, x.x, t.y);
+      if (i >= 0 && i < l && k >= l) v[e] = t;
       if (i == l - 1 && k > i) {  // row l-1 of B is final: publish X(l-1, k)
-        const Rt s = ri[i];
-        Xr[((l - 1) & 1) * nb + k] = GC{v[e].x * s, v[e].y * s};
+        const Rt s2 = ri[i];
+        Xr[((l - 1) & 1) * nb + k] = GC{v[e].x * s2, v[e].y * s2};
       }
     }
     __syncthreads();
@@ -201,6 +214,15 @@ template int chol_inv<double2>(const double2*, long, long, double2*, long, long,
 template int chol_inv<float2>(const float2*, long, long, float2*, long, long, int, int, double, double, uint32_t*,
                               cudaStream_t);
 
+// asynchronous global -> shared copy of one complex element (8 or 16 bytes)
+template <typename C>
+__device__ __forceinline__ void cp_async_elem(C* dst, const C* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(C) == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src));
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // W <- W M in place for the n1 x nb block of every slice (M nb x nb, upper
 // triangular, dense): a CTA stages TM_ROWS full rows of W and, kchunk rows at
@@ -222,9 +244,12 @@ __global__ void __launch_bounds__(256) k_rmul_block(C* __restrict__ W, long ldw,
   const int r0 = blockIdx.x * TM_ROWS;
   W += (long)b * sW;
   M += (long)b * sM;
+  // asynchronous copies: every element of the rows and of the chunk of M is in flight at once
   for (int r = tid >> 5; r < TM_ROWS; r += 8)
-    for (int k = tid & 31; k < nb; k += 32)
-      Ws[r * lw + k] = (r0 + r < n1) ? W[(long)(r0 + r) * ldw + k] : C{R(0), R(0)};
+    for (int k = tid & 31; k < nb; k += 32) {
+      if (r0 + r < n1) cp_async_elem(Ws + r * lw + k, W + (long)(r0 + r) * ldw + k);
+      else Ws[r * lw + k] = C{R(0), R(0)};
+    }
   const int ty = tid >> 4, tx = tid & 15;
   C acc[4][NU];
 #pragma unroll
@@ -236,8 +261,10 @@ __global__ void __launch_bounds__(256) k_rmul_block(C* __restrict__ W, long ldw,
     if (k0 > 0) __syncthreads();  // the previous chunk of M consumed
     for (int e = tid; e < kc * MC; e += 256) {
       const int kk = e / MC, c = e - kk * MC;
-      Ms[e] = (c < nb) ? M[(long)(k0 + kk) * ldm + c] : C{R(0), R(0)};
+      if (c < nb) cp_async_elem(Ms + e, M + (long)(k0 + kk) * ldm + c);
+      else Ms[e] = C{R(0), R(0)};
     }
+    cp_async_wait_all();
     __syncthreads();
     for (int kk = 0; kk < kc; ++kk) {
       const int k = k0 + kk;
