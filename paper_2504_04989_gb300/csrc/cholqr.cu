@@ -24,9 +24,10 @@ namespace tsvd {
 //   vector (so R-tilde = diag(R_live, I) up to a permutation);
 //   M: R-tilde^{-1} with the dead columns set to zero, so that W M is
 //   W_live R_live^{-1} on the live columns and zero on the dead ones.
-// Thread t keeps the entries p = t, t + CI_THREADS, ... of the packed upper
-// triangle (row-major) in registers, so each step is one round of independent
-// register updates between two barriers:
+// Warp w keeps the entries [32 EPT w, 32 EPT (w+1)) of the packed upper
+// triangle (row-major; lane-strided) in registers, so each step is one round
+// of independent register updates between two barriers, and a warp whose rows
+// are all finished skips the step:
 //   factorisation, step j: S(i,k) -= conj(S(j,i)) S(j,k) / d_j for
 //   j < i <= k, with row j read from shared memory, where its owners
 //   published it when it became final (end of step j-1); the published rows
@@ -57,20 +58,29 @@ __global__ void __launch_bounds__(CI_THREADS) k_chol_inv(const GC* __restrict__ 
   G += (long)b * sG;
   Mo += (long)b * sM;
   if (tid < nb) dg[tid] = G[(long)tid * ldg + tid].x;
+  // row of packed index p: largest i with rb(i) + i <= p (closed form, then corrected)
+  auto row_of = [&](int p) {
+    const double q = 2.0 * nb + 1.0;
+    int i = (int)((q - sqrt(q * q - 8.0 * p)) * 0.5);
+    i = max(0, min(i, nb - 1));
+    while (i > 0 && rb(i) + i > p) --i;
+    while (i + 1 < nb && rb(i + 1) + i + 1 <= p) ++i;
+    return i;
+  };
+  // warp w owns the packed range [32 EPT w, 32 EPT (w+1)), lane-strided; its first and last
+  // rows decide when it has nothing left to do (rows <= j in the factorisation, >= l in the inverse)
+  const int warp = tid >> 5, lane = tid & 31;
+  const int pw0 = 32 * EPT * warp, pw1 = min(pw0 + 32 * EPT, np) - 1;
+  const int wrow0 = (pw0 < np) ? row_of(pw0) : nb, wrow1 = (pw0 < np) ? row_of(pw1) : -1;
   // owned entries: (row, column) (-1 if none), packed offset and value
   int ei[EPT], ek[EPT], eo[EPT];
   GC v[EPT];
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
-    const int p = tid + e * CI_THREADS;
+    const int p = pw0 + 32 * e + lane;
     int i = -1, k = -1;
     if (p < np) {
-      // row i: largest i with rb(i) + i <= p (closed form, then corrected)
-      const double q = 2.0 * nb + 1.0;
-      i = (int)((q - sqrt(q * q - 8.0 * p)) * 0.5);
-      i = max(0, min(i, nb - 1));
-      while (i > 0 && rb(i) + i > p) --i;
-      while (i + 1 < nb && rb(i + 1) + i + 1 <= p) ++i;
+      i = row_of(p);
       k = p - rb(i);
     }
     ei[e] = i;
@@ -101,6 +111,7 @@ __global__ void __launch_bounds__(CI_THREADS) k_chol_inv(const GC* __restrict__ 
   for (int j = 0; j < nb; ++j) {
     const GC* Sj = S + rb(j);
     const Rt inv = pinv[j];
+    if (wrow1 > j) {
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
       const int i = ei[e], k = ek[e];
@@ -117,6 +128,7 @@ __global__ void __launch_bounds__(CI_THREADS) k_chol_inv(const GC* __restrict__ 
         S[eo[e]] = v[e];
         if (k == i) pivot(i, v[e].x);
       }
+    }
     }
     __syncthreads();
   }
@@ -135,6 +147,7 @@ __global__ void __launch_bounds__(CI_THREADS) k_chol_inv(const GC* __restrict__ 
     const GC* xl = Xr + (l & 1) * nb;  // X(l, k), k > l
     const Rt rl = ri[l];
     const bool live_l = dj[l] > Rt(0);
+    if (wrow0 < l) {
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
       const int i = ei[e], k = ek[e];
@@ -154,6 +167,7 @@ __global__ void __launch_bounds__(CI_THREADS) k_chol_inv(const GC* __restrict__ 
         const Rt s2 = ri[i];
         Xr[((l - 1) & 1) * nb + k] = GC{v[e].x * s2, v[e].y * s2};
       }
+    }
     }
     __syncthreads();
   }
@@ -195,7 +209,8 @@ int chol_inv(const GC* G, long ldg, long sG, GC* M, long ldm, long sM, int nb, i
   const int np = nb * (nb + 1) / 2;
   const size_t smem = ((size_t)np + 2 * (size_t)nb) * sizeof(GC);  // published rows + X rows
   auto go = [&](auto kern) {
-    if (smem > 48 * 1024 &&
+    // with the kernel's static arrays (about 4 KB) the total passes the 48 KB default earlier
+    if (smem > 40 * 1024 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
       cudaGetLastError();
       return TSVD_ERR_CUDA;

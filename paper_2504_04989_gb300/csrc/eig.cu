@@ -1534,19 +1534,28 @@ __global__ void __launch_bounds__(TP_THREADS) k_tridiag_pairs_df(int m, int R, E
 }
 
 // Inside clusters of close eigenvalues (gap < 1e-3 ||T||) the vectors are
-// made orthonormal: two classical Gram-Schmidt passes against the earlier
-// members of the cluster, then normalisation.
-// CT: arithmetic of the two Gram-Schmidt passes (FP32 on the FP32 path, whose
-// vectors are rounded to FP32 right after; FP64 otherwise).  The slice's R
-// vectors are staged in shared memory for the whole kernel (the passes are a
-// chain of short dependent steps, so every operand should be one shared-memory
-// access away); one warp per dot product.
+// made orthonormal.  On the FP32 path (CT = float) a cluster of at most
+// CO_BLOCK vectors is orthonormalised as a block by CholeskyQR2: G = Z_c^T Z_c,
+// G = R^T R (CTA-wide right-looking factorisation, one barrier per column),
+// Z_c <- Z_c R^{-1}, twice -- the basis Gram-Schmidt in eigenvalue order gives,
+// in exact arithmetic.  The inverse-iteration vectors of a cluster are close
+// to orthonormal already; a pivot below 1e-5 (condition number above about
+// 300, beyond what two FP32 passes restore) sends the cluster to two classical
+// Gram-Schmidt passes per vector against its earlier members, then
+// normalisation, which also serves larger clusters and the FP64 path.
+// CT: storage and arithmetic (FP32 on the FP32 path, whose vectors are
+// rounded to FP32 right after; FP64 otherwise).  The slice's R vectors are
+// staged in shared memory for the whole kernel when they fit.
 constexpr int CO_THREADS = 1024;
+constexpr int CO_BLOCK = 64;
 template <typename CT, bool STAGED>  // !STAGED (vectors too large for shared memory): CT = double, in place in Z
 __global__ void __launch_bounds__(CO_THREADS) k_cluster_orth(int m, int R, EigScratch e, const double* __restrict__ lam) {
   extern __shared__ __align__(16) unsigned char cosm[];
   __shared__ double red[32];
   __shared__ CT dots[128];
+  constexpr bool kBlock = std::is_same<CT, float>::value;
+  __shared__ float Gs[kBlock ? CO_BLOCK * CO_BLOCK : 1];  // Gram, then R (upper, row-major)
+  __shared__ float Rd[kBlock ? CO_BLOCK : 1];             // 1 / R_jj
   const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   double* Z = e.Z + (long)b * R * m;  // vector r at Z + r*m
   const double* l = lam + (long)b * R;
@@ -1560,82 +1569,191 @@ __global__ void __launch_bounds__(CO_THREADS) k_cluster_orth(int m, int R, EigSc
     for (int q = tid; q < R * m; q += blockDim.x) zsm[q] = (CT)Z[q];
     __syncthreads();
   }
-  int c0 = 0;
-  for (int r = 1; r < R; ++r) {
-    if (l[r - 1] - l[r] > tol) {
-      c0 = r;
-      continue;
-    }
-    CT* zr = zsm + (long)r * m;
+  // CholeskyQR2 of vectors [c0, c0 + nc) (FP32); false on a small pivot (vectors as after the
+  // last completed pass)
+  auto block_qr = [&](int c0, int nc) -> bool {
+    float* zc = (float*)zsm + (long)c0 * m;
     for (int pass = 0; pass < 2; ++pass) {
-      for (int s = c0 + warp; s < r; s += nwarp) {
-        const CT* zs = zsm + (long)s * m;
-        CT acc = 0;
-        for (int i = lane; i < m; i += 32) acc += zs[i] * zr[i];
-        acc = warp_sum(acc);
-        if (lane == 0) dots[s - c0] = acc;
-      }
+      for (int a = 0; a < nc; ++a)
+        for (int bb = a + warp; bb < nc; bb += nwarp) {
+          float acc = 0.f;
+          for (int i = lane; i < m; i += 32) acc = fmaf(zc[(long)a * m + i], zc[(long)bb * m + i], acc);
+          acc = warp_sum(acc);
+          if (lane == 0) Gs[a * CO_BLOCK + bb] = acc;
+        }
       __syncthreads();
-      for (int i = tid; i < m; i += blockDim.x) {
-        CT acc = zr[i];
-        for (int s = c0; s < r; ++s) acc -= dots[s - c0] * zsm[(long)s * m + i];
-        zr[i] = acc;
+      // G(a, k) -= G(j, a) G(j, k) / d_j for j < a <= k; row j scaled by 1/sqrt(d_j) afterwards
+      for (int j = 0; j < nc; ++j) {
+        const float d = Gs[j * CO_BLOCK + j];
+        if (!(d > 1e-5f)) return false;  // uniform: every thread reads the same pivot
+        const float id = 1.0f / d;
+        const int k = j + 1 + (tid & 63);
+        for (int a = j + 1 + (tid >> 6); a <= k && k < nc; a += CO_THREADS / 64)
+          Gs[a * CO_BLOCK + k] -= Gs[j * CO_BLOCK + a] * Gs[j * CO_BLOCK + k] * id;
+        __syncthreads();
+      }
+      if (tid < nc) Rd[tid] = 1.0f / sqrtf(Gs[tid * CO_BLOCK + tid]);
+      __syncthreads();
+      for (int i = tid; i < m; i += blockDim.x) {  // row i of Z_c: x R = z by forward substitution, in place
+        for (int bb = 0; bb < nc; ++bb) {
+          float acc = zc[(long)bb * m + i];
+          for (int a = 0; a < bb; ++a) acc = fmaf(-zc[(long)a * m + i], Gs[a * CO_BLOCK + bb] * Rd[a], acc);
+          zc[(long)bb * m + i] = acc * Rd[bb];
+        }
       }
       __syncthreads();
     }
-    double part = 0;
-    for (int i = tid; i < m; i += blockDim.x) part += (double)zr[i] * (double)zr[i];
-    const CT inv = (CT)(1.0 / sqrt(block_sum(part, red)));
-    for (int i = tid; i < m; i += blockDim.x) zr[i] *= inv;
-    __syncthreads();
+    return true;
+  };
+  auto cgs2 = [&](int c0, int c1) {
+    for (int r = c0 + 1; r < c1; ++r) {
+      CT* zr = zsm + (long)r * m;
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int s2 = c0 + warp; s2 < r; s2 += nwarp) {
+          const CT* zs = zsm + (long)s2 * m;
+          CT acc = 0;
+          for (int i = lane; i < m; i += 32) acc += zs[i] * zr[i];
+          acc = warp_sum(acc);
+          if (lane == 0) dots[s2 - c0] = acc;
+        }
+        __syncthreads();
+        for (int i = tid; i < m; i += blockDim.x) {
+          CT acc = zr[i];
+          for (int s2 = c0; s2 < r; ++s2) acc -= dots[s2 - c0] * zsm[(long)s2 * m + i];
+          zr[i] = acc;
+        }
+        __syncthreads();
+      }
+      double part = 0;
+      for (int i = tid; i < m; i += blockDim.x) part += (double)zr[i] * (double)zr[i];
+      const CT inv = (CT)(1.0 / sqrt(block_sum(part, red)));
+      for (int i = tid; i < m; i += blockDim.x) zr[i] *= inv;
+      __syncthreads();
+    }
+  };
+  int c0 = 0;
+  for (int r = 1; r <= R; ++r) {
+    if (r < R && !(l[r - 1] - l[r] > tol)) continue;  // r extends the cluster starting at c0
+    const int nc = r - c0;
+    bool done = nc < 2;
+    if constexpr (kBlock) done = done || (nc <= CO_BLOCK && block_qr(c0, nc));
+    if (!done) cgs2(c0, r);
+    c0 = r;
   }
   if (STAGED)
     for (int q = tid; q < R * m; q += blockDim.x) Z[q] = (double)zsm[q];
 }
 
-// u_r = H_0 H_1 .. H_{m-2} D z_r, one warp per eigenvector, in the precision
-// of the output (the FP32 path rounds U_c to FP32 for its GEMMs anyway).
-constexpr int BT_WARPS = 8;
-template <typename C>
-__global__ void __launch_bounds__(BT_WARPS * 32) k_backtransform(int m, int R, EigScratch e, C* __restrict__ U,
-                                                                 long ldu, long sU, int hv32) {
+// u_r = H_0 H_1 .. H_{m-2} D z_r in the precision of the output (the FP32
+// path rounds U_c to FP32 for its GEMMs anyway): BT_VPC eigenvectors per CTA,
+// one warp each, the vector in the warp's registers (entry i in lane i % 32,
+// slot i / 32).  The reflectors (VT: float2 copies from the double-float
+// reduction, else double2) are staged in shared memory by asynchronous copies
+// one reflector ahead, three buffers deep (one barrier per reflector), and
+// read by all the CTA's warps; slots wholly at or above row j are skipped.
+constexpr int BT_VPC = 16;
+__device__ __forceinline__ void bt_copy(float2* dst, const float2* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src));
+}
+__device__ __forceinline__ void bt_copy(double2* dst, const double2* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src));
+}
+template <typename C, typename VT, int NPL>  // NPL >= ceil(m / 32)
+__global__ void __launch_bounds__(BT_VPC * 32) k_backtransform(int m, int R, EigScratch e, C* __restrict__ U,
+                                                               long ldu, long sU) {
   using Rt = decltype(C().x);
   extern __shared__ __align__(16) unsigned char bts[];
-  const int b = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r = blockIdx.x * BT_WARPS + warp;
-  if (r >= R) return;
-  C* u = (C*)bts + (long)warp * m;
-  const double* z = e.Z + ((long)b * R + r) * m;
-  const double2* dl = e.delta + (long)b * m;
-  const double2* Hv = e.Hv + (long)b * m * m;
-  const float2* Hf = (const float2*)e.Hv + (long)b * m * m;  // FP32 vectors of the double-float reduction
-  for (int i = lane; i < m; i += 32) u[i] = from_c64<C>(cscale(dl[i], z[i]));
-  __syncwarp();
-  for (int j = m - 2; j >= 0; --j) {
-    const int n = m - j - 1;
-    const double2* v = Hv + (long)j * m + j + 1;
-    const float2* vf = Hf + (long)j * m + j + 1;
-    C acc;
-    acc.x = Rt(0);
-    acc.y = Rt(0);
-    for (int i = lane; i < n; i += 32) {
-      const C vi = hv32 ? C{Rt(vf[i].x), Rt(vf[i].y)} : from_c64<C>(v[i]), ui = u[j + 1 + i];
-      acc.x = fma(vi.x, ui.x, acc.x);  // acc += conj(v_i) u_i
-      acc.x = fma(vi.y, ui.y, acc.x);
-      acc.y = fma(vi.x, ui.y, acc.y);
-      acc.y = fma(-vi.y, ui.x, acc.y);
-    }
-    acc.x = warp_sum(acc.x);
-    acc.y = warp_sum(acc.y);
-    const C s2 = cscale(acc, Rt(2));
-    for (int i = lane; i < n; i += 32) {
-      const C vi = hv32 ? C{Rt(vf[i].x), Rt(vf[i].y)} : from_c64<C>(v[i]);
-      u[j + 1 + i] = csub(u[j + 1 + i], cmul(vi, s2));
-    }
-    __syncwarp();
+  VT* vb = (VT*)bts;  // [3][m]
+  const int b = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r = blockIdx.x * BT_VPC + warp;
+  const bool active = r < R;
+  const VT* Hs = (const VT*)e.Hv + (long)b * m * m;  // reflector j at Hs + j m + j + 1
+  C u[NPL];
+#pragma unroll
+  for (int t = 0; t < NPL; ++t) {
+    const int i = lane + 32 * t;
+    u[t] = C{Rt(0), Rt(0)};
+    if (active && i < m) u[t] = from_c64<C>(cscale(e.delta[(long)b * m + i], e.Z[((long)b * R + r) * m + i]));
   }
+  auto stage = [&](int j) {
+    const VT* src = Hs + (long)j * m + j + 1;
+    VT* dst = vb + (j % 3) * m + j + 1;
+    for (int i = tid; i < m - j - 1; i += blockDim.x) bt_copy(dst + i, src + i);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  if (m >= 2) stage(m - 2);
+  for (int j = m - 2; j >= 0; --j) {
+    if (j > 0) {
+      stage(j - 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();  // reflector j visible; the buffer staged next was last read two reflectors ago
+    if (active) {
+      const VT* v = vb + (j % 3) * m;
+      Rt ax = Rt(0), ay = Rt(0);
+#pragma unroll
+      for (int t = 0; t < NPL; ++t) {
+        if (32 * t + 31 > j) {
+          const int i = lane + 32 * t;
+          if (i > j && i < m) {
+            const VT vv = v[i];
+            const Rt vx = (Rt)vv.x, vy = (Rt)vv.y;
+            ax = fma(vx, u[t].x, ax);  // conj(v_i) u_i
+            ax = fma(vy, u[t].y, ax);
+            ay = fma(vx, u[t].y, ay);
+            ay = fma(-vy, u[t].x, ay);
+          }
+        }
+      }
+      ax = Rt(2) * warp_sum(ax);
+      ay = Rt(2) * warp_sum(ay);
+#pragma unroll
+      for (int t = 0; t < NPL; ++t) {
+        if (32 * t + 31 > j) {
+          const int i = lane + 32 * t;
+          if (i > j && i < m) {
+            const VT vv = v[i];
+            const Rt vx = (Rt)vv.x, vy = (Rt)vv.y;
+            u[t].x -= vx * ax - vy * ay;
+            u[t].y -= vx * ay + vy * ax;
+          }
+        }
+      }
+    }
+  }
+  if (!active) return;
   C* Ub = U + (long)b * sU;
-  for (int i = lane; i < m; i += 32) Ub[(long)i * ldu + r] = u[i];
+#pragma unroll
+  for (int t = 0; t < NPL; ++t) {
+    const int i = lane + 32 * t;
+    if (i < m) Ub[(long)i * ldu + r] = u[t];
+  }
+}
+
+template <typename C, typename VT>
+static int launch_backtransform(int m, int R, int batch, const EigScratch& e, C* U, long ldu, long sU,
+                                cudaStream_t s) {
+  const size_t smem = 3 * (size_t)m * sizeof(VT);
+  const dim3 grid(cdiv(R, BT_VPC), batch);
+  auto go = [&](auto kern) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return TSVD_ERR_CUDA;
+    }
+    kern<<<grid, BT_VPC * 32, smem, s>>>(m, R, e, U, ldu, sU);
+    TSVD_LAUNCHED();
+    return TSVD_OK;
+  };
+  const int npl = cdiv(m, 32);
+  if (npl <= 4) return go(k_backtransform<C, VT, 4>);
+  if (npl <= 8) return go(k_backtransform<C, VT, 8>);
+  if (npl <= 12) return go(k_backtransform<C, VT, 12>);
+  if (npl <= 16) return go(k_backtransform<C, VT, 16>);
+  if (npl <= 24) return go(k_backtransform<C, VT, 24>);
+  return TSVD_ERR_UNSUPPORTED;
 }
 
 static int device_attr(cudaDeviceAttr a, int fallback) {
@@ -1720,7 +1838,7 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
   } else {
     TSVD_STAGE("eig_hetrd", s);
     const size_t smem = (2 + 16) * (size_t)m * sizeof(double2);  // v, p and 16 warps' partials
-    if (smem > 48 * 1024) {
+    if (smem > 40 * 1024) {  // with the static reduction arrays
       cudaFuncSetAttribute(k_hetrd<HETRD_CLUSTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
     cudaLaunchConfig_t cfg = {};
@@ -1772,12 +1890,13 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
     size_t smem_co = (size_t)R * m * (kDoubleFloat ? sizeof(float) : sizeof(double));
     using CoKernel = void (*)(int, int, EigScratch, const double*);
     CoKernel co = kDoubleFloat ? (CoKernel)k_cluster_orth<float, true> : (CoKernel)k_cluster_orth<double, true>;
-    if (smem_co > 200 * 1024) {  // vectors stay in global memory
+    if (smem_co > 180 * 1024) {  // vectors stay in global memory
       co = k_cluster_orth<double, false>;
       smem_co = 0;
     }
-    if (smem_co > 48 * 1024 && cudaFuncSetAttribute(co, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_co) !=
-                                   cudaSuccess) {
+    // the kernel's static shared memory (the cluster Gram, 16 KB) counts against the same 48 KB default
+    if (smem_co > 0 && cudaFuncSetAttribute(co, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_co) !=
+                           cudaSuccess) {
       cudaGetLastError();
       return TSVD_ERR_CUDA;
     }
@@ -1785,12 +1904,10 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
     TSVD_LAUNCHED();
   }
   TSVD_STAGE("eig_backtransform", s);
-  const size_t smem_bt = (size_t)BT_WARPS * m * sizeof(C);
-  if (smem_bt > 48 * 1024)
-    cudaFuncSetAttribute(k_backtransform<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bt);
-  k_backtransform<C><<<dim3(cdiv(R, BT_WARPS), batch), BT_WARPS * 32, smem_bt, s>>>(m, R, e, U, ldu, sU, hv32);
-  TSVD_LAUNCHED();
-  return TSVD_OK;
+  if constexpr (kDoubleFloat) {
+    if (hv32) return launch_backtransform<C, float2>(m, R, batch, e, U, ldu, sU, s);
+  }
+  return launch_backtransform<C, double2>(m, R, batch, e, U, ldu, sU, s);
 }
 template int herm_eig_topR<double2>(double2*, long, long, int, int, int, double*, double2*, long, long, void*, int*,
                                     cudaStream_t);
