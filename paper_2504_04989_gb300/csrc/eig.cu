@@ -1370,16 +1370,35 @@ __device__ __forceinline__ dfl df_rcp(dfl b) {
 // operations rather than FP64 ones at 1/64 of the rate.  Pivots below 2^-47
 // ||T|| are raised to that size.  Factors per step (coalesced over r):
 // multiplier, reciprocal pivot and the two U super-diagonals as (hi, lo)
-// pairs, the row swaps as bits of one word per 32 steps.  The solves fetch
-// the factors TP_CHUNK steps at a time, ahead of the dependent chain.
+// pairs, the row swaps as bits of one word per 32 steps.  NTH pairs per CTA;
+// SMF: the factors of all NTH pairs stay in shared memory (16 pairs at
+// m = 300: 197 KB), so the solves never wait on L2; otherwise they live in
+// global memory and the solves fetch them TP_CHUNK steps at a time, ahead of
+// the dependent chain.
 constexpr int TP_CHUNK = 8;
-__global__ void __launch_bounds__(TP_THREADS) k_tridiag_pairs_df(int m, int R, EigScratch e,
-                                                                 const double* __restrict__ lam_out, int iters) {
+template <bool SMF>
+__device__ __forceinline__ float2 tp_ld(const float2* p) {
+  if constexpr (SMF) return *p;
+  else return __ldcg(p);
+}
+template <bool SMF>
+__device__ __forceinline__ unsigned tp_ld(const unsigned* p) {
+  if constexpr (SMF) return *p;
+  else return __ldcg(p);
+}
+static size_t tp_df_smem(int m, int nth, bool smf) {
+  size_t bytes = (size_t)m * (sizeof(float4) + nth * sizeof(float2));
+  if (smf) bytes += (size_t)m * nth * 4 * sizeof(float2) + (size_t)cdiv(m, 32) * nth * sizeof(unsigned);
+  return bytes;
+}
+template <int NTH, bool SMF>
+__global__ void __launch_bounds__(NTH) k_tridiag_pairs_df(int m, int R, EigScratch e,
+                                                          const double* __restrict__ lam_out, int iters) {
   extern __shared__ __align__(16) double tsm[];
   float4* T4 = (float4*)tsm;         // [m] (d_i hi, lo, f_i hi, lo), f_{m-1} = 0
-  float2* xs = (float2*)(T4 + m);    // [m][TP_THREADS] iterates
+  float2* xs = (float2*)(T4 + m);    // [m][NTH] iterates
   __shared__ double s_scale;
-  const int b = blockIdx.y, t = threadIdx.x, r = blockIdx.x * TP_THREADS + t;
+  const int b = blockIdx.y, t = threadIdx.x, r = blockIdx.x * NTH + t;
   if (t == 0) {
     const double tn = e.tnorm[b];
     s_scale = (tn > 0.0 && isfinite(tn)) ? 1.0 / tn : 1.0;
@@ -1399,14 +1418,21 @@ __global__ void __launch_bounds__(TP_THREADS) k_tridiag_pairs_df(int m, int R, E
     return;
   }
   const dfl nlam = df_neg(df_from(lam_out[(long)b * R + r] * sc));
-  // factor arrays of this slice, element i of thread r at [i * R + r]
-  float2* L0 = (float2*)(e.lu + (long)b * 5 * m * R);  // multiplier
-  float2* L1 = L0 + (long)m * R;                       // reciprocal pivot
-  float2* L2 = L1 + (long)m * R;                       // U first super-diagonal
-  float2* L3 = L2 + (long)m * R;                       // U second super-diagonal
-  unsigned* FL = (unsigned*)(L3 + (long)m * R);        // row swaps, [cdiv(m, 32)][R]
+  // factor arrays, element i of this pair at [i * ls + lo]: shared memory [m][NTH] (SMF), else
+  // this slice's part of e.lu, [m][R]
+  const long ls = SMF ? NTH : R;
+  float2* L0 = SMF ? (float2*)(xs + (long)m * NTH) : (float2*)(e.lu + (long)b * 5 * m * R);  // multiplier
+  float2* L1 = L0 + (long)m * ls;                      // reciprocal pivot
+  float2* L2 = L1 + (long)m * ls;                      // U first super-diagonal
+  float2* L3 = L2 + (long)m * ls;                      // U second super-diagonal
+  unsigned* FL = (unsigned*)(L3 + (long)m * ls);       // row swaps, [cdiv(m, 32)][ls]
+  L0 += SMF ? t : r;
+  L1 += SMF ? t : r;
+  L2 += SMF ? t : r;
+  L3 += SMF ? t : r;
+  FL += SMF ? t : r;
   float2* x = xs + t;
-#define X(i) x[(long)(i) * TP_THREADS]
+#define X(i) x[(long)(i) * NTH]
   const float tiny = 0x1p-47f;
   dfl dcur = df_add(dfl{T4[0].x, T4[0].y}, nlam), ucur = dfl{T4[0].z, T4[0].w};
   unsigned flags = 0;
@@ -1435,19 +1461,19 @@ __global__ void __launch_bounds__(TP_THREADS) k_tridiag_pairs_df(int m, int R, E
       dcur = nd;
       flags |= 1u << (i & 31);
     }
-    const long o = (long)i * R + r;
+    const long o = (long)i * ls;
     L0[o] = make_float2(l.hi, l.lo);
     L1[o] = make_float2(rp.hi, rp.lo);
     L2[o] = make_float2(u1.hi, u1.lo);
     L3[o] = make_float2(u2.hi, u2.lo);
     if ((i & 31) == 31 || i == m - 2) {
-      FL[(long)(i >> 5) * R + r] = flags;
+      FL[(long)(i >> 5) * ls] = flags;
       flags = 0;
     }
   }
   {
     const dfl rp = df_rcp((fabsf(dcur.hi) < tiny) ? dfl{copysignf(tiny, dcur.hi), 0.0f} : dcur);
-    const long o = (long)(m - 1) * R + r;
+    const long o = (long)(m - 1) * ls;
     L1[o] = make_float2(rp.hi, rp.lo);
     L2[o] = make_float2(0.0f, 0.0f);
     L3[o] = make_float2(0.0f, 0.0f);
@@ -1465,8 +1491,8 @@ __global__ void __launch_bounds__(TP_THREADS) k_tridiag_pairs_df(int m, int R, E
       float2 lc[TP_CHUNK];
 #pragma unroll
       for (int k = 0; k < TP_CHUNK; ++k)
-        lc[k] = (i0 + k < m - 1) ? __ldcg(L0 + (long)(i0 + k) * R + r) : make_float2(0.0f, 0.0f);
-      if ((i0 & 31) == 0) fw = __ldcg(FL + (long)(i0 >> 5) * R + r);
+        lc[k] = (i0 + k < m - 1) ? tp_ld<SMF>(L0 + (long)(i0 + k) * ls) : make_float2(0.0f, 0.0f);
+      if ((i0 & 31) == 0) fw = tp_ld<SMF>(FL + (long)(i0 >> 5) * ls);
 #pragma unroll
       for (int k = 0; k < TP_CHUNK; ++k) {
         const int i = i0 + k;
@@ -1493,10 +1519,10 @@ __global__ void __launch_bounds__(TP_THREADS) k_tridiag_pairs_df(int m, int R, E
       for (int k = 0; k < TP_CHUNK; ++k) {
         const int i = i0 - k;
         const bool ok = i >= 0;
-        const long o = (long)(ok ? i : 0) * R + r;
-        pc[k] = ok ? __ldcg(L1 + o) : make_float2(0.0f, 0.0f);
-        ac[k] = ok ? __ldcg(L2 + o) : make_float2(0.0f, 0.0f);
-        bc[k] = ok ? __ldcg(L3 + o) : make_float2(0.0f, 0.0f);
+        const long o = (long)(ok ? i : 0) * ls;
+        pc[k] = ok ? tp_ld<SMF>(L1 + o) : make_float2(0.0f, 0.0f);
+        ac[k] = ok ? tp_ld<SMF>(L2 + o) : make_float2(0.0f, 0.0f);
+        bc[k] = ok ? tp_ld<SMF>(L3 + o) : make_float2(0.0f, 0.0f);
       }
 #pragma unroll
       for (int k = 0; k < TP_CHUNK; ++k) {
@@ -1876,10 +1902,18 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
     // solves: 3 (FP64 path), 2 on the FP32 path (eigenvalues to 3e-13 ||T|| already make one solve
     // amplify the wanted direction by gap / 3e-13; the vectors end in FP32)
     if (kDoubleFloat) {
-      const size_t smem_df = (size_t)m * (sizeof(float4) + TP_THREADS * sizeof(float2));
-      if (smem_df > 48 * 1024)
-        cudaFuncSetAttribute(k_tridiag_pairs_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df);
-      k_tridiag_pairs_df<<<dim3(cdiv(R, TP_THREADS), batch), TP_THREADS, smem_df, s>>>(m, R, e, lam, 2);
+      auto go = [&](auto kern, int nth, bool smf) {
+        const size_t smem_df = tp_df_smem(m, nth, smf);
+        if (smem_df > 40 * 1024 &&
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df) != cudaSuccess) {
+          cudaGetLastError();
+          return TSVD_ERR_CUDA;
+        }
+        kern<<<dim3(cdiv(R, nth), batch), nth, smem_df, s>>>(m, R, e, lam, 2);
+        return TSVD_OK;
+      };
+      if (tp_df_smem(m, 16, true) <= 200 * 1024) TSVD_TRY(go(k_tridiag_pairs_df<16, true>, 16, true));
+      else TSVD_TRY(go(k_tridiag_pairs_df<TP_THREADS, false>, TP_THREADS, false));
     } else {
       k_tridiag_pairs<<<dim3(cdiv(R, TP_THREADS), batch), TP_THREADS, smem_tp, s>>>(m, R, e, lam, 3);
     }

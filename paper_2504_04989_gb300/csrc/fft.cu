@@ -501,17 +501,32 @@ __global__ void k_gaussian(uint64_t seed, uint32_t stream_id, uint32_t tensor_id
   if (4 * call >= n) return;
   const uint4 x = philox10(make_uint4((uint32_t)call, (uint32_t)((unsigned long long)call >> 32), stream_id, tensor_id),
                            (uint32_t)seed, (uint32_t)(seed >> 32));
-  const double inv32 = 1.0 / 4294967296.0;
   const uint32_t w[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
   for (int pair = 0; pair < 2; ++pair) {
-    const double u1 = ((double)w[2 * pair] + 1.0) * inv32;
-    const double u2 = ((double)w[2 * pair + 1] + 1.0) * inv32;
-    const double r = sqrt(-2.0 * log(u1));
-    const double th = 2.0 * 3.141592653589793 * u2;
     const long e = 4 * call + 2 * pair;
-    if (e < n) out[e] = (T)(r * cos(th));
-    if (e + 1 < n) out[e + 1] = (T)(r * sin(th));
+    T g0, g1;
+    if constexpr (sizeof(T) == sizeof(float)) {
+      // FP32 stream: the same definition evaluated in FP32 (its values are FP32 anyway; FP64
+      // transcendentals run at 1/64 of the FP32 rate here)
+      const float u1 = fmaf((float)w[2 * pair], 0x1p-32f, 0x1p-32f);
+      const float u2 = fmaf((float)w[2 * pair + 1], 0x1p-32f, 0x1p-32f);
+      const float r = sqrtf(-2.0f * logf(u1));
+      float sn, cs;
+      sincospif(2.0f * u2, &sn, &cs);
+      g0 = r * cs;
+      g1 = r * sn;
+    } else {
+      const double inv32 = 1.0 / 4294967296.0;
+      const double u1 = ((double)w[2 * pair] + 1.0) * inv32;
+      const double u2 = ((double)w[2 * pair + 1] + 1.0) * inv32;
+      const double r = sqrt(-2.0 * log(u1));
+      const double th = 2.0 * 3.141592653589793 * u2;
+      g0 = (T)(r * cos(th));
+      g1 = (T)(r * sin(th));
+    }
+    if (e < n) out[e] = g0;
+    if (e + 1 < n) out[e + 1] = g1;
   }
 }
 

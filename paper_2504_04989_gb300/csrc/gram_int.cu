@@ -24,24 +24,34 @@ static int gram_bits(int n2) {
   return std::min(23, (61 - lg) / 2);
 }
 
-// one thread per column of one slice: exponent of the largest |component|,
-// then the scaled integers (round to nearest even)
-__global__ void k_gram_quantize(const float2* __restrict__ CH, long ldc, long sC, int n2, int m, int B,
-                                int2* __restrict__ Q, int* __restrict__ colexp) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// columns of one slice in tiles of 32, 8 row groups per column: exponent of the
+// column's largest |component| (max over the groups in shared memory), then
+// the scaled integers (round to nearest even)
+__global__ void __launch_bounds__(256) k_gram_quantize(const float2* __restrict__ CH, long ldc, long sC, int n2,
+                                                       int m, int B, int2* __restrict__ Q, int* __restrict__ colexp) {
+  __shared__ float smx[8][32];
+  const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + cx;
   const int k = blockIdx.y;
-  if (i >= m) return;
+  const bool ok = i < m;
   const float2* src = CH + (long)k * sC + i;
   float mx = 0.0f;
-  for (int l = 0; l < n2; ++l) {
-    const float2 x = src[(long)l * ldc];
-    mx = fmaxf(mx, fmaxf(fabsf(x.x), fabsf(x.y)));
-  }
+  if (ok)
+    for (int l = ry; l < n2; l += 8) {
+      const float2 x = src[(long)l * ldc];
+      mx = fmaxf(mx, fmaxf(fabsf(x.x), fabsf(x.y)));
+    }
+  smx[ry][cx] = mx;
+  __syncthreads();
+  float cm = 0.0f;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) cm = fmaxf(cm, smx[r][cx]);
+  if (!ok) return;
   int e = 0;
-  if (mx > 0.0f) frexpf(mx, &e);  // mx < 2^e
-  colexp[(long)k * m + i] = e;
+  if (cm > 0.0f) frexpf(cm, &e);  // cm < 2^e
+  if (ry == 0) colexp[(long)k * m + i] = e;
   int2* dst = Q + (long)k * n2 * m + i;
-  for (int l = 0; l < n2; ++l) {
+  for (int l = ry; l < n2; l += 8) {
     const float2 x = src[(long)l * ldc];
     dst[(long)l * m] = make_int2((int)rintf(ldexpf(x.x, B - e)), (int)rintf(ldexpf(x.y, B - e)));
   }
@@ -125,7 +135,7 @@ int gram_int_fp32(const float2* CH, long ldc, long sC, int n2, int m, int batch,
   if (n2 <= 0 || m <= 0 || batch <= 0) return TSVD_OK;
   if (batch > 65535) return TSVD_ERR_UNSUPPORTED;
   const int B = gram_bits(n2);
-  k_gram_quantize<<<dim3(cdiv(m, 128), batch), 128, 0, s>>>(CH, ldc, sC, n2, m, B, Q, colexp);
+  k_gram_quantize<<<dim3(cdiv(m, 32), batch), 256, 0, s>>>(CH, ldc, sC, n2, m, B, Q, colexp);
   TSVD_LAUNCHED();
   const int nt = cdiv(m, GI_TILE);
   k_gram_int<<<dim3(nt * (nt + 1) / 2, batch), 256, 0, s>>>(Q, colexp, n2, m, B, G, ldg, sG);
