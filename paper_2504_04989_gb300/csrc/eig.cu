@@ -612,6 +612,25 @@ __device__ __forceinline__ dfl df_div(dfl a, dfl b) {
   const float r = (((a.hi - p) - pe) + a.lo) - q * b.lo;
   return df_fast_two_sum(q, r / b.hi);
 }
+// Reciprocal square root and square root without a division: the correctly
+// rounded FP32 reciprocal square root y, then one Newton correction with the
+// residual formed in double-float (y (1 + e/2), e = 1 - a y^2; for the root,
+// x = a_hi y and x + y (a - x^2) / 2 with a - x^2 exact by FMA).  About 46
+// correct bits from a 24-bit start.  a > 0.
+__device__ __forceinline__ dfl df_rsqrt(dfl a) {
+  const float y = __frsqrt_rn(a.hi);
+  const float p = y * y, pe = fmaf(y, y, -p);  // y^2 = p + pe exactly
+  const dfl ay2 = df_mul(a, dfl{p, pe});
+  const float e = (1.0f - ay2.hi) - ay2.lo;    // 1 - a y^2 (1 - ay2.hi exact: ay2.hi is within 2^-22 of 1)
+  return df_fast_two_sum(y, 0.5f * y * e);
+}
+__device__ __forceinline__ dfl df_sqrt_nodiv(dfl a) {
+  if (!(a.hi > 0.f)) return dfl{0.f, 0.f};
+  const float y = __frsqrt_rn(a.hi);
+  const float x = a.hi * y;
+  const float r = (fmaf(-x, x, a.hi)) + a.lo;  // a - x^2 (the high part exact by FMA)
+  return df_fast_two_sum(x, 0.5f * y * r);
+}
 __device__ __forceinline__ dfl df_from(double x) {
   const float h = (float)x;
   return dfl{h, (float)(x - (double)h)};
@@ -671,6 +690,10 @@ __device__ __forceinline__ cdf cdf_scale(cdf x, dfl s) {
 __device__ __forceinline__ dfl df_shfl_xor(dfl a, int o) {
   return dfl{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
+__device__ __forceinline__ cdf cdf_shfl_xor(cdf a, int o) {
+  return cdf{__shfl_xor_sync(0xffffffffu, a.rh, o), __shfl_xor_sync(0xffffffffu, a.rl, o),
+             __shfl_xor_sync(0xffffffffu, a.ih, o), __shfl_xor_sync(0xffffffffu, a.il, o)};
+}
 // block-wide sum in a fixed order, result on every thread (two barriers)
 __device__ __forceinline__ dfl df_block_sum(dfl v, dfl* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -697,6 +720,8 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df(const double2* __restrict__ 
   int* CP = (int*)(vown + (m + CL - 1) / CL);
   __shared__ dfl red[NT / 32];
   __shared__ int s_exp;
+  __shared__ cdf s_am;   // -alpha of the current reflector
+  __shared__ dfl s_vinv; // its normalisation
   cg::cluster_group cluster = cg::this_cluster();
   const int c = (CL > 1) ? (int)cluster.block_rank() : 0;
   const int b = blockIdx.x / CL;
@@ -778,35 +803,54 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df(const double2* __restrict__ 
     else __syncthreads();
     const int n = m - j - 1;
     {
-      dfl part{0.f, 0.f};
-      for (int i = tid; i < n; i += NT) {
-        const cdf x = v[j + 1 + i];
-        part = df_fma(part, cre(x), cre(x));
-        part = df_fma(part, cim(x), cim(x));
-      }
+      // |x|^2 and the reflector scalars by warp 0 alone (the other warps clear the partial
+      // products meanwhile), handed over through shared memory: lanes take entries
+      // lane + 32 u + 128 k in four independent chains, then a butterfly of double-float sums;
+      // -alpha = e^{i arg x0} |x|, v = (x - alpha e1) / sqrt(2 |x| (|x| + |x0|))
       for (int i = tid; i < n; i += NT) pv[j + 1 + i] = cdf_zero();
-      const dfl nrm2d = df_block_sum(part, red);
-      // reflector scalars in double-float on every thread (identical values, no serial section)
-      cdf am = cdf_zero();  // -alpha
-      dfl vinv{0.f, 0.f};
-      if (nrm2d.hi > 0.f) {
-        const cdf x0 = v[j + 1];
-        const dfl nrm = df_sqrt(nrm2d);
-        const dfl ax2 = df_fma(df_fma(dfl{0.f, 0.f}, cre(x0), cre(x0)), cim(x0), cim(x0));
-        const dfl ax0 = df_sqrt(ax2);
-        dfl phr{1.f, 0.f}, phi{0.f, 0.f};
-        if (ax0.hi > 0.f) {
-          phr = df_div(cre(x0), ax0);
-          phi = df_div(cim(x0), ax0);
+      if (warp == 0) {
+        dfl pa[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        for (int i0 = 0; i0 < n; i0 += 128) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = i0 + 32 * u + lane;
+            if (i < n) {
+              const cdf x = v[j + 1 + i];
+              pa[u] = df_fma(pa[u], cre(x), cre(x));
+              pa[u] = df_fma(pa[u], cim(x), cim(x));
+            }
+          }
         }
-        am = cdf_make(df_mul(phr, nrm), df_mul(phi, nrm));
-        const dfl t = df_mul(df_add(nrm, nrm), df_add(nrm, ax0));
-        vinv = df_div(dfl{1.f, 0.f}, df_sqrt(t));
+        dfl nrm2d = df_add(df_add(pa[0], pa[1]), df_add(pa[2], pa[3]));
+        for (int o = 16; o > 0; o >>= 1) nrm2d = df_add(nrm2d, df_shfl_xor(nrm2d, o));
+        cdf am = cdf_zero();  // -alpha
+        dfl vinv{0.f, 0.f};
+        if (nrm2d.hi > 0.f) {
+          const cdf x0 = v[j + 1];
+          const dfl nrm = df_sqrt_nodiv(nrm2d);
+          const dfl ax2 = df_fma(df_fma(dfl{0.f, 0.f}, cre(x0), cre(x0)), cim(x0), cim(x0));
+          dfl phr{1.f, 0.f}, phi{0.f, 0.f}, ax0{0.f, 0.f};
+          if (ax2.hi > 0.f) {
+            const dfl iax = df_rsqrt(ax2);  // 1 / |x0|
+            ax0 = df_mul(ax2, iax);
+            phr = df_mul(cre(x0), iax);
+            phi = df_mul(cim(x0), iax);
+          }
+          am = cdf_make(df_mul(phr, nrm), df_mul(phi, nrm));
+          vinv = df_rsqrt(df_mul(df_add(nrm, nrm), df_add(nrm, ax0)));
+        }
+        if (lane == 0) {
+          s_am = am;
+          s_vinv = vinv;
+          if (c == 0) {
+            const double2 al = cdf_to(am);
+            e.alpha[(long)b * m + j] = make_double2(-ldexp(al.x, ex), -ldexp(al.y, ex));
+          }
+        }
       }
-      if (c == 0 && tid == 0) {
-        const double2 al = cdf_to(am);
-        e.alpha[(long)b * m + j] = make_double2(-ldexp(al.x, ex), -ldexp(al.y, ex));
-      }
+      __syncthreads();
+      const cdf am = s_am;
+      const dfl vinv = s_vinv;
       for (int i = tid; i < n; i += NT) {
         cdf vi = v[j + 1 + i];
         if (i == 0) vi = cdf_add(vi, am);
@@ -873,15 +917,24 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df(const double2* __restrict__ 
         }
       }
       __syncthreads();
-      for (int i = tid; i < nr; i += NT) {
-        const int Pi = i * (g0 - j) + CL * i * (i - 1) / 2;
-        const int len = g0 + CL * i - j;
-        const int ta = hs_owner(Pi, L1), tb = hs_owner(Pi + len - 1, L1);
-        if (ta == tb) continue;
-        cdf sacc = (hs_seg(ta, E1, L1) == Pi) ? slotF[ta] : slotL[ta];
-        for (int t = ta + 1; t <= tb; ++t)
-          if (hs_seg(t, E1, L1) < hs_seg(t + 1, E1, L1)) sacc = cdf_add(sacc, slotF[t]);
-        pv[g0 + CL * i] = sacc;
+      // rows split between threads: 8 lanes per row sum every 8th slot, then a 3-level butterfly
+      for (int base = 0; base < nr; base += NT / 8) {
+        const int i = base + (tid >> 3), q = tid & 7;
+        cdf sacc = cdf_zero();
+        bool split = false;
+        if (i < nr) {
+          const int Pi = i * (g0 - j) + CL * i * (i - 1) / 2;
+          const int len = g0 + CL * i - j;
+          const int ta = hs_owner(Pi, L1), tb = hs_owner(Pi + len - 1, L1);
+          split = ta != tb;
+          if (split) {
+            if (q == 0) sacc = (hs_seg(ta, E1, L1) == Pi) ? slotF[ta] : slotL[ta];
+            for (int t = ta + 1 + q; t <= tb; t += 8)
+              if (hs_seg(t, E1, L1) < hs_seg(t + 1, E1, L1)) sacc = cdf_add(sacc, slotF[t]);
+          }
+        }
+        for (int o = 1; o < 8; o <<= 1) sacc = cdf_add(sacc, cdf_shfl_xor(sacc, o));
+        if (split && q == 0) pv[g0 + CL * i] = sacc;
       }
     }
     __syncthreads();
