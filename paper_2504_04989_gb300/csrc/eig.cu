@@ -808,6 +808,51 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df(const double2* __restrict__ 
       // lane + 32 u + 128 k in four independent chains, then a butterfly of double-float sums;
       // -alpha = e^{i arg x0} |x|, v = (x - alpha e1) / sqrt(2 |x| (|x| + |x0|))
       for (int i = tid; i < n; i += NT) pv[j + 1 + i] = cdf_zero();
+      if (warp > 0 && lag) {
+        // meanwhile the other warps apply the pending rank-2 update of step j-1 to the own rows'
+        // entries k in [j+1, g] (contiguous segments over NT - 32 threads), so that the
+        // matrix-vector passes below read updated values and need only v_j
+        const int q0 = hs_qfirst(j, c, CL);
+        const int nr = max(0, nq - q0);
+        const int g0 = c + CL * q0;
+        const int E1 = nr * (g0 - j) + CL * nr * (nr - 1) / 2;
+        if (E1 > 0) {
+          const int lt = tid - 32;
+          const int L = hs_seglen<NT - 32>(E1);
+          const int e0 = hs_seg(lt, E1, L), e1 = hs_seg(lt + 1, E1, L);
+          if (e0 < e1) {
+            int lo = 0, hi = nr - 1;
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if (mid * (g0 - j) + CL * mid * (mid - 1) / 2 <= e0) lo = mid;
+              else hi = mid - 1;
+            }
+            const int i = lo;
+            const int Pi = i * (g0 - j) + CL * i * (i - 1) / 2;
+            int g = g0 + CL * i;
+            int k = j + 1 + (e0 - Pi);
+            cdf* row = S + hs_rowbase(q0 + i, c, CL);
+            cdf vg = vp[g], wg = wp[g];
+            for (int el = e0; el < e1; ++el) {
+              cdf a = cdf_lag(row[k], vg, wg, vp[k], wp[k]);
+              if (k == g) {
+                a.ih = 0.f;
+                a.il = 0.f;
+              }
+              row[k] = a;
+              if (++k > g) {
+                row += g + 1;
+                g += CL;
+                k = j + 1;
+                if (el + 1 < e1) {
+                  vg = vp[g];
+                  wg = wp[g];
+                }
+              }
+            }
+          }
+        }
+      }
       if (warp == 0) {
         dfl pa[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         for (int i0 = 0; i0 < n; i0 += 128) {
@@ -861,7 +906,7 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df(const double2* __restrict__ 
     }
     __syncthreads();
 
-    // row pass (as in k_hetrd_smem)
+    // row pass (as in k_hetrd_smem, the pending update already applied)
     const int q0 = hs_qfirst(j, c, CL);
     for (int q = q0 + tid; q < nq; q += NT) vown[q] = v[c + CL * q];
     const int nr = max(0, nq - q0);
@@ -881,21 +926,11 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df(const double2* __restrict__ 
         const int Pi = i * (g0 - j) + CL * i * (i - 1) / 2;
         int g = g0 + CL * i;
         int k = j + 1 + (e0 - Pi);
-        cdf* row = S + hs_rowbase(q0 + i, c, CL);
+        const cdf* row = S + hs_rowbase(q0 + i, c, CL);
         bool whole = (e0 == Pi), first = true;
-        cdf vg = vp[g], wg = wp[g];
         cdf acc = cdf_zero();
         for (int el = e0; el < e1; ++el) {
-          cdf a = row[k];
-          if (lag) {
-            a = cdf_lag(a, vg, wg, vp[k], wp[k]);
-            if (k == g) {
-              a.ih = 0.f;
-              a.il = 0.f;
-            }
-            row[k] = a;
-          }
-          cdf_fma(acc, a, v[k]);
+          cdf_fma(acc, row[k], v[k]);
           if (++k > g) {
             if (whole) pv[g] = acc;
             else slotF[tid] = acc;
@@ -905,10 +940,6 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df(const double2* __restrict__ 
             row += g + 1;
             g += CL;
             k = j + 1;
-            if (el + 1 < e1) {
-              vg = vp[g];
-              wg = wp[g];
-            }
           }
         }
         if (k != j + 1) {
