@@ -37,9 +37,8 @@ namespace tsvd {
 //   i < l <= k, where X(l,k) = B(l,k) / R_ll, final after step l+1, is
 //   published in a double-buffered row.
 // ---------------------------------------------------------------------------
-constexpr int CI_THREADS = 512;
-template <typename GC, int EPT>  // EPT >= nb (nb+1) / 2 / CI_THREADS entries per thread
-__global__ void __launch_bounds__(CI_THREADS) k_chol_inv(const GC* __restrict__ G, long ldg, long sG,
+template <typename GC, int EPT, int NTHR>  // NTHR threads, EPT >= nb (nb+1) / 2 / NTHR entries per thread
+__global__ void __launch_bounds__(NTHR) k_chol_inv(const GC* __restrict__ G, long ldg, long sG,
                                                        GC* __restrict__ Mo, long ldm, long sM, int nb,
                                                        double shift_rel, double dead_rel,
                                                        uint32_t* __restrict__ dead_out) {
@@ -51,7 +50,7 @@ __global__ void __launch_bounds__(CI_THREADS) k_chol_inv(const GC* __restrict__ 
   __shared__ Rt dj[128];           // pivots d_j (0 for a dead column)
   __shared__ Rt pinv[128];         // 1 / d_j (0 for a dead column)
   __shared__ Rt ri[128];           // 1 / R-tilde_jj
-  __shared__ double red[CI_THREADS / 32];
+  __shared__ double red[NTHR / 32];
   const int b = blockIdx.x, tid = threadIdx.x;
   const int np = nb * (nb + 1) / 2;
   auto rb = [nb](int i) { return i * nb - (i * (i + 1)) / 2; };  // packed offset of row i, minus i
@@ -187,7 +186,7 @@ __global__ void __launch_bounds__(CI_THREADS) k_chol_inv(const GC* __restrict__ 
     }
     Mo[(long)i * ldm + k] = mv;
   }
-  for (int e = tid; e < nb * nb; e += CI_THREADS) {
+  for (int e = tid; e < nb * nb; e += NTHR) {
     const int i = e / nb, k = e - i * nb;
     if (k < i) Mo[(long)i * ldm + k] = GC{Rt(0), Rt(0)};
   }
@@ -208,21 +207,23 @@ int chol_inv(const GC* G, long ldg, long sG, GC* M, long ldm, long sM, int nb, i
   if (nb > 128) return TSVD_ERR_UNSUPPORTED;
   const int np = nb * (nb + 1) / 2;
   const size_t smem = ((size_t)np + 2 * (size_t)nb) * sizeof(GC);  // published rows + X rows
-  auto go = [&](auto kern) {
+  auto go = [&](auto kern, int nthr) {
     // with the kernel's static arrays (about 4 KB) the total passes the 48 KB default earlier
     if (smem > 40 * 1024 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
       cudaGetLastError();
       return TSVD_ERR_CUDA;
     }
-    kern<<<batch, CI_THREADS, smem, s>>>(G, ldg, sG, M, ldm, sM, nb, shift_rel, dead_rel, dead);
+    kern<<<batch, nthr, smem, s>>>(G, ldg, sG, M, ldm, sM, nb, shift_rel, dead_rel, dead);
     TSVD_LAUNCHED();
     return TSVD_OK;
   };
-  if (np <= 2 * CI_THREADS) return go(k_chol_inv<GC, 2>);
-  if (np <= 4 * CI_THREADS) return go(k_chol_inv<GC, 4>);
-  if (np <= 8 * CI_THREADS) return go(k_chol_inv<GC, 8>);
-  return go(k_chol_inv<GC, 17>);
+  // 512 threads (16 warps: a step's latency is hidden across warps; 128 threads with 16 entries
+  // each measured twice as slow at nb = 60)
+  if (np <= 2 * 512) return go(k_chol_inv<GC, 2, 512>, 512);
+  if (np <= 4 * 512) return go(k_chol_inv<GC, 4, 512>, 512);
+  if (np <= 8 * 512) return go(k_chol_inv<GC, 8, 512>, 512);
+  return go(k_chol_inv<GC, 17, 512>, 512);
 }
 template int chol_inv<double2>(const double2*, long, long, double2*, long, long, int, int, double, double, uint32_t*,
                                cudaStream_t);

@@ -1882,7 +1882,8 @@ static int device_attr(cudaDeviceAttr a, int fallback) {
 static int hetrd_smem_cluster(int m, int batch, int nt) {
   if (m < 2) return 0;
   const int sms = device_attr(cudaDevAttrMultiProcessorCount, 148);
-  const size_t smax = (size_t)device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin, 232448) - 256;
+  // the kernels' static arrays (up to about 1.3 KB) share the per-block limit with the dynamic part
+  const size_t smax = (size_t)device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin, 232448) - 2048;
   for (int CL = 8; CL >= 1; CL >>= 1) {
     if (CL > 1 && ((long)batch * CL > sms || m / CL < 48)) continue;
     if (hetrd_smem_bytes(m, CL, nt) <= smax) return CL;
