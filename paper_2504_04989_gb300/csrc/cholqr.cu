@@ -240,7 +240,7 @@ __device__ __forceinline__ void cp_async_elem(C* dst, const C* src) {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
-// W <- W M in place for the n1 x nb block of every slice (M nb x nb, upper
+// O <- W M for the n1 x nb block of every slice (M nb x nb, upper
 // triangular, dense): a CTA stages TM_ROWS full rows of W and, kchunk rows at
 // a time, M in shared memory (all of M at once when it fits); thread
 // (ty, tx) accumulates rows ty + 16a (a < 4) and columns tx + 16u in
@@ -248,8 +248,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // ---------------------------------------------------------------------------
 constexpr int TM_ROWS = 64;
 template <typename C, int NU>  // NU = ceil(nb / 16) column groups per thread
-__global__ void __launch_bounds__(256) k_rmul_block(C* __restrict__ W, long ldw, long sW, const C* __restrict__ M,
-                                                  long ldm, long sM, int n1, int nb, int kchunk) {
+__global__ void __launch_bounds__(256) k_rmul_block(const C* W, long ldw, long sW, const C* __restrict__ M,
+                                                  long ldm, long sM, int n1, int nb, int kchunk, C* O, long ldo,
+                                                  long sO) {
   using R = decltype(C().x);
   extern __shared__ __align__(16) unsigned char rmsm[];
   constexpr int MC = 16 * NU;
@@ -260,6 +261,7 @@ __global__ void __launch_bounds__(256) k_rmul_block(C* __restrict__ W, long ldw,
   const int r0 = blockIdx.x * TM_ROWS;
   W += (long)b * sW;
   M += (long)b * sM;
+  O += (long)b * sO;
   // asynchronous copies: every element of the rows and of the chunk of M is in flight at once
   for (int r = tid >> 5; r < TM_ROWS; r += 8)
     for (int k = tid & 31; k < nb; k += 32) {
@@ -310,14 +312,15 @@ __global__ void __launch_bounds__(256) k_rmul_block(C* __restrict__ W, long ldw,
 #pragma unroll
       for (int u = 0; u < NU; ++u) {
         const int c = tx + 16 * u;
-        if (c < nb) W[(long)r * ldw + c] = acc[q][u];
+        if (c < nb) O[(long)r * ldo + c] = acc[q][u];
       }
     }
   }
 }
 
 template <typename C>
-int rmul_block(C* W, long ldw, long sW, const C* M, long ldm, long sM, int n1, int nb, int batch, cudaStream_t s) {
+int rmul_block(const C* W, long ldw, long sW, const C* M, long ldm, long sM, int n1, int nb, int batch, C* O, long ldo,
+               long sO, cudaStream_t s) {
   if (nb <= 0 || n1 <= 0 || batch <= 0) return TSVD_OK;
   if (nb > 128) return TSVD_ERR_UNSUPPORTED;
   if (batch > 65535) return TSVD_ERR_UNSUPPORTED;
@@ -333,7 +336,7 @@ int rmul_block(C* W, long ldw, long sW, const C* M, long ldm, long sM, int n1, i
       cudaGetLastError();
       return TSVD_ERR_CUDA;
     }
-    kern<<<grid, 256, smem, s>>>(W, ldw, sW, M, ldm, sM, n1, nb, kchunk);
+    kern<<<grid, 256, smem, s>>>(W, ldw, sW, M, ldm, sM, n1, nb, kchunk, O, ldo, sO);
     TSVD_LAUNCHED();
     return TSVD_OK;
   };
@@ -348,8 +351,10 @@ int rmul_block(C* W, long ldw, long sW, const C* M, long ldm, long sM, int n1, i
     default: return go(k_rmul_block<C, 8>);
   }
 }
-template int rmul_block<double2>(double2*, long, long, const double2*, long, long, int, int, int, cudaStream_t);
-template int rmul_block<float2>(float2*, long, long, const float2*, long, long, int, int, int, cudaStream_t);
+template int rmul_block<double2>(const double2*, long, long, const double2*, long, long, int, int, int, double2*, long,
+                                 long, cudaStream_t);
+template int rmul_block<float2>(const float2*, long, long, const float2*, long, long, int, int, int, float2*, long, long,
+                                cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Dependent Krylov columns (exact low rank, zero data): replace column c+j by

@@ -1524,27 +1524,19 @@ __global__ void __launch_bounds__(NTH) k_tridiag_pairs_df(int m, int R, EigScrat
     const float4 c0 = T4[i], c1 = T4[i + 1];
     const dfl sub = dfl{c0.z, c0.w};
     const dfl dn = df_add(dfl{c1.x, c1.y}, nlam), un = dfl{c1.z, c1.w};
-    dfl l, rp, u1, u2;
-    if (fabsf(dcur.hi) >= fabsf(sub.hi)) {
-      const dfl piv = (fabsf(dcur.hi) < tiny) ? dfl{copysignf(tiny, dcur.hi), 0.0f} : dcur;
-      rp = df_rcp(piv);
-      l = df_mul(sub, rp);
-      u1 = ucur;
-      u2 = dfl{0.0f, 0.0f};
-      dcur = df_fma(dn, df_neg(l), ucur);
-      ucur = un;
-    } else {
-      // swap rows i and i+1: the new row i is (sub, dn, un); the old row i is eliminated
-      const dfl sb = (fabsf(sub.hi) < tiny) ? dfl{copysignf(tiny, sub.hi), 0.0f} : sub;
-      rp = df_rcp(sb);
-      l = df_mul(dcur, rp);
-      u1 = dn;
-      u2 = un;
-      const dfl nd = df_fma(ucur, df_neg(l), dn);
-      ucur = df_mul(df_neg(l), un);
-      dcur = nd;
-      flags |= 1u << (i & 31);
-    }
+    // partial pivoting without a branch (lanes would diverge on the swaps): with a swap the new
+    // row i is (sub, dn, un) and the old one is eliminated; both cases are one reciprocal, one
+    // multiply and one multiply-add on selected operands
+    const bool sw = !(fabsf(dcur.hi) >= fabsf(sub.hi));
+    const dfl pv = sw ? sub : dcur, nm = sw ? dcur : sub;
+    const dfl rp = df_rcp((fabsf(pv.hi) < tiny) ? dfl{copysignf(tiny, pv.hi), 0.0f} : pv);
+    const dfl l = df_mul(nm, rp);
+    const dfl u1 = sw ? dn : ucur, u2 = sw ? un : dfl{0.0f, 0.0f};
+    const dfl ua = sw ? ucur : dn, ub = sw ? dn : ucur;
+    const dfl lu = df_mul(df_neg(l), un);
+    dcur = df_fma(ua, df_neg(l), ub);  // dn - l ucur, or ucur - l dn after a swap
+    ucur = sw ? lu : un;
+    flags |= (sw ? 1u : 0u) << (i & 31);
     const long o = (long)i * ls;
     L0[o] = make_float2(l.hi, l.lo);
     L1[o] = make_float2(rp.hi, rp.lo);

@@ -76,9 +76,11 @@ int copy_cx(const C* src, long lds, long ss, C* dst, long ldd, long sd, int rows
 template <typename GC>
 int chol_inv(const GC* G, long ldg, long sG, GC* M, long ldm, long sM, int nb, int batch, double shift_rel,
              double dead_rel, uint32_t* dead, cudaStream_t s);
-// W <- W M in place for the n1 x nb blocks of every slice (M nb x nb dense).
+// O <- W M for the n1 x nb blocks of every slice (M nb x nb dense); O may be W itself (each CTA
+// stages its rows of W before writing).
 template <typename C>
-int rmul_block(C* W, long ldw, long sW, const C* M, long ldm, long sM, int n1, int nb, int batch, cudaStream_t s);
+int rmul_block(const C* W, long ldw, long sW, const C* M, long ldm, long sM, int n1, int nb, int batch, C* O, long ldo,
+               long sO, cudaStream_t s);
 // Replace dead columns [c, c+nb) of Q (n1 x ldq per slice) by unit vectors
 // orthogonal to columns [0, c+nb): Philox directions projected twice.
 template <typename C>

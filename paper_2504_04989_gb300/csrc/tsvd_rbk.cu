@@ -220,12 +220,13 @@ static int orth_block(const RbkDims& d, RbkWs<T>& w, int c, int nb, int block_id
     }
     {
       TSVD_STAGE("orth_trsm", s);
-      TSVD_TRY(rmul_block<CL>(W, b, sW, Mi, b, sG, n1, nb, h, s));
+      // the last pass writes the finished block straight into its columns of Q
+      if (pass < 2) TSVD_TRY(rmul_block<CL>(W, b, sW, Mi, b, sG, n1, nb, h, W, b, sW, s));
+      else TSVD_TRY(rmul_block<CL>(W, b, sW, Mi, b, sG, n1, nb, h, Q + c, m, sQ, s));
     }
   }
   {
     TSVD_STAGE("orth_repair", s);
-    TSVD_TRY(copy_cx<CL>(W, b, sW, Q + c, m, sQ, n1, nb, h, s));
     TSVD_TRY(repair_dead<CL>(Q, m, sQ, n1, c, nb, w.dead, h, seed, block_id, w.counters + 1, s));
   }
   if (!std::is_same<T, L>::value) {
