@@ -112,22 +112,22 @@ __global__ void __launch_bounds__(NTHR) k_chol_inv(const GC* __restrict__ G, lon
     const Rt inv = pinv[j];
     if (wrow1 > j) {
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      const int i = ei[e], k = ek[e];
-      const GC a = Sj[max(i, 0)];
-      const GC c = Sj[max(k, 0)];
-      const Rt ax = a.x * inv, ay = a.y * inv;  // conj(a) / d times c
-      GC t = v[e];
-      t.x = fma(-ax, c.x, t.x);
-      t.x = fma(-ay, c.y, t.x);
-      t.y = fma(-ax, c.y, t.y);
-      t.y = fma(ay, c.x, t.y);
-      if (i > j) v[e] = t;
-      if (i == j + 1) {  // row j+1 is final
-        S[eo[e]] = v[e];
-        if (k == i) pivot(i, v[e].x);
+      for (int e = 0; e < EPT; ++e) {
+        const int i = ei[e], k = ek[e];
+        const GC a = Sj[max(i, 0)];
+        const GC c = Sj[max(k, 0)];
+        const Rt ax = a.x * inv, ay = a.y * inv;  // conj(a) / d times c
+        GC t = v[e];
+        t.x = fma(-ax, c.x, t.x);
+        t.x = fma(-ay, c.y, t.x);
+        t.y = fma(-ax, c.y, t.y);
+        t.y = fma(ay, c.x, t.y);
+        if (i > j) v[e] = t;
+        if (i == j + 1) {  // row j+1 is final
+          S[eo[e]] = v[e];
+          if (k == i) pivot(i, v[e].x);
+        }
       }
-    }
     }
     __syncthreads();
   }
@@ -148,25 +148,25 @@ __global__ void __launch_bounds__(NTHR) k_chol_inv(const GC* __restrict__ G, lon
     const bool live_l = dj[l] > Rt(0);
     if (wrow0 < l) {
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      const int i = ei[e], k = ek[e];
-      const int ic = max(i, 0), kc = max(k, 0);
-      const GC cr = S[rb(ic) + l];
-      const GC xv = xl[kc];
-      const Rt sc = live_l ? er[e] : Rt(0);
-      const Rt cx = cr.x * sc, cy = cr.y * sc;
-      const GC x = (k == l) ? GC{rl, Rt(0)} : xv;
-      GC t = v[e];
-      t.x = fma(-cx, x.x, t.x);
-      t.x = fma(cy, x.y, t.x);
-      t.y = fma(-cx, x.y, t.y);
-      t.y = fma(-cy, x.x, t.y);
-      if (i >= 0 && i < l && k >= l) v[e] = t;
-      if (i == l - 1 && k > i) {  // row l-1 of B is final: publish X(l-1, k)
-        const Rt s2 = ri[i];
-        Xr[((l - 1) & 1) * nb + k] = GC{v[e].x * s2, v[e].y * s2};
+      for (int e = 0; e < EPT; ++e) {
+        const int i = ei[e], k = ek[e];
+        const int ic = max(i, 0), kc = max(k, 0);
+        const GC cr = S[rb(ic) + l];
+        const GC xv = xl[kc];
+        const Rt sc = live_l ? er[e] : Rt(0);
+        const Rt cx = cr.x * sc, cy = cr.y * sc;
+        const GC x = (k == l) ? GC{rl, Rt(0)} : xv;
+        GC t = v[e];
+        t.x = fma(-cx, x.x, t.x);
+        t.x = fma(cy, x.y, t.x);
+        t.y = fma(-cx, x.y, t.y);
+        t.y = fma(-cy, x.x, t.y);
+        if (i >= 0 && i < l && k >= l) v[e] = t;
+        if (i == l - 1 && k > i) {  // row l-1 of B is final: publish X(l-1, k)
+          const Rt s2 = ri[i];
+          Xr[((l - 1) & 1) * nb + k] = GC{v[e].x * s2, v[e].y * s2};
+        }
       }
-    }
     }
     __syncthreads();
   }
