@@ -377,3 +377,50 @@ def test_argument_errors(orc):
         orc.rtsvd_fourier(X, 7)  # R > min(n1, n2)
     with pytest.raises(ValueError):
         orc.dft_mode3(X, slices=[5])
+
+
+# --------------------------------------------------------------------------- Alg. 1 pin
+def _alg1_numpy(Xk, Omk, R, q):
+    """Alg. 1 (Sec. 3) on one Fourier slice, written with numpy / LAPACK only:
+    Y = (X X^H)^q X Om, Q = qr(Y), and the rank-R SVD of Q^H X."""
+    Y = Xk @ Omk
+    for _ in range(q):
+        Y = Xk @ (Xk.conj().T @ Y)
+    Q, _ = np.linalg.qr(Y)
+    s = np.linalg.svd(Q.conj().T @ Xk, compute_uv=False)
+    return Q, s[:R]
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_alg1_against_numpy_power_iteration(orc, q):
+    """The oracle's Alg. 1 mode against a numpy/LAPACK restatement on small
+    well-conditioned slices (spectrum 1..0.4, so (X X^H)^q X Om stays well
+    conditioned without intermediate orthonormalisation): the range projector
+    Q Q^H to 1e-10 and the top-R singular values of Q^H X to 1e-12.  A missing
+    power step, X in place of X^H, or Omega's rows taken from n1 all fail."""
+    n3, n1, n2, R, P = 5, 14, 11, 3, 2
+    sig = np.linspace(1.0, 0.4, 11)
+    X = wl.low_tubal_rank(n1, n2, n3, sig, noise_std=1e-2, seed=21)
+    om = wl.omega(n2, R + P, n3, seed=22)
+    Xh = np.fft.rfft(X, axis=0)
+    Omh = np.fft.rfft(om, axis=0)
+    Qo = orc.range_basis(X, R, P, q, mode="alg1", omega=om)
+    ro = orc.rtsvd_fourier(X, R, P, q, mode="alg1", omega=om)
+    for k in range(n3 // 2 + 1):
+        Qn, sn = _alg1_numpy(Xh[k], Omh[k], R, q)
+        np.testing.assert_allclose(Qo[k] @ Qo[k].conj().T, Qn @ Qn.conj().T, atol=1e-10)
+        np.testing.assert_allclose(ro["sig"][k], sn, rtol=1e-12, atol=0)
+
+
+def test_alg1_full_basis_is_exact_tsvd(orc):
+    """Degenerate case R + P >= min(n1, n2): the Alg. 1 basis spans the whole
+    column space, so its singular values are the exact per-slice ones (LAPACK)."""
+    n3, n1, n2, R, P = 4, 9, 6, 4, 3   # b = 7 > n2 = 6
+    X = rand(n3, n1, n2)
+    om = wl.omega(n2, R + P, n3, seed=5)
+    ro = orc.rtsvd_fourier(X, R, P, 1, mode="alg1", omega=om)
+    Xh = np.fft.rfft(X, axis=0)
+    for k in range(n3 // 2 + 1):
+        s = np.linalg.svd(Xh[k], compute_uv=False)[:R]
+        np.testing.assert_allclose(ro["sig"][k], s, rtol=1e-12)
+        assert ro["m"][k] == n2
