@@ -75,8 +75,12 @@ def _apply_reflectors_left(vs: np.ndarray, ph: np.ndarray, M: np.ndarray) -> np.
 
 
 def tensor_from_fourier(Xhat: np.ndarray, n3: int) -> np.ndarray:
-    """Real spatial tensor (n3, n1, n2) from its half spectrum (numpy irfft)."""
-    return np.fft.irfft(Xhat, n=n3, axis=0)
+    """Real spatial tensor (n3, n1, n2) from its half spectrum (library irfft)."""
+    try:
+        import scipy.fft as sf
+        return sf.irfft(Xhat, n=n3, axis=0, workers=-1)
+    except ImportError:
+        return np.fft.irfft(Xhat, n=n3, axis=0)
 
 
 def low_tubal_rank(n1: int, n2: int, n3: int, sigma, noise_std: float = 0.0, seed: int = 0,
@@ -97,28 +101,50 @@ def low_tubal_rank(n1: int, n2: int, n3: int, sigma, noise_std: float = 0.0, see
     return X
 
 
+def _reflected_diagonal(d, uvs, uph, vvs, vph):
+    """U diag(d) V^H for U = H_1..H_r diag(uph), V = H'_1..H'_r diag(vph)
+    (H = I - 2 v v^H), kept as diag(d') + L R^H while the reflectors are
+    applied (each adds one column to L and R), then formed by one n x 2r x n
+    product.  Same matrix as applying the reflectors to the dense product."""
+    n = d.shape[0]
+    dd = (uph * d).astype(np.complex128)            # diag(uph) diag(d)
+    L = np.zeros((n, 0), dtype=np.complex128)
+    Rm = np.zeros((n, 0), dtype=np.complex128)
+    for v in uvs[::-1]:                             # M <- H M: M - 2 v (M^H v)^H
+        w = dd.conj() * v + Rm @ (L.conj().T @ v)
+        L = np.concatenate([L, -2.0 * v[:, None]], axis=1)
+        Rm = np.concatenate([Rm, w[:, None]], axis=1)
+    dd = dd * vph.conj()                            # M <- M diag(vph)^H
+    Rm = Rm * vph[:, None]
+    for v in vvs[::-1]:                             # M <- M H': M - 2 (M v) v^H
+        mv = dd * v + L @ (Rm.conj().T @ v)
+        L = np.concatenate([L, -2.0 * mv[:, None]], axis=1)
+        Rm = np.concatenate([Rm, v[:, None]], axis=1)
+    M = L @ Rm.conj().T
+    M[np.arange(n), np.arange(n)] += dd
+    return M
+
+
 def power_law_reflector(n1: int, n2: int, n3: int, sigma, noise_rel: float = 0.0, seed: int = 0,
                         dtype=np.float64):
     """Large full-spectrum tensor: Xhat_k = U_k diag(sigma) V_k^H with U_k, V_k
     random reflector products (exact singular values sigma on every slice),
-    plus Gaussian noise of std noise_rel x RMS of the noise-free entries."""
+    plus Gaussian noise of std noise_rel x RMS of the noise-free entries.
+    Square slices (n1 == n2) with len(sigma) == n1."""
     sigma = np.asarray(sigma, dtype=np.float64)
-    r = len(sigma)
+    assert n1 == n2 == len(sigma)
     rng = _rng(seed, 3)
     h = n3 // 2 + 1
     uvs, uph = reflector_fourier_factor(n1, n3, rng)
     vvs, vph = reflector_fourier_factor(n2, n3, rng)
     Xh = np.empty((h, n1, n2), dtype=np.complex128)
     for k in range(h):
-        core = np.zeros((n1, n2), dtype=np.complex128)
-        core[np.arange(r), np.arange(r)] = sigma
-        M = _apply_reflectors_left(uvs[k], uph[k], core)            # U_k Sigma
-        M = _apply_reflectors_left(vvs[k], vph[k], M.conj().T)      # V_k (U_k Sigma)^H
-        Xh[k] = M.conj().T                                          # U_k Sigma V_k^H
+        Xh[k] = _reflected_diagonal(sigma, uvs[k], uph[k], vvs[k], vph[k])
     X = tensor_from_fourier(Xh, n3)
+    del Xh
     if noise_rel > 0:
         rms = float(np.sqrt(np.mean(X * X)))
-        X = X + noise_rel * rms * rng.standard_normal(X.shape)
+        X += noise_rel * rms * rng.standard_normal(X.shape, dtype=np.float32)
     return X.astype(dtype, copy=False)
 
 
