@@ -44,6 +44,8 @@ def lib():
         L.orc_range_basis_fourier.argtypes = [dp, i, i, i, i, i, i, i, dp, C.c_uint64, ip, i, dp]
         L.orc_rtsvd.argtypes = [dp, i, i, i, i, i, i, i, dp, C.c_uint64, dp, dp, dp, dp]
         L.orc_reconstruct.argtypes = [dp, dp, dp, i, i, i, i, dp]
+        L.orc_tqr.argtypes = [dp, i, i, i, dp, dp]
+        L.orc_tpinv.argtypes = [dp, i, i, i, dp]
         L.orc_num_threads.argtypes = []
         _lib = L
     return _lib
@@ -261,3 +263,23 @@ def rel_error(X, Xr):
     """Relative error e = ||X - Xr||_F / ||X||_F (Sec. 5)."""
     X = np.asarray(X, dtype=np.float64)
     return float(np.linalg.norm((X - Xr).ravel()) / np.linalg.norm(X.ravel()))
+
+
+def tqr(X):
+    """Alg. TQR: X = Q * R; returns Q (n3, n1, p), R (n3, p, n2), p = min(n1, n2)."""
+    X = _f64(X)
+    n3, n1, n2 = X.shape
+    p = min(n1, n2)
+    Q = np.empty((n3, n1, p))
+    R = np.empty((n3, p, n2))
+    _check(lib().orc_tqr(_dp(X), n1, n2, n3, _dp(Q), _dp(R)), "tqr")
+    return Q, R
+
+
+def tpinv(X):
+    """Alg. mp: the Moore-Penrose pseudoinverse (n3, n2, n1) of X (n3, n1, n2)."""
+    X = _f64(X)
+    n3, n1, n2 = X.shape
+    out = np.empty((n3, n2, n1))
+    _check(lib().orc_tpinv(_dp(X), n1, n2, n3, _dp(out)), "tpinv")
+    return out

@@ -372,7 +372,7 @@ int orc_tprod_backward(const double* A, const double* B, const double* dC, int n
   return 0;
 }
 
-/* Gradient of L = <dY, Q*Q^T*A> (the projection of Lemma mn38):
+/* Gradient of L = <dY, Q*Q^T*A> (the projection Q*Q^T*A of Sec. 4):
  * dA = Q*(Q^T*dY),  dQ = dY*(A^T*Q) + A*(dY^T*Q).  Q: n1 x m, A, dY: n1 x n2. */
 int orc_tproj_backward(const double* Q, const double* A, const double* dY, int n1, int m, int n2, int n3,
                        double* dQ, double* dA) {
@@ -662,5 +662,102 @@ int orc_reconstruct(const double* U, const double* S, const double* V, int n1, i
   orc_ttranspose(V, n2, R, n3, VT);
   orc_tprod(US, VT, n1, R, n2, n3, Xr);
   free(Sf); free(US); free(VT);
+  return 0;
+}
+
+/* ========================================================================== */
+/* Alg. TQR (Sec. 2): per non-redundant Fourier slice the economy QR          */
+/* qr(Xbar_k, 0), the other slices by conjugate symmetry, then the inverse    */
+/* DFT of both factors.  With p = min(n1, n2): Q is n1 x p x n3, R is          */
+/* p x n2 x n3.  A slice wider than tall (n1 < n2) is factored on its first   */
+/* n1 columns (what Householder QR of the whole slice does: the reflectors    */
+/* come from those columns) and R = Q^H Xbar_k.  The QR of a slice is unique  */
+/* only up to unit phases on the diagonal of R: this oracle (reading of the   */
+/* paper's MATLAB qr) fixes the diagonal of R real and non-negative, which    */
+/* keeps the DC and Nyquist factors real.                                     */
+/* ========================================================================== */
+static void qr_slice(int n1, int n2, const cplx* X, cplx* Q, cplx* R) {
+  const int p = n1 < n2 ? n1 : n2;
+  cplx* lead = (cplx*)malloc(sizeof(cplx) * (long)n1 * p);
+  cplx* Rl = (cplx*)malloc(sizeof(cplx) * (long)p * p);
+  take_cols(n1, n2, X, 0, p, lead);
+  orc_householder_qr(n1, p, lead, Q, Rl);
+  for (int j = 0; j < p; ++j) { /* Q <- Q D, with D = diag(phase of R_jj) */
+    const cplx d = Rl[(long)j * p + j];
+    const cplx ph = (cabs(d) > 0) ? d / cabs(d) : 1.0;
+    for (int i = 0; i < n1; ++i) Q[(long)i * p + j] *= ph;
+  }
+  cgemm('H', 'N', p, n2, n1, Q, X, R); /* R = Q^H X: upper trapezoidal, real diagonal >= 0 */
+  for (int i = 0; i < p; ++i) {
+    for (int c = 0; c < i && c < n2; ++c) R[(long)i * n2 + c] = 0;
+    R[(long)i * n2 + i] = creal(R[(long)i * n2 + i]);
+  }
+  free(lead);
+  free(Rl);
+}
+
+int orc_tqr(const double* X, int n1, int n2, int n3, double* Q, double* R) {
+  if (n1 < 1 || n2 < 1 || n3 < 1) return -1;
+  const int h = n3 / 2 + 1, p = n1 < n2 ? n1 : n2;
+  cplx* Xh = (cplx*)malloc(sizeof(cplx) * (long)h * n1 * n2);
+  cplx* Qh = (cplx*)malloc(sizeof(cplx) * (long)h * n1 * p);
+  cplx* Rh = (cplx*)malloc(sizeof(cplx) * (long)h * p * n2);
+  orc_dft_mode3(X, n1, n2, n3, NULL, 0, Xh);
+#pragma omp parallel for schedule(dynamic)
+  for (int k = 0; k < h; ++k)
+    qr_slice(n1, n2, Xh + (long)k * n1 * n2, Qh + (long)k * n1 * p, Rh + (long)k * p * n2);
+  orc_idft_mode3(Qh, n1, p, n3, Q);
+  orc_idft_mode3(Rh, p, n2, n3, R);
+  free(Xh);
+  free(Qh);
+  free(Rh);
+  return 0;
+}
+
+/* ========================================================================== */
+/* Alg. mp (Sec. 2): per non-redundant Fourier slice the Moore-Penrose        */
+/* pseudoinverse pinv(Xbar_k) = V diag(1/s) W^H over the singular values above */
+/* the tolerance max(n1, n2) * eps * s_max (MATLAB's pinv default), from the   */
+/* one-sided Jacobi SVD (of Xbar_k^H when the slice is wide, since            */
+/* pinv(X) = pinv(X^H)^H); conjugate symmetry and the inverse DFT give the    */
+/* n2 x n1 x n3 tensor X^dagger.                                              */
+/* ========================================================================== */
+static void pinv_slice(int n1, int n2, const cplx* X, cplx* Xp) {
+  const int tall = n1 >= n2;
+  const int M = tall ? n1 : n2, N = tall ? n2 : n1;
+  cplx* A = (cplx*)malloc(sizeof(cplx) * (long)M * N);
+  cplx* W = (cplx*)malloc(sizeof(cplx) * (long)M * N);
+  cplx* V = (cplx*)malloc(sizeof(cplx) * (long)N * N);
+  double* s = (double*)malloc(sizeof(double) * N);
+  for (int i = 0; i < M; ++i)
+    for (int c = 0; c < N; ++c) A[(long)i * N + c] = tall ? X[(long)i * n2 + c] : conj(X[(long)c * n2 + i]);
+  orc_jacobi_svd(M, N, A, W, s, V); /* A = W diag(s) V^H */
+  const double tol = (double)M * DBL_EPSILON * s[0];
+  /* pinv(A) = V diag(1/s) W^H is N x M; pinv(X) = pinv(A) (tall) or pinv(A)^H (wide) */
+  for (int r = 0; r < N; ++r)
+    for (int c = 0; c < M; ++c) {
+      cplx acc = 0;
+      for (int k = 0; k < N; ++k)
+        if (s[k] > tol) acc += V[(long)r * N + k] * (1.0 / s[k]) * conj(W[(long)c * N + k]);
+      if (tall) Xp[(long)r * n1 + c] = acc;   /* Xp is n2 x n1 = N x M */
+      else Xp[(long)c * n1 + r] = conj(acc);  /* Xp is n2 x n1 = M x N */
+    }
+  free(A);
+  free(W);
+  free(V);
+  free(s);
+}
+
+int orc_tpinv(const double* X, int n1, int n2, int n3, double* Xp) {
+  if (n1 < 1 || n2 < 1 || n3 < 1) return -1;
+  const int h = n3 / 2 + 1;
+  cplx* Xh = (cplx*)malloc(sizeof(cplx) * (long)h * n1 * n2);
+  cplx* Ph = (cplx*)malloc(sizeof(cplx) * (long)h * n2 * n1);
+  orc_dft_mode3(X, n1, n2, n3, NULL, 0, Xh);
+#pragma omp parallel for schedule(dynamic)
+  for (int k = 0; k < h; ++k) pinv_slice(n1, n2, Xh + (long)k * n1 * n2, Ph + (long)k * n2 * n1);
+  orc_idft_mode3(Ph, n2, n1, n3, Xp);
+  free(Xh);
+  free(Ph);
   return 0;
 }

@@ -78,6 +78,11 @@ int orc_rtsvd(const double* X, int n1, int n2, int n3, int R, int P, int q, int 
 /* X_R = U * S * V^T from spatial factors (S given as (n3,R) f-diagonal tubes) */
 int orc_reconstruct(const double* U, const double* S, const double* V, int n1, int n2, int n3, int R, double* Xr);
 
+/* Alg. TQR: X (n3,n1,n2) = Q * R with Q (n3,n1,p), R (n3,p,n2), p = min(n1,n2);
+ * per Fourier slice the economy QR with the diagonal of R real and >= 0. */
+int orc_tqr(const double* X, int n1, int n2, int n3, double* Q, double* R);
+/* Alg. mp: Moore-Penrose pseudoinverse Xp (n3,n2,n1) of X (n3,n1,n2). */
+int orc_tpinv(const double* X, int n1, int n2, int n3, double* Xp);
 int orc_num_threads(void);
 
 #ifdef __cplusplus
