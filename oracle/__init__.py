@@ -17,7 +17,7 @@ from . import build as _build
 
 _lib = None
 
-MODES = {"canonical": 0, "literal": 1, "alg1": 2, "exact": 3}
+MODES = {"canonical": 0, "literal": 1, "alg1": 2, "exact": 3, "qtrunc": 4}
 
 
 def lib():

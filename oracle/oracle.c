@@ -542,7 +542,16 @@ static int rtsvd_slice(const cplx* Xk, const cplx* Om, int n1, int n2, int R, in
   } else {
     int mmax = ((mode == ORC_ALG1_POWER) ? 1 : (q + 1)) * b;
     cplx* Qb = (cplx*)malloc(sizeof(cplx) * (long)n1 * mmax);
-    m = range_basis(Xk, Om, n1, n2, b, q, mode, Qb);
+    m = range_basis(Xk, Om, n1, n2, b, q, (mode == ORC_ALG2_QTRUNC) ? ORC_ALG2_CANONICAL : mode, Qb);
+    if (mode == ORC_ALG2_QTRUNC && m > b) {
+      /* Ex. 1 (Sec. 5): the factor Q of Alg. 2 truncated to k + p = R + P terms
+       * before the projection; read as its leading R + P columns */
+      cplx* Qt = (cplx*)malloc(sizeof(cplx) * (long)n1 * b);
+      take_cols(n1, m, Qb, 0, b, Qt);
+      free(Qb);
+      Qb = Qt;
+      m = b;
+    }
     cplx* CH = (cplx*)malloc(sizeof(cplx) * (long)n2 * m); /* C^H = Xk^H Q */
     cgemm('H', 'N', n2, m, n1, Xk, Qb, CH);
     cplx* W = (cplx*)malloc(sizeof(cplx) * (long)n2 * m);
@@ -574,7 +583,7 @@ int orc_rtsvd_fourier(const double* X, int n1, int n2, int n3, int R, int P, int
                       cplx* Uhat, double* sig, cplx* Vhat, double* err2, int* m_used) {
   if (n1 < 1 || n2 < 1 || n3 < 1 || R < 1 || P < 0 || q < 0) return -1;
   if (R > n1 || R > n2) return -1;
-  if (mode < ORC_ALG2_CANONICAL || mode > ORC_EXACT) return -1;
+  if (mode < ORC_ALG2_CANONICAL || mode > ORC_ALG2_QTRUNC) return -1;
   const int h = n3 / 2 + 1;
   if (!slices) ns = h;
   const int b = R + P;

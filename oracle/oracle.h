@@ -55,7 +55,9 @@ int orc_householder_qr(int M, int N, const orc_cplx* X, orc_cplx* Q, orc_cplx* R
 int orc_jacobi_svd(int M, int N, const orc_cplx* X, orc_cplx* W, double* s, orc_cplx* V);
 
 /* ---- randomized T-SVD in the Fourier domain (Sec. 3) ---- */
-enum { ORC_ALG2_CANONICAL = 0, ORC_ALG2_LITERAL = 1, ORC_ALG1_POWER = 2, ORC_EXACT = 3 };
+/* ORC_ALG2_QTRUNC: Alg. 2 with the basis Q truncated to its leading R+P
+ * columns before the projection (the variant Ex. 1 of Sec. 5 reports). */
+enum { ORC_ALG2_CANONICAL = 0, ORC_ALG2_LITERAL = 1, ORC_ALG1_POWER = 2, ORC_EXACT = 3, ORC_ALG2_QTRUNC = 4 };
 /*
  * For every requested Fourier slice k (slices[s], 0 <= k < h):
  *   Uhat[s] : n1 x R complex,  sig[s] : R (descending),  Vhat[s] : n2 x R complex

@@ -151,7 +151,7 @@ def power_law_reflector(n1: int, n2: int, n3: int, sigma, noise_rel: float = 0.0
 def optimal_error2(sigma, R: int) -> float:
     """Eckart-Young closed form for the constructions above (no noise):
     ||X - X_R||_F^2 = (1/n3) sum_k sum_{i>R} sigma_i^2 = sum_{i>R} sigma_i^2,
-    by Parseval (Sec. 2, eq_fou) and the per-slice matrix Eckart-Young theorem."""
+    by Parseval (Sec. 2, the Parseval relation of the mode-3 DFT) and the per-slice matrix Eckart-Young theorem."""
     s = np.asarray(sigma, dtype=np.float64)
     return float(np.sum(s[R:] ** 2))
 
@@ -193,6 +193,19 @@ def make_c5(seed: int = 0):
     X = low_tubal_rank(256, 256, 100, np.linspace(10.0, 1.0, 20), noise_std=0.0, seed=seed)
     mask = (_rng(seed, 4).random(X.shape) < 0.3)
     return X, mask
+
+
+def ex1_sigma(n: int, case: int) -> np.ndarray:
+    """Ex. 1 (Sec. 5) singular values of every frontal slice: case 1
+    sigma_m = m^-5, case 2 m^-6, case 3 0.5^m, m = 1..n."""
+    m = np.arange(1, n + 1, dtype=np.float64)
+    return {1: m ** -5.0, 2: m ** -6.0, 3: 0.5 ** m}[case]
+
+
+def make_ex1(n: int, case: int, seed: int = 0) -> np.ndarray:
+    """n x n x n tensor with the Ex. 1 spectrum on every Fourier slice (Haar
+    t-factors, no noise)."""
+    return low_tubal_rank(n, n, n, ex1_sigma(n, case), noise_std=0.0, seed=seed)
 
 
 def make_c4(seed: int = 0, count: int = 256):

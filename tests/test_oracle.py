@@ -63,7 +63,7 @@ def test_idft_inverse_and_parseval(orc, n3):
     Xh = orc.dft_mode3(X)
     np.testing.assert_allclose(orc.idft_mode3(Xh, n3), X, atol=1e-12)
     np.testing.assert_allclose(orc.idft_mode3(Xh, n3), np.fft.irfft(Xh, n=n3, axis=0), atol=1e-12)
-    # Parseval (Sec. 2, eq_fou) over the full spectrum, i.e. half-spectrum weights 1, 2, .., (1)
+    # Parseval (Sec. 2, the Parseval relation) over the full spectrum, i.e. half-spectrum weights 1, 2, .., (1)
     full = np.fft.fft(X, axis=0)
     assert np.isclose(np.sum(X ** 2), np.sum(np.abs(full) ** 2) / n3, rtol=1e-12)
     w = np.full(n3 // 2 + 1, 2.0)
@@ -265,7 +265,7 @@ def test_basis_orthogonal_tensor(orc):
 
 def test_alg2_monotone_in_q_and_beats_alg1(orc):
     """With a fixed Omega the Krylov spaces are nested in q, and the Rayleigh-Ritz
-    result is the best rank-R approximation from range(Q) (eq. mn39), so the
+    result is the best rank-R approximation from range(Q) (Sec. 4, best approximation within range(Q)), so the
     error cannot grow with q and Alg. 2 is never worse than Alg. 1."""
     X = wl.low_tubal_rank(40, 36, 6, np.arange(1, 37) ** -1.0, seed=7)
     R, P = 5, 2
@@ -292,8 +292,8 @@ def test_nested_krylov_bases(orc):
         assert np.linalg.norm(resid) < 1e-10
 
 
-def test_lemma_mn38_and_theorems(orc):
-    """Lemma mn38: the output equals the projection U_k U_k^H A (i.e.
+def test_projection_lemma_and_theorems(orc):
+    """Sec. 4, the projection lemma: the output equals the projection U_k U_k^H A (i.e.
     Q (Q^H A)_k); Thm. 3 (Frobenius) and Thm. 1 (spectral) bounds, per slice."""
     sig = np.arange(1, 21) ** -0.7
     X = wl.low_tubal_rank(24, 20, 5, sig, noise_std=1e-3, seed=8)
@@ -325,7 +325,7 @@ def test_lemma_mn38_and_theorems(orc):
         Z = np.concatenate(blocks, axis=1)
         Pz = Z - Q @ (Q.conj().T @ Z)
         assert np.linalg.norm(A - Q @ C, 2) <= np.linalg.norm(Pz, 2) ** (1.0 / (2 * q + 1)) * (1 + 1e-10)
-        # Lemma jens:lem: ||P M P||^r <= ||P M^r P|| for PSD M and an orthogonal projector P
+        # Sec. 4, the projected power inequality: ||P M P||^r <= ||P M^r P|| for PSD M and an orthogonal projector P
         Pm = np.eye(A.shape[0]) - Q @ Q.conj().T
         M = A @ A.conj().T
         r = 2 * q + 1
@@ -424,3 +424,23 @@ def test_alg1_full_basis_is_exact_tsvd(orc):
         s = np.linalg.svd(Xh[k], compute_uv=False)[:R]
         np.testing.assert_allclose(ro["sig"][k], s, rtol=1e-12)
         assert ro["m"][k] == n2
+
+
+# --------------------------------------------------------------------------- Ex. 1 truncated basis
+def test_qtrunc_against_numpy_sketch(orc):
+    """The Q-truncated variant of Alg. 2 (Ex. 1, Sec. 5: Q cut to its leading
+    R + P columns before the projection) against numpy/LAPACK: the leading
+    R + P columns of the Krylov basis span X Omega, so the result is the
+    rank-R SVD of Q_0^H X with Q_0 = qr(X Omega), whatever q is."""
+    n3, n1, n2, R, P, q = 5, 30, 26, 4, 3, 2
+    X = wl.low_tubal_rank(n1, n2, n3, np.arange(1, 27) ** -2.0, noise_std=1e-3, seed=31)
+    om = wl.omega(n2, R + P, n3, seed=32)
+    ro = orc.rtsvd_fourier(X, R, P, q, mode="qtrunc", omega=om)
+    assert np.all(ro["m"] == R + P)
+    Xh, Omh = np.fft.rfft(X, axis=0), np.fft.rfft(om, axis=0)
+    for k in range(n3 // 2 + 1):
+        Q0, _ = np.linalg.qr(Xh[k] @ Omh[k])
+        s = np.linalg.svd(Q0.conj().T @ Xh[k], compute_uv=False)[:R]
+        np.testing.assert_allclose(ro["sig"][k], s, rtol=1e-12)
+    full = orc.rtsvd_fourier(X, R, P, q, omega=om)  # the full basis is at least as good (nested spans)
+    assert np.all(full["err2"] <= ro["err2"] * (1 + 1e-12))
