@@ -17,9 +17,16 @@
 //    same call), so nothing is cleared;
 //  * calls whose kernels overlap on the GPU (different streams, or different
 //    host threads, without ordering between them) race on the array;
-//  * the first call on a device looks up the array's device address on that
-//    device (cudaGetSymbolAddress), so make that first call before any CUDA
-//    graph capture.
+//  * the array lives in this file's own module, which holds no kernel; under
+//    CUDA's lazy module loading (the default) that module, and with it the
+//    16 MiB, is loaded on a device at the first call there (the address
+//    lookup below), so make that first call before sealing a pool or arena
+//    that must not grow afterwards, and before any CUDA graph capture;
+//  * every call outside stream capture looks the address up again
+//    (cudaGetSymbolAddress allocates nothing once the module is loaded), so a
+//    device reset that reloads the module at another address is followed;
+//    inside a capture the address of the last uncaptured call on the device
+//    is used.
 #include <type_traits>
 
 #include "common.cuh"
@@ -35,19 +42,29 @@ constexpr size_t TPROD_NOALLOC_SCRATCH_BYTES = (size_t)16 << 20;
 static __device__ __align__(256) unsigned char g_tprod_scratch[TPROD_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
-static void* g_scratch_ptr[kMaxDevices];  // device address of g_tprod_scratch per device (null = not set up)
+static void* g_scratch_ptr[kMaxDevices];  // last looked-up device address of g_tprod_scratch per device
 
-// Once per device, with that device current: the device address of the array.
-static int scratch_address(void** out) {
+// The device address of the array on the current device: looked up on every
+// call outside stream capture (a context re-created after a device reset can
+// place the module elsewhere), the cached one inside a capture.
+static int scratch_address(cudaStream_t s, void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TSVD_ERR_CUDA;
-  void* p = __atomic_load_n(&g_scratch_ptr[dev], __ATOMIC_ACQUIRE);
-  if (!p) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    cap = cudaStreamCaptureStatusActive;  // cannot tell: do not call into the runtime's module tables
+  }
+  void* p = nullptr;
+  if (cap == cudaStreamCaptureStatusNone) {
     if (cudaGetSymbolAddress(&p, g_tprod_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return TSVD_ERR_CUDA;
     }
     __atomic_store_n(&g_scratch_ptr[dev], p, __ATOMIC_RELEASE);
+  } else {
+    p = __atomic_load_n(&g_scratch_ptr[dev], __ATOMIC_ACQUIRE);
+    if (!p) return TSVD_ERR_CUDA;  // no uncaptured call on this device yet
   }
   *out = p;
   return TSVD_OK;
@@ -57,6 +74,11 @@ template <typename T>
 static int tprod_noalloc_run(const T* A, const T* B, T* Cout, int n1, int n2, int n4, int n3, cudaStream_t s) {
   using C = cx_t<T>;
   const size_t h = n3 / 2 + 1;
+  // each operand's size in floating point first: the size_t products below
+  // could wrap for very large dimensions and pass the limit check
+  const double lim = (double)TPROD_NOALLOC_SCRATCH_BYTES / sizeof(C);
+  if ((double)h * n1 * n2 > lim || (double)h * n2 * n4 > lim || (double)h * n1 * n4 > lim)
+    return TSVD_ERR_UNSUPPORTED;
   Carver cv(nullptr);
   cv.take<C>(h * n1 * n2);
   cv.take<C>(h * n2 * n4);
@@ -64,7 +86,7 @@ static int tprod_noalloc_run(const T* A, const T* B, T* Cout, int n1, int n2, in
   const size_t operands = cv.bytes();
   if (operands > TPROD_NOALLOC_SCRATCH_BYTES) return TSVD_ERR_UNSUPPORTED;
   void* base = nullptr;
-  TSVD_TRY(scratch_address(&base));
+  TSVD_TRY(scratch_address(s, &base));
   Carver w(base);
   C* Ah = w.take<C>(h * n1 * n2);
   C* Bh = w.take<C>(h * n2 * n4);
