@@ -1,18 +1,23 @@
 """Benchmark of the randomized block Krylov truncated T-SVD (arXiv 2504.04989).
 
-Workload (one step = one whole T-SVD, every stage of Alg. 2): the image-like
-512 x 512 x 64 float32 tensor with per-Fourier-slice singular values
-sigma_i = i^-1.5 (full rank), R = 50, P = 10, q = 4, synthetic (seeded), the
-input resident in HBM.  Metric: rank-R T-SVD approximations per second.
+Workload (one step = one whole T-SVD, every stage of Alg. 2): the video-like
+2048 x 2048 x 128 float32 tensor with per-Fourier-slice singular values
+sigma_i = 1/i plus Gaussian noise of 1e-4 x the RMS entry, R = 100, P = 20,
+q = 3, synthetic (seeded), the input resident in HBM.  Metric: rank-R T-SVD
+approximations per second on the mixed-precision path (Krylov products on the
+tensor cores in TF32), next to the FP64 path on the same tensor at equal
+reconstruction error, and the t-product TFLOP/s on the paper-shaped products.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision tf32|bf16|fp32|fp64]
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
 
 Under torchrun every rank runs its own independent tensor (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
 """
 import argparse
+import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -24,27 +29,62 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="image-like 512x512x64 fp32, sigma_i=i^-1.5 full rank, R=50 P=10 q=4",
-                n1=512, n2=512, n3=64, R=50, P=10, q=4)
+WORKLOAD = dict(name="video-like 2048x2048x128 fp32, sigma_i=1/i + noise 1e-4 x RMS, R=100 P=20 q=3",
+                n1=2048, n2=2048, n3=128, R=100, P=20, q=3)
+C2 = dict(name="image-like 512x512x64 fp32, sigma_i=i^-1.5 full rank, R=50 P=10 q=4",
+          n1=512, n2=512, n3=64, R=50, P=10, q=4)
 METRIC = "rank-R T-SVD approximations/s"
-# ALU peaks from unit counts and clocks (GB300: 152 SMs at 2.07 GHz; per SM and
-# clock 2 FP64 FMA lanes, 128 FP32 FMA lanes).
-SMS, CLOCK_GHZ = 152, 2.07
-FP64_PEAK_TFLOPS = SMS * CLOCK_GHZ * 2 * 2 / 1e3            # 1.259
-FP32_ISSUE_TINST = SMS * CLOCK_GHZ * 128 / 1e3               # 40.3 T FP32 instructions/s
-DF_FMA_INSTR = 15                                            # FP32 instructions per double-float multiply-add
-DF_PEAK_TFLOPS = FP32_ISSUE_TINST / DF_FMA_INSTR * 2         # 5.37 (FP64-accuracy flops on the FP32 pipe)
-# DRAM bytes per launch of the dominant kernel from the committed ncu capture of
-# the same kernel and workload (profiles/k_hetrd_df_512x512x64_fp32.md); None
-# once the kernel changes.
-NCU_TRAFFIC = {"eig_hetrd": 24.80e6}
+DF_FMA_INSTR = 15  # FP32 instructions per double-float multiply-add (TwoProduct, cross terms, TwoSum, renormalisation)
+# DRAM bytes per launch of a kernel from an ncu capture, valid only while the
+# source file the capture was taken on is unchanged (sha256 prefix of that file).
+NCU_TRAFFIC = {}
 
 
-def peaks():
+def peaks_file():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "fallback": True}
+
+
+def src_sha16(relpath):
+    try:
+        return hashlib.sha256(open(os.path.join(ROOT, relpath), "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+
+
+def ncu_traffic(stage):
+    t = NCU_TRAFFIC.get(stage)
+    if t and src_sha16(t["src"]) == t["sha16"]:
+        return t["bytes_per_launch"]
+    return None
+
+
+def measure_alu_peaks(torch, dev, stream):
+    """Dense-matmul peaks measured here (cuBLAS, the same kind of denominator as
+    the driver's bf16 number): FP64, FP32 without TF32 and TF32, TFLOP/s."""
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    for name, dt, n, tf32 in (("fp64", torch.float64, 8192, False), ("fp32", torch.float32, 8192, False),
+                              ("tf32", torch.float32, 8192, True)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device=dev, dtype=dt)
+        b = torch.randn(n, n, device=dev, dtype=dt)
+        c = a @ b
+        torch.cuda.synchronize(dev)
+        reps = 3 if name == "fp64" else 10
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            torch.matmul(a, b, out=c)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        out[name] = 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        del a, b, c
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    out["double_float"] = out["fp32"] / DF_FMA_INSTR * 2  # FP64-accuracy flops on the FP32 pipe
+    return out
 
 
 def algorithmic(stage, d, precision):
@@ -59,18 +99,18 @@ def algorithmic(stage, d, precision):
         return {"flops": 16.0 / 3.0 * m ** 3 * h}
     if stage == "gram_c":         # G = C C^H (Hermitian: half of the m x m outputs)
         return {"flops": cm * n2 * m * (m + 1) / 2 * h}
-    if stage == "orth_cgs":       # two classical Gram-Schmidt sweeps per block
-        return {"flops": sum(2 * 2 * cm * n1 * c * nb for c, nb in zip(c_before, blocks)) * h}
+    if stage == "orth_cgs":       # two classical Gram-Schmidt sweeps per block pass (3 passes)
+        return {"flops": sum(3 * 2 * cm * n1 * c * nb for c, nb in zip(c_before, blocks)) * h}
     if stage == "orth_gram":
-        return {"flops": sum(2 * cm * n1 * nb * (nb + 1) / 2 for nb in blocks) * h}
+        return {"flops": sum(3 * cm * n1 * nb * (nb + 1) / 2 for nb in blocks) * h}
     if stage == "orth_trsm":
-        return {"flops": sum(2 * cm * n1 * nb * nb / 2 for nb in blocks) * h}
-    if stage == "krylov_gemm":    # A Omega, then A^H Q and A Y per Krylov step, and the last A^H Q
+        return {"flops": sum(3 * cm * n1 * nb * nb / 2 for nb in blocks) * h}
+    if stage in ("krylov_gemm", "krylov_gemm_tc"):  # A Omega, A^H Q and A Y per Krylov step, the last A^H Q
         return {"flops": cm * n1 * n2 * (sum(blocks) + sum(blocks[:-1]) + blocks[-1]) * h}
-    if stage in ("rfft", "irfft"):
-        s = 8 if precision == "fp64" else 4
-        if stage == "rfft":
-            return {"bytes": s * (n1 * n2 * n3 + 2 * n1 * n2 * h)}
+    s = 8 if precision == "fp64" else 4
+    if stage == "rfft":
+        return {"bytes": s * (n1 * n2 * n3 + 2 * n1 * n2 * h)}
+    if stage == "irfft":
         return {"bytes": s * (2 * (n1 + n2) * R * h + (n1 + n2) * R * n3)}
     return {}
 
@@ -84,6 +124,7 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.lines = []
 
     def __enter__(self):
         try:
@@ -127,48 +168,67 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-ORACLE_SLICES = 16  # bounded sample: this many of the workload's Fourier slices per oracle run
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
 
 
-def oracle_sample(X, d, nslices=ORACLE_SLICES):
-    """The FP64 CPU oracle, as it stands, on `nslices` of the workload's
-    h = n3/2 + 1 independent Fourier slices (OpenMP across slices); the time
-    of a whole T-SVD is that of the sample scaled by h / nslices."""
+def oracle_slices(X, d, slices):
+    """The FP64 CPU oracle, as it stands, on the listed Fourier slices of one
+    T-SVD of X (each slice: its DFT, the Krylov basis, the projection and the
+    small SVD; OpenMP across the slices).  Returns the wall time."""
     import oracle
-    h = d["n3"] // 2 + 1
-    om = oracle.gaussian(0, d["n3"] * d["n2"] * (d["R"] + d["P"])).reshape(d["n3"], d["n2"], d["R"] + d["P"])
     t0 = time.perf_counter()
-    oracle.rtsvd_fourier(X, d["R"], d["P"], d["q"], omega=om, slices=list(range(nslices)))
-    dt = time.perf_counter() - t0
-    return dt * h / nslices, dt, oracle.num_threads()
+    oracle.rtsvd_fourier(X, d["R"], d["P"], d["q"], seed=0, slices=list(slices))
+    return time.perf_counter() - t0, oracle.num_threads()
 
 
 def cpu_baseline(X, d):
-    per_tsvd, dt, cores = oracle_sample(X.astype(np.float64), d)
-    return {"value": 1.0 / per_tsvd, "unit": "T-SVD/s", "cores": cores, "kind": "oracle",
-            "sample": "%d of the %d Fourier slices of one T-SVD of the workload (FP64, %.1f s), scaled to the whole "
-                      "T-SVD" % (ORACLE_SLICES, d["n3"] // 2 + 1, dt)}
+    """One full wave of the oracle: as many Fourier slices as host threads, run
+    at once by the oracle's loop over slices.  value = the T-SVD work done
+    (slices / h) / wall time; a single T-SVD needs ceil(h / threads) waves."""
+    import oracle
+    h = d["n3"] // 2 + 1
+    cores = oracle.num_threads()
+    ns = min(cores, h)
+    dt, cores = oracle_slices(X, d, range(ns))
+    return {"value": (ns / h) / dt, "unit": "T-SVD/s", "cores": cores, "kind": "oracle",
+            "sample": "%d of the %d Fourier slices of one T-SVD (their DFT, Krylov basis, projection and SVD; FP64), "
+                      "run at once on %d host threads in %.1f s; value = (%d/%d T-SVD) / wall time; one whole T-SVD "
+                      "takes ceil(%d/%d) = %d such waves, %.0f s" % (ns, h, cores, dt, ns, h, h, cores,
+                                                                    math.ceil(h / cores), math.ceil(h / cores) * dt),
+            "cpu_model": cpu_model(), "nproc": os.cpu_count()}
 
 
 def run_reference(args, d, rank, world):
+    """The oracle on the bench workload: W warm-up steps, then K timed steps,
+    each step the oracle's Alg. 2 on one Fourier slice (1/h of a T-SVD); the K
+    steps go to the oracle's OpenMP loop over slices as one call, timed as a
+    whole."""
     if rank != 0:
         return
     from paper_2504_04989_gb300 import workloads as wl
-    X = wl.make_c2(0).astype(np.float32).astype(np.float64)
-    steps = []
-    for i in range(args.warmup + args.steps):
-        per, dt, cores = oracle_sample(X, d)
-        if i >= args.warmup:
-            steps.append(per)
-    t = sum(steps)
-    val = args.steps / t
+    X = wl.make_c3(0).astype(np.float64)
+    h = d["n3"] // 2 + 1
+    if args.warmup > 0:
+        oracle_slices(X, d, [i % h for i in range(args.warmup)])
+    dt, cores = oracle_slices(X, d, [(args.warmup + i) % h for i in range(args.steps)])
+    val = (args.steps / h) / dt
+    sample = ("each step: the oracle's Alg. 2 on one of the %d Fourier slices of one T-SVD (1/%d of the T-SVD: "
+              "the slice's DFT, Krylov basis, projection, SVD; FP64); the %d steps run as one call of the oracle's "
+              "OpenMP loop over slices on %d threads, %.1f s wall" % (h, h, args.steps, cores, dt))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "T-SVD/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": d["name"], "precision": "fp64 CPU oracle"},
-            "cpu_baseline": {"value": val, "unit": "T-SVD/s", "cores": cores, "kind": "oracle",
-                             "sample": "each step: %d of the %d Fourier slices of one T-SVD, scaled to the whole "
-                                       "T-SVD" % (ORACLE_SLICES, d["n3"] // 2 + 1)},
+            "cpu_baseline": {"value": val, "unit": "T-SVD/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model(), "nproc": os.cpu_count()},
             "e2e": {"value": val, "unit": "T-SVD/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -190,6 +250,19 @@ def job_value(steps, world, seconds):
     return world * steps / seconds
 
 
+def timed_calls(torch, fn, k, flush, stream, dev):
+    """k calls of fn, each bracketed by CUDA events on `stream` after an L2
+    flush; mean milliseconds."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    return sum(a.elapsed_time(b) for a, b in ev) / k
+
+
 def batched_bench(api, wl, dev, count, lanes, steps, flush, stream):
     """Uneven batch (n1, n2 ~ U{32..512}, n3 ~ U{8,16,32,64}, tubal rank
     r ~ U{5..40}, R = r, P = 5, q = 2, FP32): `count` tensors as one
@@ -201,26 +274,15 @@ def batched_bench(api, wl, dev, count, lanes, steps, flush, stream):
     Rs = [it["R"] for it in items]
     xs = [torch.from_numpy(it["X"].astype(np.float32)).to(dev) for it in items]
     del items
-
-    def timed(plan, k):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
-        for a, b in ev:
-            flush.zero_()
-            a.record(stream)
-            plan()
-            b.record(stream)
-        torch.cuda.synchronize(dev)
-        return sum(a.elapsed_time(b) for a, b in ev) / k
-
     eager = api.RbkBatchPlan(shapes, Rs, P=5, q=2, seed=0, precision="fp32", lanes=1, device=dev)
     eager(xs)
-    ms_eager = timed(eager, 1)
+    ms_eager = timed_calls(torch, eager, 1, flush, stream, dev)
     del eager
     plan = api.RbkBatchPlan(shapes, Rs, P=5, q=2, seed=0, precision="fp32", lanes=lanes, device=dev, graph=True)
     plan(xs)
     torch.cuda.synchronize(dev)
-    timed(plan, 1)
-    ms = timed(plan, steps)
+    timed_calls(torch, plan, 1, flush, stream, dev)
+    ms = timed_calls(torch, plan, steps, flush, stream, dev)
     return {"workload": "uneven batch: n1, n2 ~ U{32..512}, n3 ~ U{8,16,32,64}, rank ~ U{5..40}, P=5, q=2, fp32",
             "tensors": count, "lanes": lanes, "graph": True, "ms_per_batch": ms,
             "tsvd_per_s": count * 1000.0 / ms, "eager_single_stream_ms": ms_eager}
@@ -232,9 +294,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "bf16", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batched-count", type=int, default=64,
+    ap.add_argument("--batched-count", type=int, default=256,
                     help="tensors of the uneven batch timed after the main workload (0: skip)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -256,10 +318,12 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    X = wl.make_c2(seed=rank).astype(np.float32 if args.precision == "fp32" else np.float64)
+    X = wl.make_c3(seed=rank)                       # float32 (n3, n1, n2), 2.1 GB
     Xd = torch.from_numpy(X).to(dev)
-    plan = api.RbkPlan(d["n1"], d["n2"], d["n3"], d["R"], d["P"], d["q"], seed=0, precision=args.precision,
-                       device=dev)
+    if args.precision == "fp64":
+        Xd = Xd.double()
+    n1, n2, n3, R, P, q = (d[k] for k in ("n1", "n2", "n3", "R", "P", "q"))
+    plan = api.RbkPlan(n1, n2, n3, R, P, q, seed=0, precision=args.precision, device=dev)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
     stream = torch.cuda.current_stream(dev)
 
@@ -286,9 +350,11 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = max_over_ranks(sum(step_ms) / 1000.0, dev)
     value = job_value(args.steps, world, total_s)
+    ms_step = 1000 * total_s / args.steps
 
     # end to end through the public API: pinned host input -> device -> T-SVD -> host outputs
-    Xh = torch.from_numpy(X).pin_memory()
+    Xh = torch.from_numpy(X).pin_memory() if args.precision != "fp64" else torch.from_numpy(
+        X.astype(np.float64)).pin_memory()
     outs_h = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (plan.U, plan.S, plan.V, plan.sig)]
     Xe = torch.empty_like(Xd)
     h2d = Xh.numel() * Xh.element_size()
@@ -306,36 +372,39 @@ def main():
     barrier()
     e2e_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev) / 1000.0, dev)
     e2e_value = job_value(args.steps, world, e2e_s)
+    del Xe, Xh
 
     # per-stage times (CUDA events recorded by the library on this stream)
     with api.profile() as pr:
-        for _ in range(3):
+        for _ in range(2):
             flush.zero_()
             plan(Xd)
-    stages = {k: v[0] / 3 for k, v in pr.stages.items()}
-    launches = {k: v[1] // 3 for k, v in pr.stages.items()}
+    stages = {k: v[0] / 2 for k, v in pr.stages.items()}
     dom = max(stages, key=stages.get)
-    pk = peaks()
+    pk = peaks_file()
+    props = torch.cuda.get_device_properties(dev)
+    alu = measure_alu_peaks(torch, dev, stream)
 
     def roofline_of(stage):
         work = algorithmic(stage, d, args.precision)
         t = stages[stage] * 1e-3
         if "flops" in work:
-            if args.precision == "fp64":
-                peak, src = FP64_PEAK_TFLOPS, "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz"
+            fp64_stage = args.precision == "fp64" or (stage == "eig_hetrd" and d["m"] > 320)
+            if fp64_stage:
+                peak, src = alu["fp64"], "measured here: cuBLAS FP64 GEMM"
             elif stage == "eig_hetrd":
-                peak, src = DF_PEAK_TFLOPS, "derived: FP32 issue rate / 15 instructions per double-float FMA"
-            elif stage == "gram_c":
-                peak, src = 2 * FP32_ISSUE_TINST, "derived: one 32x32->64-bit multiply-add per lane and clock"
+                peak, src = alu["double_float"], "measured FP32 GEMM rate / 15 instructions per double-float FMA x 2"
+            elif stage == "krylov_gemm_tc":
+                peak, src = alu["tf32"], "measured here: cuBLAS TF32 GEMM"
             else:
-                peak, src = 2 * FP32_ISSUE_TINST, "derived: 152 SMs x 128 FP32 FMA/clk x 2.07 GHz"
+                peak, src = alu["fp32"], "measured here: cuBLAS FP32 GEMM (no TF32)"
             a = work["flops"] / t / 1e12
             return {"kernel": stage, "bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s",
-                    "frac": a / peak, "traffic": NCU_TRAFFIC.get(stage), "peak_source": src}
+                    "frac": a / peak, "traffic": ncu_traffic(stage), "peak_source": src}
         if "bytes" in work:
             a = work["bytes"] / t / 1e9
             return {"kernel": stage, "bound": "hbm", "achieved": a, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": a / pk["hbm_gbs"], "traffic": NCU_TRAFFIC.get(stage),
+                    "frac": a / pk["hbm_gbs"], "traffic": ncu_traffic(stage),
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
         return None
 
@@ -344,102 +413,103 @@ def main():
     roof["stages"] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in r.items()
                           if kk in ("bound", "achieved", "peak", "unit", "frac")}
                       for k in stages for r in [roofline_of(k)] if r}
+    roof["measured_peaks_tflops"] = {k: round(v, 2) for k, v in alu.items()}
+    roof["sms"] = props.multi_processor_count
 
-    # reconstruction error of this path and of the FP64 path on the same tensor ("equal error")
-    def rel_err(U, S, V, Xref):
-        Sf = torch.zeros((d["n3"], d["R"], d["R"]), dtype=torch.float64, device=dev)
-        Sf.diagonal(dim1=1, dim2=2).copy_(S.double())
-        VT = torch.zeros((d["n3"], d["R"], d["n2"]), dtype=torch.float64, device=dev)
-        VT[0] = V[0].double().T
-        VT[1:] = V.double().flip(0)[:-1].transpose(1, 2)      # tensor transpose (Sec. 2)
-        Xr = api.tprod(api.tprod(U.double(), Sf, "fp64"), VT, "fp64")
-        return float(torch.linalg.vector_norm(Xref - Xr) / torch.linalg.vector_norm(Xref))
+    # reconstruction errors: this path, the other mixed path, the configuration's
+    # FP64 orthonormalisation, and the FP64 path on the same (FP32-rounded) tensor
+    X64 = Xd.double() if Xd.dtype != torch.float64 else Xd
+    xnorm2 = float(torch.linalg.vector_norm(X64) ** 2)
 
-    X64 = Xd.double()
-    err_path = rel_err(plan.U, plan.S, plan.V, X64)
-    plan64 = api.RbkPlan(d["n1"], d["n2"], d["n3"], d["R"], d["P"], d["q"], seed=0, precision="fp64", device=dev)
-    plan64(X64)
-    torch.cuda.synchronize(dev)
-    ev64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
-    for a, b in ev64:
-        flush.zero_()
-        a.record(stream)
-        plan64(X64)
-        b.record(stream)
-    torch.cuda.synchronize(dev)
-    fp64_ms = sum(a.elapsed_time(b) for a, b in ev64) / len(ev64)
-    err_fp64 = rel_err(plan64.U, plan64.S, plan64.V, X64)
-    opt = float(np.sqrt(wl.optimal_error2(wl.c2_sigma(d["n1"]), d["R"])) / torch.linalg.vector_norm(X64).item())
+    def rel_err(pl):
+        e2 = api.tsvd_error(X64, pl.U.double(), pl.S.double(), pl.V.double(), "fp64").item()
+        return math.sqrt(max(e2, 0.0) / xnorm2)
 
-    # mixed paths (basis-building products on tcgen05, TF32 / BF16, the rest as on the FP32 path)
-    # and Alg. 1 of the paper on the FP32 path
-    mixed = {}
-    if args.precision == "fp32":
-        for prec in ("tf32", "bf16", "alg1"):
-            # "alg1": Alg. 1 of the paper (power iteration) on the FP32 path, same Omega
-            pl = api.RbkPlan(d["n1"], d["n2"], d["n3"], d["R"], d["P"], d["q"], seed=0,
-                             precision="fp32" if prec == "alg1" else prec, device=dev, alg1=prec == "alg1")
-            pl(Xd)
-            torch.cuda.synchronize(dev)
-            evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
-            for a, b in evm:
-                flush.zero_()
-                a.record(stream)
-                pl(Xd)
-                b.record(stream)
-            torch.cuda.synchronize(dev)
-            ms_m = sum(a.elapsed_time(b) for a, b in evm) / len(evm)
-            mixed[prec] = {"ms_per_tsvd": ms_m, "tsvd_per_s": 1000.0 / ms_m,
-                           "rel_error": rel_err(pl.U, pl.S, pl.V, X64)}
-            del pl
+    err_this = rel_err(plan)
+    paths = {"this": {"precision": args.precision, "ms_per_tsvd": ms_step, "rel_error": err_this}}
+    del plan
+    torch.cuda.empty_cache()
+
+    def time_path(tag, precision, k, xin, **kw):
+        pl = api.RbkPlan(n1, n2, n3, R, P, q, seed=0, precision=precision, device=dev, **kw)
+        pl(xin)
+        torch.cuda.synchronize(dev)
+        ms = timed_calls(torch, lambda: pl(xin), k, flush, stream, dev)
+        paths[tag] = {"ms_per_tsvd": ms, "tsvd_per_s": 1000.0 / ms, "rel_error": rel_err(pl)}
+        del pl
+        torch.cuda.empty_cache()
+
+    X32 = Xd if Xd.dtype == torch.float32 else Xd.float()
+    for prec in ("tf32", "bf16", "fp32"):
+        if prec != args.precision:
+            time_path(prec, prec, 3, X32)
+    time_path(args.precision + "+fp64_qr" if args.precision != "fp64" else "tf32+fp64_qr",
+              args.precision if args.precision != "fp64" else "tf32", 2, X32, fp64_qr=True)
+    time_path("alg1_" + ("tf32" if args.precision == "fp64" else args.precision),
+              "tf32" if args.precision == "fp64" else args.precision, 3, X32, alg1=True)
+    if args.precision != "fp64":
+        time_path("fp64", "fp64", 2, X64)
+        e64 = paths["fp64"]["rel_error"]
+        paths["speedup_vs_fp64"] = paths["fp64"]["ms_per_tsvd"] / ms_step
+        paths["error_rel_diff_vs_fp64"] = abs(err_this - e64) / e64
+        paths["equal_error"] = abs(err_this - e64) / e64 <= 1e-3
+    del X64
+
+    # the image-like 512 x 512 x 64 configuration (FP32 and FP64 paths) with its Eckart-Young optimum
+    Xc2 = torch.from_numpy(wl.make_c2(0).astype(np.float32)).to(dev)
+    c2 = {}
+    for prec in ("fp32", "fp64"):
+        xin = Xc2 if prec == "fp32" else Xc2.double()
+        pl = api.RbkPlan(512, 512, 64, 50, 10, 4, seed=0, precision=prec, device=dev)
+        pl(xin)
+        torch.cuda.synchronize(dev)
+        ms = timed_calls(torch, lambda: pl(xin), 5 if prec == "fp32" else 2, flush, stream, dev)
+        e2 = api.tsvd_error(Xc2.double(), pl.U.double(), pl.S.double(), pl.V.double(), "fp64").item()
+        c2[prec] = {"ms_per_tsvd": ms, "rel_error": math.sqrt(e2) / float(torch.linalg.vector_norm(Xc2.double()))}
+        del pl
+    c2["eckart_young_optimum_rel_error"] = float(np.sqrt(wl.optimal_error2(wl.c2_sigma(512), 50)) /
+                                                 torch.linalg.vector_norm(Xc2.double()).item())
+    c2["workload"] = C2["name"]
+    paths["c2"] = c2
+    del Xc2
 
     # t-product throughput on the paper-shaped products (flops 8 n1 n2 n4 h, whole call incl. FFTs)
     tprod_tflops = {}
-    for name, n1, n2, n4, n3 in (("2048x2048x128*2048x120x128", 2048, 2048, 120, 128),
+    for name, a1, a2, a4, a3 in (("2048x2048x128*2048x120x128", 2048, 2048, 120, 128),
                                  ("1024x1024x64*1024x1024x64", 1024, 1024, 1024, 64),
                                  ("256x20x100*20x256x100", 256, 20, 256, 100)):
-        fl = 8.0 * n1 * n2 * n4 * (n3 // 2 + 1)
+        fl = 8.0 * a1 * a2 * a4 * (a3 // 2 + 1)
         row = {}
         for prec in ("fp64", "fp32", "tf32", "bf16"):
             dt = torch.float64 if prec == "fp64" else torch.float32
-            A = torch.randn(n3, n1, n2, device=dev, dtype=dt)
-            B = torch.randn(n3, n2, n4, device=dev, dtype=dt)
+            A = torch.randn(a3, a1, a2, device=dev, dtype=dt)
+            B = torch.randn(a3, a2, a4, device=dev, dtype=dt)
             api.tprod(A, B, prec)
             ts = []
             for _ in range(3):
-                flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                api.tprod(A, B, prec)
-                b.record(stream)
-                torch.cuda.synchronize(dev)
-                ts.append(a.elapsed_time(b))
+                ts.append(timed_calls(torch, lambda: api.tprod(A, B, prec), 1, flush, stream, dev))
             row[prec] = round(fl / (min(ts) * 1e-3) / 1e12, 3)
             del A, B
         tprod_tflops[name] = row
 
     batched = None
-    if args.batched_count > 0 and args.precision == "fp32":
+    if args.batched_count > 0 and args.precision != "fp64":
         batched = batched_bench(api, wl, dev, args.batched_count, 8, 3, flush, stream)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "T-SVD/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64+f64" if args.precision == "fp32" else "f64",
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32(tcgen05 %s)+i64+f64" % args.precision,
                 "data": "synthetic",
                 "config": {"workload": d["name"], "precision": args.precision, "m_eff": d["m"],
-                           "l2": "flushed between steps (256 MB write)", "parallelism": "dp%d" % world},
+                           "l2": "inputs larger than L2 (2.1 GB); L2 also flushed between steps (256 MB write)",
+                           "parallelism": "dp%d" % world},
                 "e2e": {"value": e2e_value, "unit": "T-SVD/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches_timed, "roofline": roof, "clocks": clk.summary(),
-                "paths": {"this": {"precision": args.precision, "ms_per_tsvd": 1000 * total_s / args.steps,
-                                   "rel_error": err_path},
-                          "fp64": {"ms_per_tsvd": fp64_ms, "tsvd_per_s": 1000.0 / fp64_ms, "rel_error": err_fp64},
-                          **mixed,
-                          "speedup_vs_fp64": fp64_ms / (1000 * total_s / args.steps),
-                          "eckart_young_optimum_rel_error": opt},
-                "tprod_tflops": tprod_tflops, "batched": batched}
+                "paths": paths, "tprod_tflops": tprod_tflops, "batched": batched}
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(X, d)
+            line["cpu_baseline"] = cpu_baseline(X.astype(np.float64), d)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
