@@ -45,6 +45,7 @@ extern "C" {
 #define TSVD_ERR_CUDA (-3)          /* a CUDA launch or API call failed */
 #define TSVD_ERR_UNSUPPORTED (-4)   /* size beyond a documented kernel limit */
 #define TSVD_ERR_NOT_CONVERGED (-5) /* device side: an eigen solve did not converge */
+#define TSVD_ERR_RANK_DEFICIENT (-6) /* device side: a Fourier slice of a pseudoinverse input lacks full rank */
 
 /* ---- precision of the streaming contractions (FFT, Krylov, projection GEMMs) ---- */
 typedef enum {
@@ -78,6 +79,17 @@ typedef struct {
    x = hi + lo with hi the nearest TF32, products hi*hi + hi*lo + lo*hi in FP32, about 22
    significant bits) */
 #define TSVD_FLAG_SIMT 4
+/* bit 3 (TSVD_FLAG_QTRUNC): Alg. 2 with the basis Q truncated to its leading R+P columns
+   before the projection C = Q^T * X (the variant Sec. 5, Ex. 1 reports timings for); the
+   Krylov steps still run in full.  m_eff then reports R+P. */
+#define TSVD_FLAG_QTRUNC 8
+/* bit 4 (TSVD_FLAG_DEFLATE, FP64 path only): deflated Rayleigh-Ritz passes in the small SVD.
+   The Gram C C^H resolves singular values only down to ~1e-8 sigma_1; with this flag each
+   pass keeps the eigenpairs with lambda >= 1e-6 lambda_max, projects them out of C and
+   solves the rest again (six passes), so singular values down to the FP64 floor of C
+   (absolute ~eps sigma_1) are returned, e.g. for the fast-decaying spectra of Sec. 5, Ex. 1.
+   Other precisions return TSVD_ERR_UNSUPPORTED. */
+#define TSVD_FLAG_DEFLATE 16
 
 /* ---- device-side outcome, read back only when requested ---- */
 typedef struct {
@@ -176,7 +188,8 @@ TSVD_API int tprod(const void* A, const void* B, void* C, int n1, int n2, int n4
 
 /*
  * tproj -- projection Y = Q * Q^T * A onto the range of Q (the projector of
- * Lemma mn38), per Fourier slice Y_k = Q_k (Q_k^H A_k).
+ * the Sec. 4 lemma A - U_k * U_k^T * A = A - Q * (Q^T * A)_k), per Fourier
+ * slice Y_k = Q_k (Q_k^H A_k).
  *   Q device (n3, n1, m), A device (n3, n1, n2), Y device out (n3, n1, n2).
  */
 TSVD_API int tproj_workspace_size(int n1, int m, int n2, int n3, int precision, size_t* bytes);
@@ -196,7 +209,8 @@ TSVD_API int tprod_backward(const void* A, const void* B, const void* dC, void* 
 
 /*
  * tproj_backward -- adjoint of the projection Y = Q * Q^T * A (the projector
- * of Lemma mn38): dA = Q * (Q^T * dY) and dQ = dY * (A^T * Q) + A * (dY^T * Q).
+ * of the Sec. 4 lemma): dA = Q * (Q^T * dY) and
+ * dQ = dY * (A^T * Q) + A * (dY^T * Q).
  *   Q (n3,n1,m), A (n3,n1,n2), dY (n3,n1,n2); dQ (n3,n1,m), dA (n3,n1,n2).
  *   Either output may be NULL.
  */
@@ -242,6 +256,38 @@ TSVD_API int tsvd_error(const void* X, const void* U, const void* S, const void*
                         int precision, double* err2, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * tqr -- T-QR decomposition X = Q * R (Alg. TQR, Sec. 2): per non-redundant
+ * Fourier slice the economy QR of X_k with p = min(n1, n2), the other slices
+ * by conjugate symmetry, and the inverse transform of both factors.  The QR of
+ * a slice is unique up to unit phases on the diagonal of R; this library
+ * returns the factors whose Fourier slices have diag(R_k) real and >= 0.  A
+ * slice wider than tall is factored on its first n1 columns (R = Q^H X).
+ *   A device (n3, n1, n2) real; Q device out (n3, n1, p); R device out
+ *   (n3, p, n2); precision TSVD_FP64 (double) or TSVD_FP32 (float).
+ *   Workspace from tqr_workspace_size, 256-byte aligned.  Numerically
+ *   dependent columns are replaced by orthonormal directions (Q keeps
+ *   orthonormal columns; R has ~0 on those diagonal entries); their number is
+ *   returned in info->dead_columns when info is non-NULL (synchronises).
+ */
+TSVD_API int tqr_workspace_size(int n1, int n2, int n3, int precision, size_t* bytes);
+TSVD_API int tqr(const void* A, int n1, int n2, int n3, int precision, void* Q, void* R, void* ws, size_t ws_bytes,
+                 void* stream, tsvd_info* info);
+
+/*
+ * tpinv -- Moore-Penrose pseudoinverse X^+ (Alg. mp, Sec. 2): per Fourier
+ * slice pinv(X_k), computed as R_k^{-1} Q_k^H from the QR of X_k (n1 >= n2) or
+ * of X_k^H (n1 < n2, pinv(X) = pinv(X^H)^H), then the inverse transform.  It
+ * equals the pseudoinverse when every Fourier slice has full rank
+ * min(n1, n2); a rank-deficient slice sets info->status to
+ * TSVD_ERR_RANK_DEFICIENT (info non-NULL: the call synchronises) and the
+ * output is then not the pseudoinverse.
+ *   A device (n3, n1, n2) real; X device out (n3, n2, n1); precision FP64 / FP32.
+ */
+TSVD_API int tpinv_workspace_size(int n1, int n2, int n3, int precision, size_t* bytes);
+TSVD_API int tpinv(const void* A, int n1, int n2, int n3, int precision, void* X, void* ws, size_t ws_bytes,
+                   void* stream, tsvd_info* info);
+
+/*
  * tprod_noalloc -- the t-product C = A * B of tprod(), for callers that cannot
  * allocate device memory (an arena or pool that must not grow, a plug-in whose
  * host process owns every device allocation, a real-time loop where an
@@ -255,9 +301,15 @@ TSVD_API int tsvd_error(const void* X, const void* U, const void* S, const void*
  * n1*n4) complex elements (8 bytes each in FP32, 16 in FP64, each array rounded
  * up to 256 bytes), must fit in 16 MiB; larger problems return
  * TSVD_ERR_UNSUPPORTED and launch nothing.
- * All calls share the array: calls whose kernels overlap on the GPU race.  The
- * first call on each device looks up the array's device address, so make it
- * before capturing a CUDA graph.
+ * All calls share the array: calls whose kernels overlap on the GPU race.
+ * The array sits in a module of the library that holds no kernel; with CUDA's
+ * lazy module loading (the default) that module, and its 16 MiB, is loaded on
+ * a device by the first call there, so make that first call before sealing a
+ * pool that must not grow and before capturing a CUDA graph.  Every call
+ * outside a capture looks the array's address up again (nothing is allocated
+ * by that once the module is loaded), so a device reset is followed; inside a
+ * capture the address from the last uncaptured call on the device is used
+ * (TSVD_ERR_CUDA if there was none).
  */
 TSVD_API int tprod_noalloc(const void* A, const void* B, void* C, int n1, int n2, int n4, int n3, int precision,
                            void* stream);

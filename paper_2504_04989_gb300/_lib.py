@@ -14,10 +14,13 @@ TSVD_FP64, TSVD_FP32, TSVD_MIXED_TF32, TSVD_MIXED_BF16 = 0, 1, 2, 3
 TSVD_FLAG_FP64_QR = 1
 TSVD_FLAG_ALG1 = 2
 TSVD_FLAG_SIMT = 4
+TSVD_FLAG_QTRUNC = 8
+TSVD_FLAG_DEFLATE = 16
 PRECISIONS = {"fp64": TSVD_FP64, "fp32": TSVD_FP32, "tf32": TSVD_MIXED_TF32, "bf16": TSVD_MIXED_BF16}
 
 ERRORS = {0: "ok", -1: "invalid argument", -2: "workspace too small", -3: "CUDA failure",
-          -4: "unsupported size or mode", -5: "eigen solve did not converge"}
+          -4: "unsupported size or mode", -5: "eigen solve did not converge",
+          -6: "rank-deficient Fourier slice"}
 
 
 class TsvdParams(C.Structure):
@@ -60,6 +63,10 @@ SIGNATURES = {
     "tsvd_error_workspace_size": (_i, [_i, _i, _i, _i, _i, C.POINTER(C.c_size_t)]),
     "tsvd_error": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, C.c_size_t, _vp]),
     "tprod_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp]),
+    "tqr_workspace_size": (_i, [_i, _i, _i, _i, C.POINTER(_sz)]),
+    "tqr": (_i, [_vp, _i, _i, _i, _i, _vp, _vp, _vp, _sz, _vp, C.POINTER(TsvdInfo)]),
+    "tpinv_workspace_size": (_i, [_i, _i, _i, _i, C.POINTER(_sz)]),
+    "tpinv": (_i, [_vp, _i, _i, _i, _i, _vp, _vp, _sz, _vp, C.POINTER(TsvdInfo)]),
     "tsvd_gaussian": (_i, [_u64, _u32, _u32, _l, _vp, _vp]),
     "tsvd_philox_words": (_i, [C.POINTER(_u32), _u32, _u32, _u32, _l, _vp, _vp]),
     "tsvd_profile_begin": (_i, []),

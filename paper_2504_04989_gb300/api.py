@@ -43,7 +43,13 @@ def _workspace(nbytes, device):
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
-def rbk(A, R, P=10, q=2, seed=0, precision="fp32", omega=None, return_info=False, fp64_qr=False, alg1=False):
+def _flags(fp64_qr, alg1, q_trunc, deflate=False):
+    return ((_lib.TSVD_FLAG_FP64_QR if fp64_qr else 0) | (_lib.TSVD_FLAG_ALG1 if alg1 else 0) |
+            (_lib.TSVD_FLAG_QTRUNC if q_trunc else 0) | (_lib.TSVD_FLAG_DEFLATE if deflate else 0))
+
+
+def rbk(A, R, P=10, q=2, seed=0, precision="fp32", omega=None, return_info=False, fp64_qr=False, alg1=False,
+        q_trunc=False, deflate=False):
     """Randomized block Krylov truncated T-SVD (Alg. 2): A ~ U * S * V^T.
 
     A: (n3, n1, n2) CUDA tensor.  Returns U (n3, n1, R), S (n3, R) singular
@@ -51,7 +57,10 @@ def rbk(A, R, P=10, q=2, seed=0, precision="fp32", omega=None, return_info=False
     singular values (descending per slice).  omega (n3, n2, R + P) replaces the
     Philox-drawn test tensor when given.  fp64_qr=True orthonormalises the
     Krylov blocks in FP64 on the FP32 path as well; alg1=True runs Alg. 1
-    (power iteration, basis of R+P columns) instead of Alg. 2.
+    (power iteration, basis of R+P columns) instead of Alg. 2; q_trunc=True
+    projects on the leading R+P basis columns only (Ex. 1's truncated Q);
+    deflate=True (FP64 only) resolves singular values below ~1e-8 sigma_1 by
+    deflated Rayleigh-Ritz passes in the small SVD.
     """
     lib = _lib.load()
     pr = _prec(precision)
@@ -59,7 +68,7 @@ def rbk(A, R, P=10, q=2, seed=0, precision="fp32", omega=None, return_info=False
     A = A.contiguous()
     _need_cuda(A, omega, dtype=dt)
     n3, n1, n2 = A.shape
-    flags = (_lib.TSVD_FLAG_FP64_QR if fp64_qr else 0) | (_lib.TSVD_FLAG_ALG1 if alg1 else 0)
+    flags = _flags(fp64_qr, alg1, q_trunc, deflate)
     p = _lib.TsvdParams(R=int(R), P=int(P), q=int(q), precision=pr, seed=int(seed), flags=flags)
     nbytes = C.c_size_t()
     _lib.check(lib.tsvd_rbk_workspace_size(n1, n2, n3, C.byref(p), C.byref(nbytes)), "tsvd_rbk_workspace_size")
@@ -89,10 +98,10 @@ class RbkPlan:
     (no allocation per call, so a loop of calls can be captured in a CUDA graph)."""
 
     def __init__(self, n1, n2, n3, R, P=10, q=2, seed=0, precision="fp32", device="cuda", fp64_qr=False,
-                 alg1=False):
+                 alg1=False, q_trunc=False, deflate=False):
         self.lib = _lib.load()
         self.dt = _DT[precision]
-        flags = (_lib.TSVD_FLAG_FP64_QR if fp64_qr else 0) | (_lib.TSVD_FLAG_ALG1 if alg1 else 0)
+        flags = _flags(fp64_qr, alg1, q_trunc, deflate)
         self.p = _lib.TsvdParams(R=int(R), P=int(P), q=int(q), precision=_prec(precision), seed=int(seed),
                                  flags=flags)
         self.shape = (n1, n2, n3)
@@ -308,7 +317,7 @@ def tprod(A, B, precision=None):
 
 
 def tproj(Q, A, precision=None):
-    """Projection Y = Q * Q^T * A (Lemma mn38); differentiable."""
+    """Projection Y = Q * Q^T * A (Sec. 4: the Alg. 2 output lies in the projection Q*Q^T*A); differentiable."""
     return TProj.apply(Q, A, _precision_of(Q, precision))
 
 
@@ -404,3 +413,51 @@ def masked_residual(C, X, mask, out=None, loss=None, partial=None):
         _lib.check(lib.tsvd_masked_residual(_ptr(C), _ptr(X), _ptr(mask), _ptr(R), _ptr(loss), _ptr(partial),
                                             C.numel(), _prec(precision), _stream(C.device)), "masked_residual")
     return R, loss
+
+
+def tqr(A, precision=None, return_info=False):
+    """T-QR decomposition A = Q * R (Alg. TQR): A (n3, n1, n2) CUDA tensor;
+    returns Q (n3, n1, p) and R (n3, p, n2), p = min(n1, n2), whose Fourier
+    slices have diag(R_k) real and >= 0."""
+    lib = _lib.load()
+    precision = _precision_of(A, precision)
+    pr = _prec(precision)
+    A = A.contiguous()
+    _need_cuda(A, dtype=_DT[precision])
+    n3, n1, n2 = A.shape
+    p = min(n1, n2)
+    nbytes = C.c_size_t()
+    _lib.check(lib.tqr_workspace_size(n1, n2, n3, pr, C.byref(nbytes)), "tqr_workspace_size")
+    ws = _workspace(nbytes.value, A.device)
+    Q = torch.empty((n3, n1, p), dtype=A.dtype, device=A.device)
+    R = torch.empty((n3, p, n2), dtype=A.dtype, device=A.device)
+    info = _lib.TsvdInfo()
+    with torch.cuda.device(A.device):
+        _lib.check(lib.tqr(_ptr(A), n1, n2, n3, pr, _ptr(Q), _ptr(R), _ptr(ws), nbytes.value, _stream(A.device),
+                           C.byref(info) if return_info else None), "tqr")
+    if return_info:
+        return Q, R, {"status": info.status, "dead_columns": info.dead_columns}
+    return Q, R
+
+
+def tpinv(A, precision=None, return_info=False):
+    """Moore-Penrose pseudoinverse (Alg. mp): A (n3, n1, n2) -> (n3, n2, n1).
+    Every Fourier slice must have full rank min(n1, n2) (status
+    TSVD_ERR_RANK_DEFICIENT in the info otherwise)."""
+    lib = _lib.load()
+    precision = _precision_of(A, precision)
+    pr = _prec(precision)
+    A = A.contiguous()
+    _need_cuda(A, dtype=_DT[precision])
+    n3, n1, n2 = A.shape
+    nbytes = C.c_size_t()
+    _lib.check(lib.tpinv_workspace_size(n1, n2, n3, pr, C.byref(nbytes)), "tpinv_workspace_size")
+    ws = _workspace(nbytes.value, A.device)
+    X = torch.empty((n3, n2, n1), dtype=A.dtype, device=A.device)
+    info = _lib.TsvdInfo()
+    with torch.cuda.device(A.device):
+        _lib.check(lib.tpinv(_ptr(A), n1, n2, n3, pr, _ptr(X), _ptr(ws), nbytes.value, _stream(A.device),
+                             C.byref(info) if return_info else None), "tpinv")
+    if return_info:
+        return X, {"status": info.status, "dead_columns": info.dead_columns}
+    return X

@@ -360,12 +360,12 @@ template int rmul_block<float2>(const float2*, long, long, const float2*, long, 
 // Dependent Krylov columns (exact low rank, zero data): replace column c+j by
 // a Philox Gaussian direction (stream 3) projected twice against every other
 // live column of the basis, then normalised.  Any orthonormal completion of
-// span(K) leaves the Rayleigh-Ritz result of Alg. 2 optimal (eq. mn39).
+// span(K) leaves the Rayleigh-Ritz result of Alg. 2 optimal (Sec. 4: Q (Q^T A)_k is the best rank-k approximation within range(Q)).
 // ---------------------------------------------------------------------------
 template <typename C>
 __global__ void __launch_bounds__(256) k_repair_dead(C* __restrict__ Q, long ldq, long sQ, int n1, int c, int nb,
                                                      const uint32_t* __restrict__ dead, uint64_t seed, int block_id,
-                                                     int* __restrict__ dead_count) {
+                                                     int* __restrict__ dead_count, int last_real) {
   using R = decltype(C().x);
   __shared__ double red[32];
   const int b = blockIdx.x, tid = threadIdx.x;
@@ -378,6 +378,7 @@ __global__ void __launch_bounds__(256) k_repair_dead(C* __restrict__ Q, long ldq
   }
   if (ndead == 0) return;
   Q += (long)b * sQ;
+  const bool real_slice = (b == 0) || (last_real && b == (int)gridDim.x - 1);
   if (tid == 0) atomicAdd(dead_count, ndead);
   uint32_t pending[4] = {dm[0], dm[1], dm[2], dm[3]};
   for (int j = 0; j < nb; ++j) {
@@ -393,9 +394,11 @@ __global__ void __launch_bounds__(256) k_repair_dead(C* __restrict__ Q, long ldq
         const double r = sqrt(-2.0 * log(u1));
         double sn, cs;
         sincospi(2.0 * u2, &sn, &cs);
+        // the DC slice (and the Nyquist slice of an even-length transform) of a real
+        // tensor's spectrum is real: its replacement directions are real too
         C v;
         v.x = (R)(r * cs);
-        v.y = (R)(r * sn);
+        v.y = real_slice ? (R)0 : (R)(r * sn);
         Q[(long)i * ldq + col] = v;
       }
       __syncthreads();
@@ -433,15 +436,73 @@ __global__ void __launch_bounds__(256) k_repair_dead(C* __restrict__ Q, long ldq
 
 template <typename C>
 int repair_dead(C* Q, long ldq, long sQ, int n1, int c, int nb, const uint32_t* dead, int batch, uint64_t seed,
-                int block_id, int* dead_count, cudaStream_t s) {
+                int block_id, int* dead_count, int last_real, cudaStream_t s) {
   if (nb <= 0 || batch <= 0) return TSVD_OK;
-  k_repair_dead<C><<<batch, 256, 0, s>>>(Q, ldq, sQ, n1, c, nb, dead, seed, block_id, dead_count);
+  k_repair_dead<C><<<batch, 256, 0, s>>>(Q, ldq, sQ, n1, c, nb, dead, seed, block_id, dead_count, last_real);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }
 template int repair_dead<double2>(double2*, long, long, int, int, int, const uint32_t*, int, uint64_t, int, int*,
-                                  cudaStream_t);
-template int repair_dead<float2>(float2*, long, long, int, int, int, const uint32_t*, int, uint64_t, int, int*,
+                                  int, cudaStream_t);
+template int repair_dead<float2>(float2*, long, long, int, int, int, const uint32_t*, int, uint64_t, int, int*, int,
                                  cudaStream_t);
+
+// Orthonormalise the nb leading columns of W (n1 x b per slice) against the c
+// finished columns of Q and write them to Q columns [c, c+nb), in the
+// precision L: shifted CholeskyQR3 (the shift makes the first Cholesky
+// succeed for any W; the next two passes restore orthogonality to rounding
+// level), each pass preceded by a classical Gram-Schmidt projection against
+// Q_{<i}; dependent columns are then replaced.
+template <typename L>
+int orth_block_cols(int n1, int b, int m, int h, const OrthWs& w, int c, int nb, int block_id, uint64_t seed,
+                    cudaStream_t s) {
+  using CL = cx_t<L>;
+  const long sQ = (long)n1 * m, sW = (long)n1 * b, sP = (long)m * b, sG = (long)b * b;
+  CL* Q = (CL*)w.Q;
+  CL* W = (CL*)w.W;
+  CL* P = (CL*)w.P;
+  CL* Gs = (CL*)w.G;
+  const size_t sk = std::is_same<L, double>::value ? w.splitk_elems : 2 * w.splitk_elems;
+  // FP64: Fukaya et al.'s shift 11 (n nb + nb (nb+1)) u ||W||^2 (trace as the norm
+  // bound); FP32: 1e-5 trace(G), above the FP32 Gram error ~ sqrt(n) u ||W||^2
+  const double shift = std::is_same<L, double>::value
+                           ? 11.0 * ((double)n1 * nb + (double)nb * (nb + 1)) * 1.1102230246251565e-16
+                           : 1e-5;
+  const double dead_rel = std::is_same<L, double>::value ? 1e-12 : 1e-7;
+  for (int pass = 0; pass < 3; ++pass) {
+    if (c > 0) {
+      TSVD_STAGE("orth_cgs", s);
+      TSVD_TRY(cgemm<CL>(gemm('H', 'N', c, nb, n1, 1.0, Q, m, sQ, W, b, sW, 0.0, P, nb, sP, h), w.splitk, sk, s));
+      TSVD_TRY(cgemm<CL>(gemm('N', 'N', n1, nb, c, -1.0, Q, m, sQ, P, nb, sP, 1.0, W, b, sW, h), w.splitk, sk, s));
+    }
+    {
+      TSVD_STAGE("orth_gram", s);
+      TSVD_TRY(cgemm<CL>(gemm('H', 'N', nb, nb, n1, 1.0, W, b, sW, W, b, sW, 0.0, Gs, b, sG, h), w.splitk, sk, s));
+    }
+    CL* Mi = (CL*)w.Minv;  // R-tilde^{-1}, nb x nb per slice (leading dimension b)
+    {
+      TSVD_STAGE("orth_chol", s);
+      TSVD_TRY(chol_inv<CL>(Gs, b, sG, Mi, b, sG, nb, h, pass == 0 ? shift : 0.0, dead_rel, w.dead, s));
+    }
+    {
+      TSVD_STAGE("orth_trsm", s);
+      // the last pass writes the finished block straight into its columns of Q
+      if (pass < 2) TSVD_TRY(rmul_block<CL>(W, b, sW, Mi, b, sG, n1, nb, h, W, b, sW, s));
+      else TSVD_TRY(rmul_block<CL>(W, b, sW, Mi, b, sG, n1, nb, h, Q + c, m, sQ, s));
+    }
+  }
+  {
+    TSVD_STAGE("orth_repair", s);
+    TSVD_TRY(repair_dead<CL>(Q, m, sQ, n1, c, nb, w.dead, h, seed, block_id, w.dead_count, w.last_real, s));
+  }
+  if (w.Qt) {
+    TSVD_STAGE("convert", s);
+    TSVD_TRY(convert_c64_to_c32((const double2*)Q + c, m, sQ, (float2*)w.Qt + c, m, sQ, n1, nb, h, s));
+  }
+  return TSVD_OK;
+}
+
+template int orth_block_cols<double>(int, int, int, int, const OrthWs&, int, int, int, uint64_t, cudaStream_t);
+template int orth_block_cols<float>(int, int, int, int, const OrthWs&, int, int, int, uint64_t, cudaStream_t);
 
 }  // namespace tsvd

@@ -47,6 +47,29 @@ struct GemmArgs {
   long ldc, sC;
   int batch;
 };
+// GemmArgs from its fields (strided batch)
+inline GemmArgs gemm(char opA, char opB, int M, int N, int K, double alpha, const void* A, long lda, long sA,
+                     const void* B, long ldb, long sB, double beta, void* Cm, long ldc, long sC, int batch) {
+  GemmArgs g;
+  g.opA = opA;
+  g.opB = opB;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.alpha = alpha;
+  g.beta = beta;
+  g.A = A;
+  g.lda = lda;
+  g.sA = sA;
+  g.B = B;
+  g.ldb = ldb;
+  g.sB = sB;
+  g.C = Cm;
+  g.ldc = ldc;
+  g.sC = sC;
+  g.batch = batch;
+  return g;
+}
 template <typename C>
 int cgemm(const GemmArgs& g, void* splitk_ws, size_t splitk_elems, cudaStream_t s);
 // C = op(A) op(B) known to be Hermitian (square, beta = 0, e.g. A^H A): only
@@ -82,10 +105,35 @@ template <typename C>
 int rmul_block(const C* W, long ldw, long sW, const C* M, long ldm, long sM, int n1, int nb, int batch, C* O, long ldo,
                long sO, cudaStream_t s);
 // Replace dead columns [c, c+nb) of Q (n1 x ldq per slice) by unit vectors
-// orthogonal to columns [0, c+nb): Philox directions projected twice.
+// orthogonal to columns [0, c+nb): Philox directions projected twice.  Slice 0
+// (and slice batch-1 when last_real is set: the Nyquist slice of an even n3)
+// gets real directions, as the spectrum of a real tensor is real there.
 template <typename C>
 int repair_dead(C* Q, long ldq, long sQ, int n1, int c, int nb, const uint32_t* dead, int batch, uint64_t seed,
-                int block_id, int* dead_count, cudaStream_t s);
+                int block_id, int* dead_count, int last_real, cudaStream_t s);
+// Block orthonormalisation step of a basis Q (n1 x m per slice, leading dim m)
+// in precision L: the nb leading columns of W (n1 x b, leading dim b) are made
+// orthonormal against Q's c finished columns by shifted CholeskyQR3 with a
+// classical Gram-Schmidt projection before each pass, written to Q columns
+// [c, c + nb); dependent columns are replaced (repair_dead, counted in
+// *dead_count).  P (m x b), G and Minv (b x b) are scratch; when Qt is set the
+// block is also converted to FP32 there (L = double with FP32 GEMM data).
+struct OrthWs {
+  void* Q;
+  void* W;
+  void* P;
+  void* G;
+  void* Minv;
+  uint32_t* dead;
+  int* dead_count;
+  void* Qt;
+  void* splitk;
+  size_t splitk_elems;  // in double2 elements
+  int last_real;        // the last slice is the (real) Nyquist slice of an even-length transform
+};
+template <typename L>
+int orth_block_cols(int n1, int b, int m, int h, const OrthWs& w, int c, int nb, int block_id, uint64_t seed,
+                    cudaStream_t s);
 // tc_gemm.cu -- tcgen05 tensor-core GEMM C_b (M x N, FP32) = A_b (M x K) B_b^T
 // with A (M x K) and B (N x K) K-major, TF32 (FP32 storage) or BF16.  Needs
 // 16-byte aligned bases, row strides and batch strides (tc_gemm_supported);
@@ -124,6 +172,13 @@ int sigma_from_lambda(const double* lam, int R, int batch, double* sig, cx_t<T>*
 // columns r of V (rows x R per slice) scaled by 1 / sqrt(lam_r) (zero where lam_r <= 0)
 template <typename T>
 int scale_columns_inv(cx_t<T>* V, long ldv, long sV, int rows, int R, const double* lam, int batch, cudaStream_t s);
+
+// deflate.cu -- one merge step of the deflated Rayleigh-Ritz passes: the
+// pass's eigenpairs with lambda >= 1e-6 lambda_max (all missing ones when
+// `last`) are appended per slice to lamF (batch x R) and UF, Um (batch x mp x
+// R; Um keeps zeros beyond the accepted columns); acc (batch) counts them.
+int deflate_merge(const double* lam_p, const double2* U_p, int mp, int R, int batch, double* lamF, double2* UF,
+                  double2* Um, int* acc, bool first, bool last, cudaStream_t s);
 
 // gram_int.cu -- G = C C^H (Hermitian, FP64 out) from FP32 C^H (n2 x m per
 // slice, leading dimension ldc): per-column power-of-two scaling to integers

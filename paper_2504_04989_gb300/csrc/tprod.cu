@@ -6,7 +6,7 @@
 // Backward: for L = <dC, A*B>, bcirc(X^T) = bcirc(X)^T (Lemma on bcirc) makes
 //           the adjoint the t-product with the transpose, whose Fourier slice
 //           is the conjugate transpose:  dA_k = dC_k B_k^H,  dB_k = A_k^H dC_k.
-// Projection Y = Q*Q^T*A (Lemma mn38): dA_k = Q_k (Q_k^H dY_k),
+// Projection Y = Q*Q^T*A (Sec. 4, the lemma equating the Alg. 2 residual with A - Q (Q^T A)_k): dA_k = Q_k (Q_k^H dY_k),
 //           dQ_k = dY_k (A_k^H Q_k) + A_k (dY_k^H Q_k).
 #include <type_traits>
 

@@ -37,6 +37,8 @@ struct RbkDims {
   int tc;    // basis-building products on tcgen05 in one pass: 0 none, 1 TF32, 2 BF16
   int tc3;   // FP32-accurate products on tcgen05 (split TF32): FP32 data unless TSVD_FLAG_SIMT
   int alg1;  // Alg. 1 (power iteration, last block only) instead of Alg. 2
+  int mp;    // basis columns used by the projection: m, or R+P with TSVD_FLAG_QTRUNC
+  int deflate;  // deflated Rayleigh-Ritz passes for the small SVD (FP64 path)
 };
 
 static int rbk_dims(int n1, int n2, int n3, const tsvd_params* p, RbkDims* d) {
@@ -58,6 +60,9 @@ static int rbk_dims(int n1, int n2, int n3, const tsvd_params* p, RbkDims* d) {
   long m = (long)(d->alg1 ? 1 : p->q + 1) * d->b;
   m = std::min<long>(m, std::min(n1, n2));
   d->m = (int)m;
+  d->mp = (p->flags & TSVD_FLAG_QTRUNC) ? std::min(d->b, d->m) : d->m;
+  d->deflate = (p->flags & TSVD_FLAG_DEFLATE) ? 1 : 0;
+  if (d->deflate && p->precision != TSVD_FP64) return TSVD_ERR_UNSUPPORTED;
   if (d->b > 128 || d->m > 512) return TSVD_ERR_UNSUPPORTED;
   if ((long)d->h * n1 * n2 > (1L << 40)) return TSVD_ERR_UNSUPPORTED;
   return TSVD_OK;
@@ -101,6 +106,13 @@ struct RbkWs {
   int* tc_err;    // set by a tcgen05 pipeline wait that timed out
   double2* splitk;
   size_t splitk_elems;
+  // deflated passes (FP64 path with TSVD_FLAG_DEFLATE)
+  double* lamF;   // accepted eigenvalues (h x R)
+  double2* UF;    // accepted eigenvectors (h x mp x R)
+  double2* Um;    // the same, zero beyond the accepted columns
+  double2* T1;    // C^H Um (h x n2 x R)
+  double2* CpH;   // projected C^H (h x n2 x mp)
+  int* acc;       // accepted count per slice
   size_t bytes;
 };
 
@@ -154,86 +166,40 @@ static RbkWs<T> carve_rbk(void* base, const RbkDims& d) {
   }
   w.splitk_elems = 8 * h * (size_t)d.m * std::max(d.b, 64);
   w.splitk = cv.take<double2>(w.splitk_elems);
+  w.lamF = nullptr;
+  w.UF = w.Um = w.T1 = w.CpH = nullptr;
+  w.acc = nullptr;
+  if (d.deflate) {
+    w.lamF = cv.take<double>(h * d.R);
+    w.UF = cv.take<double2>(h * d.mp * d.R);
+    w.Um = cv.take<double2>(h * d.mp * d.R);
+    w.T1 = cv.take<double2>(h * d.n2 * d.R);
+    w.CpH = cv.take<double2>(h * d.n2 * d.mp);
+    w.acc = cv.take<int>(h);
+  }
   w.bytes = cv.bytes();
   return w;
 }
 
-static GemmArgs gemm(char opA, char opB, int M, int N, int K, double alpha, const void* A, long lda, long sA,
-                     const void* B, long ldb, long sB, double beta, void* Cm, long ldc, long sC, int batch) {
-  GemmArgs g;
-  g.opA = opA;
-  g.opB = opB;
-  g.M = M;
-  g.N = N;
-  g.K = K;
-  g.alpha = alpha;
-  g.beta = beta;
-  g.A = A;
-  g.lda = lda;
-  g.sA = sA;
-  g.B = B;
-  g.ldb = ldb;
-  g.sB = sB;
-  g.C = Cm;
-  g.ldc = ldc;
-  g.sC = sC;
-  g.batch = batch;
-  return g;
-}
 
-// Orthonormalise the nb leading columns of W (n1 x b per slice) against the c
-// finished columns of Q and write them to Q columns [c, c+nb), in the
-// precision L: shifted CholeskyQR3 (the shift makes the first Cholesky
-// succeed for any W; the next two passes restore orthogonality to rounding
-// level), each pass preceded by a classical Gram-Schmidt projection against
-// Q_{<i}; dependent columns are then replaced.
+// Orthonormalise the nb leading columns of the Krylov block W against the c
+// finished columns of Q (orth_block_cols in cholqr.cu: shifted CholeskyQR3
+// with classical Gram-Schmidt, dead columns replaced) in the precision L.
 template <typename T, typename L>
 static int orth_block(const RbkDims& d, RbkWs<T>& w, int c, int nb, int block_id, uint64_t seed, cudaStream_t s) {
-  using CL = cx_t<L>;
-  const int n1 = d.n1, b = d.b, m = d.m, h = d.h;
-  const long sQ = (long)n1 * m, sW = (long)n1 * b, sP = (long)m * b, sG = (long)b * b;
-  CL* Q = (CL*)w.Ql;
-  CL* W = (CL*)w.Wl;
-  CL* P = (CL*)w.Pl;
-  CL* Gs = (CL*)w.Gl;
-  const size_t sk = std::is_same<L, double>::value ? w.splitk_elems : 2 * w.splitk_elems;
-  // FP64: Fukaya et al.'s shift 11 (n nb + nb (nb+1)) u ||W||^2 (trace as the norm
-  // bound); FP32: 1e-5 trace(G), above the FP32 Gram error ~ sqrt(n) u ||W||^2
-  const double shift = std::is_same<L, double>::value
-                           ? 11.0 * ((double)n1 * nb + (double)nb * (nb + 1)) * 1.1102230246251565e-16
-                           : 1e-5;
-  const double dead_rel = std::is_same<L, double>::value ? 1e-12 : 1e-7;
-  for (int pass = 0; pass < 3; ++pass) {
-    if (c > 0) {
-      TSVD_STAGE("orth_cgs", s);
-      TSVD_TRY(cgemm<CL>(gemm('H', 'N', c, nb, n1, 1.0, Q, m, sQ, W, b, sW, 0.0, P, nb, sP, h), w.splitk, sk, s));
-      TSVD_TRY(cgemm<CL>(gemm('N', 'N', n1, nb, c, -1.0, Q, m, sQ, P, nb, sP, 1.0, W, b, sW, h), w.splitk, sk, s));
-    }
-    {
-      TSVD_STAGE("orth_gram", s);
-      TSVD_TRY(cgemm<CL>(gemm('H', 'N', nb, nb, n1, 1.0, W, b, sW, W, b, sW, 0.0, Gs, b, sG, h), w.splitk, sk, s));
-    }
-    CL* Mi = (CL*)w.Rs;  // R-tilde^{-1}, nb x nb per slice (leading dimension b)
-    {
-      TSVD_STAGE("orth_chol", s);
-      TSVD_TRY(chol_inv<CL>(Gs, b, sG, Mi, b, sG, nb, h, pass == 0 ? shift : 0.0, dead_rel, w.dead, s));
-    }
-    {
-      TSVD_STAGE("orth_trsm", s);
-      // the last pass writes the finished block straight into its columns of Q
-      if (pass < 2) TSVD_TRY(rmul_block<CL>(W, b, sW, Mi, b, sG, n1, nb, h, W, b, sW, s));
-      else TSVD_TRY(rmul_block<CL>(W, b, sW, Mi, b, sG, n1, nb, h, Q + c, m, sQ, s));
-    }
-  }
-  {
-    TSVD_STAGE("orth_repair", s);
-    TSVD_TRY(repair_dead<CL>(Q, m, sQ, n1, c, nb, w.dead, h, seed, block_id, w.counters + 1, s));
-  }
-  if (!std::is_same<T, L>::value) {
-    TSVD_STAGE("convert", s);
-    TSVD_TRY(convert_c64_to_c32((const double2*)Q + c, m, sQ, (float2*)w.Qt + c, m, sQ, n1, nb, h, s));
-  }
-  return TSVD_OK;
+  OrthWs o;
+  o.Q = w.Ql;
+  o.W = w.Wl;
+  o.P = w.Pl;
+  o.G = w.Gl;
+  o.Minv = w.Rs;
+  o.dead = w.dead;
+  o.dead_count = w.counters + 1;
+  o.Qt = std::is_same<T, L>::value ? nullptr : (void*)w.Qt;
+  o.splitk = w.splitk;
+  o.splitk_elems = w.splitk_elems;
+  o.last_real = (d.n3 % 2 == 0) && d.h > 1;
+  return orth_block_cols<L>(d.n1, d.b, d.m, d.h, o, c, nb, block_id, seed, s);
 }
 
 // Krylov block from the GEMM precision to the orthonormalisation precision
@@ -290,6 +256,36 @@ static int conj_product(const RbkDims& d, RbkWs<T>& w, int col0, int nb, cudaStr
   return cgemm<cx_t<T>>(gemm('H', 'N', n2, nb, n1, 1.0, w.Ah, n2, sA, w.Qt + col0, m, sQ, 0.0, w.CHt + col0, m, sCH,
                              h),
                         w.splitk, w.splitk_elems * 2, s);
+}
+
+// Deflated Rayleigh-Ritz passes of the small SVD (FP64 path, deflate.cu):
+// pass 0 is the eigen-solve already done; each further pass projects the
+// accepted directions out of C twice, re-forms the Gram and solves it.
+static int deflated_passes(const RbkDims& d, RbkWs<double>& w, cudaStream_t s) {
+  constexpr int kPasses = 6;  // six decades of lambda each: the whole FP64 range
+  const int n2 = d.n2, m = d.m, mp = d.mp, R = d.R, h = d.h;
+  const long sCH = (long)n2 * m, sU = (long)mp * R, sT = (long)n2 * R, sP = (long)n2 * mp;
+  TSVD_STAGE("eig_deflate", s);
+  if (cudaMemsetAsync(w.Um, 0, sizeof(double2) * (size_t)h * sU, s) != cudaSuccess) return TSVD_ERR_CUDA;
+  TSVD_TRY(deflate_merge(w.lam, w.Uct, mp, R, h, w.lamF, w.UF, w.Um, w.acc, true, false, s));
+  for (int pass = 1; pass < kPasses; ++pass) {
+    TSVD_TRY(copy_cx<double2>(w.CH64, m, sCH, w.CpH, mp, sP, n2, mp, h, s));
+    for (int sweep = 0; sweep < 2; ++sweep) {  // C_p^H <- C_p^H - (C_p^H U_m) U_m^H, twice
+      TSVD_TRY(cgemm<double2>(gemm('N', 'N', n2, R, mp, 1.0, w.CpH, mp, sP, w.Um, R, sU, 0.0, w.T1, R, sT, h), w.splitk,
+                              w.splitk_elems, s));
+      TSVD_TRY(cgemm<double2>(gemm('N', 'H', n2, mp, R, -1.0, w.T1, R, sT, w.Um, R, sU, 1.0, w.CpH, mp, sP, h),
+                              w.splitk, w.splitk_elems, s));
+    }
+    TSVD_TRY(cgemm_herm<double2>(gemm('H', 'N', mp, mp, n2, 1.0, w.CpH, mp, sP, w.CpH, mp, sP, 0.0, w.G, mp,
+                                      (long)mp * mp, h),
+                                 w.splitk, w.splitk_elems, s));
+    TSVD_TRY(herm_eig_topR<double2>(w.G, mp, (long)mp * mp, mp, R, h, w.lam, w.Uct, R, sU, w.eig, w.counters, s));
+    TSVD_TRY(deflate_merge(w.lam, w.Uct, mp, R, h, w.lamF, w.UF, w.Um, w.acc, false, pass == kPasses - 1, s));
+  }
+  if (cudaMemcpyAsync(w.lam, w.lamF, sizeof(double) * (size_t)h * R, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(w.Uct, w.UF, sizeof(double2) * (size_t)h * sU, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return TSVD_ERR_CUDA;
+  return TSVD_OK;
 }
 
 template <typename T, typename L>
@@ -363,32 +359,39 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
     c += bi;
     pw = bi;
   }
-  // last block of C^H = A^H Q_last
-  {
+  // last block of C^H = A^H Q_last (not needed when the projection keeps only
+  // the leading R+P basis columns: their block Y_1 of C^H exists already)
+  if (d.mp == m || c == pw) {
   TSVD_STAGE(d.tc3 ? "krylov_gemm_tc" : "krylov_gemm", s);
   TSVD_TRY(conj_product<T>(d, w, c - pw, pw, s));
   }
+  // the projection uses the leading mp columns of Q (Ex. 1's Q truncated to
+  // k + p terms when mp < m) and of C^H, which C^H's leading dimension m keeps
+  const int mp = d.mp;
 
   // G = C C^H in FP64 (FP64 path) or exactly in integers from the FP32 C^H, and its top-R eigenpairs
   {
   TSVD_STAGE("gram_c", s);
   if constexpr (std::is_same<T, double>::value) {
-    TSVD_TRY(cgemm_herm<double2>(gemm('H', 'N', m, m, n2, 1.0, w.CH64, m, sCH, w.CH64, m, sCH, 0.0, w.G, m,
-                                      (long)m * m, h),
+    TSVD_TRY(cgemm_herm<double2>(gemm('H', 'N', mp, mp, n2, 1.0, w.CH64, m, sCH, w.CH64, m, sCH, 0.0, w.G, mp,
+                                      (long)mp * mp, h),
                                  w.splitk, w.splitk_elems, s));
   } else {
-    TSVD_TRY(gram_int_fp32((const float2*)w.CHt, m, sCH, n2, m, h, w.Qint, w.colexp, w.G, m, (long)m * m, s));
+    TSVD_TRY(gram_int_fp32((const float2*)w.CHt, m, sCH, n2, mp, h, w.Qint, w.colexp, w.G, mp, (long)mp * mp, s));
   }
   }
-  TSVD_TRY(herm_eig_topR<C>(w.G, m, (long)m * m, m, R, h, w.lam, w.Uct, R, (long)m * R, w.eig, w.counters, s));
+  TSVD_TRY(herm_eig_topR<C>(w.G, mp, (long)mp * mp, mp, R, h, w.lam, w.Uct, R, (long)mp * R, w.eig, w.counters, s));
+  if constexpr (std::is_same<T, double>::value) {
+    if (d.deflate) TSVD_TRY(deflated_passes(d, w, s));
+  }
   {
   TSVD_STAGE("outputs", s);
   TSVD_TRY(sigma_from_lambda<T>(w.lam, R, h, sig, w.Sh, s, w.counters));
 
   // Uhat = Q U_c,  Vhat = C^H U_c S^{-1}
-  TSVD_TRY(cgemm<C>(gemm('N', 'N', n1, R, m, 1.0, w.Qt, m, sQ, w.Uct, R, (long)m * R, 0.0, w.Uh, R, (long)n1 * R, h),
+  TSVD_TRY(cgemm<C>(gemm('N', 'N', n1, R, mp, 1.0, w.Qt, m, sQ, w.Uct, R, (long)mp * R, 0.0, w.Uh, R, (long)n1 * R, h),
                     w.splitk, w.splitk_elems * 2, s));
-  TSVD_TRY(cgemm<C>(gemm('N', 'N', n2, R, m, 1.0, w.CHt, m, sCH, w.Uct, R, (long)m * R, 0.0, w.Vh, R, (long)n2 * R, h),
+  TSVD_TRY(cgemm<C>(gemm('N', 'N', n2, R, mp, 1.0, w.CHt, m, sCH, w.Uct, R, (long)mp * R, 0.0, w.Vh, R, (long)n2 * R, h),
                     w.splitk, w.splitk_elems * 2, s));
   TSVD_TRY(scale_columns_inv<T>(w.Vh, R, (long)n2 * R, n2, R, w.lam, h, s));
   }
@@ -408,7 +411,7 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
     if (cudaStreamSynchronize(s) != cudaSuccess) return TSVD_ERR_CUDA;
     info->status = tcerr ? TSVD_ERR_CUDA : host[0];
     info->dead_columns = host[1];
-    info->m_eff = m;
+    info->m_eff = mp;
     info->reserved = 0;
   }
   return TSVD_OK;
@@ -607,6 +610,7 @@ extern "C" const char* tsvd_strerror(int code) {
     case TSVD_ERR_CUDA: return "CUDA launch or API failure";
     case TSVD_ERR_UNSUPPORTED: return "size or mode beyond a kernel limit";
     case TSVD_ERR_NOT_CONVERGED: return "eigen solve produced a non-finite value";
+    case TSVD_ERR_RANK_DEFICIENT: return "a Fourier slice is rank deficient (pseudoinverse by QR needs full rank)";
     default: return "unknown status";
   }
 }

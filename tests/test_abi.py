@@ -49,5 +49,9 @@ def test_argument_errors_without_gpu(lib):
     assert lib.tsvd_rbk_workspace_size(512, 512, 8, C.byref(big), C.byref(n)) == -4
     assert lib.tsvd_rbk(None, 32, 32, 8, C.byref(p), None, None, None, None, None, None, 0, None, None) == -1
     assert lib.tprod_workspace_size(0, 3, 3, 3, 1, C.byref(n)) == -1
+    assert lib.tqr_workspace_size(0, 3, 3, 0, C.byref(n)) == -1
+    assert lib.tpinv_workspace_size(4, 3, 3, 2, C.byref(n)) == -1  # FP64 / FP32 only
+    assert lib.tqr_workspace_size(40, 30, 8, 0, C.byref(n)) == 0 and n.value > 0
+    assert lib.tqr(None, 4, 3, 3, 0, None, None, None, 0, None, None) == -1
     assert lib.tsvd_strerror(-2) == b"workspace too small"
     assert lib.tsvd_version() >= 100
