@@ -256,6 +256,36 @@ TSVD_API int tsvd_error(const void* X, const void* U, const void* S, const void*
                         int precision, double* err2, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * tsvd_rfft3 / tsvd_irfft3 -- the mode-3 transforms of the method (Sec. 2,
+ * Def. of F_n: unnormalised forward DFT along the third mode, omega =
+ * e^{-2 pi i / n3}; the inverse scaled by 1/n3 after the conjugate mirror of
+ * Alg. TP).  X device (n3, plane) real, a tensor (n3, rows, cols) with
+ * plane = rows * cols; Xhat device (floor(n3/2)+1, plane) complex
+ * interleaved.  precision TSVD_FP64 (double) or TSVD_FP32 (float).
+ */
+TSVD_API int tsvd_rfft3(const void* X, long plane, int n3, int precision, void* Xhat, void* stream);
+TSVD_API int tsvd_irfft3(const void* Xhat, long plane, int n3, int precision, void* X, void* stream);
+
+/*
+ * tsvd_rbk_fourier -- Alg. 2 (Sec. 3) on the block of Fourier slices
+ * [k0, k0 + ns) of an n1 x n2 x n3 tensor whose half spectrum the caller
+ * already holds (the remark opening Sec. 4: the slices are independent
+ * problems).  This is the per-device step of the slice-sharded multi-GPU
+ * path.  Every slice sees the same test tensor as tsvd_rbk: the real Omega
+ * (n3, n2, R+P) is drawn (or taken from Omega) and transformed whole.
+ *   Ahat device (ns, n1, n2) complex (double2 for FP64, float2 otherwise),
+ *   slice k0 + s at index s; outputs in the Fourier domain: Uhat device
+ *   (ns, n1, R), Vhat device (ns, n2, R) in Ahat's complex type, sigma_hat
+ *   device (ns, R) double.  params, workspace, stream and info as tsvd_rbk.
+ *   0 <= k0, ns >= 1, k0 + ns <= floor(n3/2)+1, else TSVD_ERR_INVALID_ARG.
+ */
+TSVD_API int tsvd_rbk_fourier_workspace_size(int n1, int n2, int n3, int k0, int ns, const tsvd_params* params,
+                                             size_t* bytes);
+TSVD_API int tsvd_rbk_fourier(const void* Ahat, int n1, int n2, int n3, int k0, int ns, const tsvd_params* params,
+                              const void* Omega, void* Uhat, void* Vhat, double* sigma_hat, void* ws, size_t ws_bytes,
+                              void* stream, tsvd_info* info);
+
+/*
  * tqr -- T-QR decomposition X = Q * R (Alg. TQR, Sec. 2): per non-redundant
  * Fourier slice the economy QR of X_k with p = min(n1, n2), the other slices
  * by conjugate symmetry, and the inverse transform of both factors.  The QR of

@@ -44,6 +44,7 @@ def lib():
         L.orc_range_basis_fourier.argtypes = [dp, i, i, i, i, i, i, i, dp, C.c_uint64, ip, i, dp]
         L.orc_rtsvd.argtypes = [dp, i, i, i, i, i, i, i, dp, C.c_uint64, dp, dp, dp, dp]
         L.orc_reconstruct.argtypes = [dp, dp, dp, i, i, i, i, dp]
+        L.orc_rtsvd_hat.argtypes = [dp, dp, i, i, i, i, i, i, i, dp, dp, dp, dp, ip]
         L.orc_tqr.argtypes = [dp, i, i, i, dp, dp]
         L.orc_tpinv.argtypes = [dp, i, i, i, dp]
         L.orc_num_threads.argtypes = []
@@ -204,6 +205,22 @@ def rtsvd_fourier(X, R, P=0, q=0, mode="canonical", omega=None, seed=0, slices=N
     _check(lib().orc_rtsvd_fourier(_dp(X), n1, n2, n3, R, P, q, MODES[mode], _dp(om) if om is not None else None,
                                    C.c_uint64(int(seed)), slp, ns, _dp(Uh), _dp(sg), _dp(Vh), _dp(e2),
                                    mu.ctypes.data_as(C.POINTER(C.c_int))), "rtsvd_fourier")
+    return {"Uhat": Uh, "sig": sg, "Vhat": Vh, "err2": e2, "m": mu}
+
+
+def rtsvd_hat(Xhat, Omhat, R, P=0, q=0, mode="canonical"):
+    """Alg. 2 on given Fourier slices Xhat (ns, n1, n2) with test blocks Omhat
+    (ns, n2, R+P); returns the dict of rtsvd_fourier."""
+    Xhat, Omhat = _c128(Xhat), _c128(Omhat)
+    ns, n1, n2 = Xhat.shape
+    assert Omhat.shape == (ns, n2, R + P), Omhat.shape
+    Uh = np.empty((ns, n1, R), dtype=np.complex128)
+    sg = np.empty((ns, R))
+    Vh = np.empty((ns, n2, R), dtype=np.complex128)
+    e2 = np.empty(ns)
+    mu = np.empty(ns, dtype=np.int32)
+    _check(lib().orc_rtsvd_hat(_dp(Xhat), _dp(Omhat), ns, n1, n2, R, P, q, MODES[mode], _dp(Uh), _dp(sg), _dp(Vh),
+                               _dp(e2), mu.ctypes.data_as(C.POINTER(C.c_int))), "rtsvd_hat")
     return {"Uhat": Uh, "sig": sg, "Vhat": Vh, "err2": e2, "m": mu}
 
 

@@ -610,6 +610,21 @@ int orc_rtsvd_fourier(const double* X, int n1, int n2, int n3, int R, int P, int
   return 0;
 }
 
+/* Alg. 2 (or the chosen mode) on Fourier slices given directly: Xhat (ns, n1, n2)
+ * and the transformed test blocks Omhat (ns, n2, R+P); per slice as
+ * orc_rtsvd_fourier (used to check the slice-sharded multi-rank path). */
+int orc_rtsvd_hat(const cplx* Xhat, const cplx* Omhat, int ns, int n1, int n2, int R, int P, int q, int mode,
+                  cplx* Uhat, double* sig, cplx* Vhat, double* err2, int* m_used) {
+  if (ns < 1 || n1 < 1 || n2 < 1 || R < 1 || P < 0 || q < 0 || R > n1 || R > n2) return -1;
+  if (mode < ORC_ALG2_CANONICAL || mode > ORC_ALG2_QTRUNC || mode == ORC_EXACT) return -1;
+  const int b = R + P;
+#pragma omp parallel for schedule(dynamic)
+  for (int s = 0; s < ns; ++s)
+    rtsvd_slice(Xhat + (long)s * n1 * n2, Omhat + (long)s * n2 * b, n1, n2, R, b, q, mode, Uhat + (long)s * n1 * R,
+                sig + (long)s * R, Vhat + (long)s * n2 * R, err2 + s, m_used + s);
+  return 0;
+}
+
 int orc_range_basis_fourier(const double* X, int n1, int n2, int n3, int R, int P, int q, int mode,
                             const double* Omega, uint64_t seed, const int* slices, int ns, cplx* Qhat) {
   if (n1 < 1 || n2 < 1 || n3 < 1 || R < 1 || P < 0 || q < 0 || R > n1 || R > n2) return -1;

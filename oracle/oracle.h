@@ -74,6 +74,9 @@ int orc_rtsvd_fourier(const double* X, int n1, int n2, int n3, int R, int P, int
  * Qhat[s] is n1 x m (m = returned value, the same for every slice). */
 int orc_range_basis_fourier(const double* X, int n1, int n2, int n3, int R, int P, int q, int mode,
                             const double* Omega, uint64_t seed, const int* slices, int ns, orc_cplx* Qhat);
+/* the same on Fourier slices given directly: Xhat (ns,n1,n2), Omhat (ns,n2,R+P) */
+int orc_rtsvd_hat(const orc_cplx* Xhat, const orc_cplx* Omhat, int ns, int n1, int n2, int R, int P, int q, int mode,
+                  orc_cplx* Uhat, double* sig, orc_cplx* Vhat, double* err2, int* m_used);
 /* spatial factors U (n3,n1,R), S tubes (n3,R), V (n3,n2,R) from all h Fourier slices */
 int orc_rtsvd(const double* X, int n1, int n2, int n3, int R, int P, int q, int mode,
               const double* Omega, uint64_t seed, double* U, double* S, double* V, double* sig_hat);

@@ -63,6 +63,11 @@ SIGNATURES = {
     "tsvd_error_workspace_size": (_i, [_i, _i, _i, _i, _i, C.POINTER(C.c_size_t)]),
     "tsvd_error": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, C.c_size_t, _vp]),
     "tprod_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp]),
+    "tsvd_rfft3": (_i, [_vp, _l, _i, _i, _vp, _vp]),
+    "tsvd_irfft3": (_i, [_vp, _l, _i, _i, _vp, _vp]),
+    "tsvd_rbk_fourier_workspace_size": (_i, [_i, _i, _i, _i, _i, C.POINTER(TsvdParams), C.POINTER(_sz)]),
+    "tsvd_rbk_fourier": (_i, [_vp, _i, _i, _i, _i, _i, C.POINTER(TsvdParams), _vp, _vp, _vp, _vp, _vp, _sz, _vp,
+                              C.POINTER(TsvdInfo)]),
     "tqr_workspace_size": (_i, [_i, _i, _i, _i, C.POINTER(_sz)]),
     "tqr": (_i, [_vp, _i, _i, _i, _i, _vp, _vp, _vp, _sz, _vp, C.POINTER(TsvdInfo)]),
     "tpinv_workspace_size": (_i, [_i, _i, _i, _i, C.POINTER(_sz)]),

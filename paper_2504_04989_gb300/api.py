@@ -461,3 +461,72 @@ def tpinv(A, precision=None, return_info=False):
     if return_info:
         return X, {"status": info.status, "dead_columns": info.dead_columns}
     return X
+
+
+_CDT = {torch.float64: torch.complex128, torch.float32: torch.complex64}
+
+
+def rfft3(X, precision=None):
+    """Mode-3 transform of a real (n3, rows, cols) CUDA tensor: its
+    floor(n3/2)+1 non-redundant Fourier slices (h, rows, cols), complex."""
+    lib = _lib.load()
+    precision = _precision_of(X, precision)
+    X = X.contiguous()
+    _need_cuda(X, dtype=_DT[precision])
+    n3 = X.shape[0]
+    out = torch.empty((n3 // 2 + 1,) + tuple(X.shape[1:]), dtype=_CDT[X.dtype], device=X.device)
+    plane = X[0].numel()
+    with torch.cuda.device(X.device):
+        _lib.check(lib.tsvd_rfft3(_ptr(X), plane, n3, _prec(precision), _ptr(out), _stream(X.device)), "tsvd_rfft3")
+    return out
+
+
+def irfft3(Xh, n3):
+    """Inverse of rfft3: (h, rows, cols) complex -> real (n3, rows, cols)."""
+    lib = _lib.load()
+    Xh = Xh.contiguous()
+    _need_cuda(Xh)
+    rdt = torch.float64 if Xh.dtype == torch.complex128 else torch.float32
+    if Xh.shape[0] != n3 // 2 + 1:
+        raise ValueError("irfft3: %d slices given, n3 = %d needs %d" % (Xh.shape[0], n3, n3 // 2 + 1))
+    out = torch.empty((n3,) + tuple(Xh.shape[1:]), dtype=rdt, device=Xh.device)
+    plane = Xh[0].numel()
+    pr = _lib.TSVD_FP64 if rdt == torch.float64 else _lib.TSVD_FP32
+    with torch.cuda.device(Xh.device):
+        _lib.check(lib.tsvd_irfft3(_ptr(Xh), plane, n3, pr, _ptr(out), _stream(Xh.device)), "tsvd_irfft3")
+    return out
+
+
+def rbk_fourier(Ahat, n3, k0, R, P=10, q=2, seed=0, precision="fp32", omega=None, return_info=False, **flags):
+    """Alg. 2 on the Fourier slices k0 .. k0 + ns - 1 of an n1 x n2 x n3 tensor
+    given as Ahat (ns, n1, n2) complex CUDA tensor (complex128 for "fp64",
+    complex64 otherwise).  Returns Uhat (ns, n1, R), Vhat (ns, n2, R) complex
+    and sigma_hat (ns, R) float64, as the slices k0.. of tsvd_rbk's factors."""
+    lib = _lib.load()
+    pr = _prec(precision)
+    cdt = torch.complex128 if precision == "fp64" else torch.complex64
+    Ahat = Ahat.contiguous()
+    _need_cuda(Ahat, dtype=cdt)
+    ns, n1, n2 = Ahat.shape
+    p = _lib.TsvdParams(R=int(R), P=int(P), q=int(q), precision=pr, seed=int(seed), flags=_flags(**{
+        "fp64_qr": flags.get("fp64_qr", False), "alg1": flags.get("alg1", False),
+        "q_trunc": flags.get("q_trunc", False), "deflate": flags.get("deflate", False)}))
+    nbytes = C.c_size_t()
+    _lib.check(lib.tsvd_rbk_fourier_workspace_size(n1, n2, n3, k0, ns, C.byref(p), C.byref(nbytes)),
+               "tsvd_rbk_fourier_workspace_size")
+    dev = Ahat.device
+    ws = _workspace(nbytes.value, dev)
+    Uh = torch.empty((ns, n1, R), dtype=cdt, device=dev)
+    Vh = torch.empty((ns, n2, R), dtype=cdt, device=dev)
+    sig = torch.empty((ns, R), dtype=torch.float64, device=dev)
+    if omega is not None:
+        omega = omega.contiguous()
+        _need_cuda(omega, dtype=_DT[precision])
+    info = _lib.TsvdInfo()
+    with torch.cuda.device(dev):
+        _lib.check(lib.tsvd_rbk_fourier(_ptr(Ahat), n1, n2, n3, k0, ns, C.byref(p), _ptr(omega), _ptr(Uh), _ptr(Vh),
+                                        _ptr(sig), _ptr(ws), nbytes.value, _stream(dev),
+                                        C.byref(info) if return_info else None), "tsvd_rbk_fourier")
+    if return_info:
+        return Uh, Vh, sig, {"status": info.status, "m_eff": info.m_eff, "dead_columns": info.dead_columns}
+    return Uh, Vh, sig

@@ -365,7 +365,7 @@ template int rmul_block<float2>(const float2*, long, long, const float2*, long, 
 template <typename C>
 __global__ void __launch_bounds__(256) k_repair_dead(C* __restrict__ Q, long ldq, long sQ, int n1, int c, int nb,
                                                      const uint32_t* __restrict__ dead, uint64_t seed, int block_id,
-                                                     int* __restrict__ dead_count, int last_real) {
+                                                     int* __restrict__ dead_count, int k0, int nyq) {
   using R = decltype(C().x);
   __shared__ double red[32];
   const int b = blockIdx.x, tid = threadIdx.x;
@@ -378,7 +378,8 @@ __global__ void __launch_bounds__(256) k_repair_dead(C* __restrict__ Q, long ldq
   }
   if (ndead == 0) return;
   Q += (long)b * sQ;
-  const bool real_slice = (b == 0) || (last_real && b == (int)gridDim.x - 1);
+  const int k = k0 + b;  // Fourier slice index of this problem
+  const bool real_slice = (k == 0) || (k == nyq);
   if (tid == 0) atomicAdd(dead_count, ndead);
   uint32_t pending[4] = {dm[0], dm[1], dm[2], dm[3]};
   for (int j = 0; j < nb; ++j) {
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(256) k_repair_dead(C* __restrict__ Q, long ldq
     for (int attempt = 0; attempt < 4; ++attempt) {
       for (int i = tid; i < n1; i += blockDim.x) {
         const uint4 x = philox10(make_uint4((uint32_t)i, (uint32_t)col | ((uint32_t)attempt << 24),
-                                            (uint32_t)block_id, 3u + ((uint32_t)b << 8)),
+                                            (uint32_t)block_id, 3u + ((uint32_t)k << 8)),
                                  (uint32_t)seed, (uint32_t)(seed >> 32));
         const double u1 = ((double)x.x + 1.0) * (1.0 / 4294967296.0);
         const double u2 = ((double)x.y + 1.0) * (1.0 / 4294967296.0);
@@ -436,16 +437,16 @@ __global__ void __launch_bounds__(256) k_repair_dead(C* __restrict__ Q, long ldq
 
 template <typename C>
 int repair_dead(C* Q, long ldq, long sQ, int n1, int c, int nb, const uint32_t* dead, int batch, uint64_t seed,
-                int block_id, int* dead_count, int last_real, cudaStream_t s) {
+                int block_id, int* dead_count, int k0, int nyq, cudaStream_t s) {
   if (nb <= 0 || batch <= 0) return TSVD_OK;
-  k_repair_dead<C><<<batch, 256, 0, s>>>(Q, ldq, sQ, n1, c, nb, dead, seed, block_id, dead_count, last_real);
+  k_repair_dead<C><<<batch, 256, 0, s>>>(Q, ldq, sQ, n1, c, nb, dead, seed, block_id, dead_count, k0, nyq);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }
 template int repair_dead<double2>(double2*, long, long, int, int, int, const uint32_t*, int, uint64_t, int, int*,
-                                  int, cudaStream_t);
+                                  int, int, cudaStream_t);
 template int repair_dead<float2>(float2*, long, long, int, int, int, const uint32_t*, int, uint64_t, int, int*, int,
-                                 cudaStream_t);
+                                 int, cudaStream_t);
 
 // Orthonormalise the nb leading columns of W (n1 x b per slice) against the c
 // finished columns of Q and write them to Q columns [c, c+nb), in the
@@ -493,7 +494,7 @@ int orth_block_cols(int n1, int b, int m, int h, const OrthWs& w, int c, int nb,
   }
   {
     TSVD_STAGE("orth_repair", s);
-    TSVD_TRY(repair_dead<CL>(Q, m, sQ, n1, c, nb, w.dead, h, seed, block_id, w.dead_count, w.last_real, s));
+    TSVD_TRY(repair_dead<CL>(Q, m, sQ, n1, c, nb, w.dead, h, seed, block_id, w.dead_count, w.k0, w.nyq, s));
   }
   if (w.Qt) {
     TSVD_STAGE("convert", s);

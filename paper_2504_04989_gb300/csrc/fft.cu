@@ -568,3 +568,23 @@ extern "C" int tsvd_philox_words(const uint32_t key[2], uint32_t ctr1, uint32_t 
   TSVD_LAUNCHED();
   return TSVD_OK;
 }
+
+// The mode-3 transforms on their own (Sec. 2, Def. of F_n; Alg. TP first and
+// last lines), for callers that move Fourier slices between devices.
+extern "C" int tsvd_rfft3(const void* X, long plane, int n3, int precision, void* Xhat, void* stream) {
+  if (!X || !Xhat || plane < 1 || n3 < 1) return TSVD_ERR_INVALID_ARG;
+  if (precision == TSVD_FP64)
+    return tsvd::launch_rfft3<double>((const double*)X, (double2*)Xhat, plane, n3, (cudaStream_t)stream);
+  if (precision == TSVD_FP32)
+    return tsvd::launch_rfft3<float>((const float*)X, (float2*)Xhat, plane, n3, (cudaStream_t)stream);
+  return TSVD_ERR_INVALID_ARG;
+}
+
+extern "C" int tsvd_irfft3(const void* Xhat, long plane, int n3, int precision, void* X, void* stream) {
+  if (!X || !Xhat || plane < 1 || n3 < 1) return TSVD_ERR_INVALID_ARG;
+  if (precision == TSVD_FP64)
+    return tsvd::launch_irfft3<double>((const double2*)Xhat, (double*)X, plane, n3, (cudaStream_t)stream);
+  if (precision == TSVD_FP32)
+    return tsvd::launch_irfft3<float>((const float2*)Xhat, (float*)X, plane, n3, (cudaStream_t)stream);
+  return TSVD_ERR_INVALID_ARG;
+}

@@ -105,12 +105,12 @@ template <typename C>
 int rmul_block(const C* W, long ldw, long sW, const C* M, long ldm, long sM, int n1, int nb, int batch, C* O, long ldo,
                long sO, cudaStream_t s);
 // Replace dead columns [c, c+nb) of Q (n1 x ldq per slice) by unit vectors
-// orthogonal to columns [0, c+nb): Philox directions projected twice.  Slice 0
-// (and slice batch-1 when last_real is set: the Nyquist slice of an even n3)
-// gets real directions, as the spectrum of a real tensor is real there.
+// orthogonal to columns [0, c+nb): Philox directions projected twice.  Problem
+// b is Fourier slice k0 + b; slice 0 and slice nyq (n3/2 for an even n3, else
+// -1) get real directions, as the spectrum of a real tensor is real there.
 template <typename C>
 int repair_dead(C* Q, long ldq, long sQ, int n1, int c, int nb, const uint32_t* dead, int batch, uint64_t seed,
-                int block_id, int* dead_count, int last_real, cudaStream_t s);
+                int block_id, int* dead_count, int k0, int nyq, cudaStream_t s);
 // Block orthonormalisation step of a basis Q (n1 x m per slice, leading dim m)
 // in precision L: the nb leading columns of W (n1 x b, leading dim b) are made
 // orthonormal against Q's c finished columns by shifted CholeskyQR3 with a
@@ -129,7 +129,8 @@ struct OrthWs {
   void* Qt;
   void* splitk;
   size_t splitk_elems;  // in double2 elements
-  int last_real;        // the last slice is the (real) Nyquist slice of an even-length transform
+  int k0;               // Fourier slice index of problem 0
+  int nyq;              // index of the (real) Nyquist slice, n3/2 for an even n3, else -1
 };
 template <typename L>
 int orth_block_cols(int n1, int b, int m, int h, const OrthWs& w, int c, int nb, int block_id, uint64_t seed,

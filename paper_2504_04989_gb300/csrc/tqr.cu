@@ -183,7 +183,8 @@ static int tqr_factor(const TqrDims& d, TqrWs<T>& w, const cx_t<T>* M, cudaStrea
   o.Qt = nullptr;
   o.splitk = w.splitk;
   o.splitk_elems = w.splitk_elems;
-  o.last_real = (d.n3 % 2 == 0) && d.h > 1;
+  o.k0 = 0;
+  o.nyq = (d.n3 % 2 == 0) ? d.n3 / 2 : -1;
   for (int c = 0; c < p; c += b) {
     const int nb = std::min(b, p - c);
     TSVD_TRY(copy_cx<C>(M + c, Nc, (long)Mr * Nc, w.W, b, (long)Mr * b, Mr, nb, h, s));

@@ -34,6 +34,9 @@ namespace tsvd {
 
 struct RbkDims {
   int n1, n2, n3, h, R, P, q, b, m;
+  int hfull;    // floor(n3/2) + 1 non-redundant slices of the transform
+  int k0;       // first Fourier slice processed (h slices from k0 on)
+  int fourier;  // the caller passes the Fourier slices (tsvd_rbk_fourier): no transforms here
   int tc;    // basis-building products on tcgen05 in one pass: 0 none, 1 TF32, 2 BF16
   int tc3;   // FP32-accurate products on tcgen05 (split TF32): FP32 data unless TSVD_FLAG_SIMT
   int alg1;  // Alg. 1 (power iteration, last block only) instead of Alg. 2
@@ -49,6 +52,9 @@ static int rbk_dims(int n1, int n2, int n3, const tsvd_params* p, RbkDims* d) {
   d->n2 = n2;
   d->n3 = n3;
   d->h = n3 / 2 + 1;
+  d->hfull = d->h;
+  d->k0 = 0;
+  d->fourier = 0;
   d->R = p->R;
   d->P = p->P;
   d->q = p->q;
@@ -125,9 +131,9 @@ static RbkWs<T> carve_rbk(void* base, const RbkDims& d) {
   Carver cv(base);
   RbkWs<T> w;
   const size_t h = d.h;
-  w.Ah = cv.take<C>(h * d.n1 * d.n2);
+  w.Ah = d.fourier ? nullptr : cv.take<C>(h * d.n1 * d.n2);
   w.Om = cv.take<T>((size_t)d.n3 * d.n2 * d.b);
-  w.Omh = cv.take<C>(h * d.n2 * d.b);
+  w.Omh = cv.take<C>((size_t)d.hfull * d.n2 * d.b);
   w.Ql = cv.take<CL>(h * d.n1 * d.m);
   w.Qt = same ? (C*)w.Ql : cv.take<C>(h * d.n1 * d.m);
   w.Wl = cv.take<CL>(h * d.n1 * d.b);
@@ -144,8 +150,8 @@ static RbkWs<T> carve_rbk(void* base, const RbkDims& d) {
   w.G = cv.take<double2>(h * d.m * d.m);
   w.lam = cv.take<double>(h * d.R);
   w.Uct = cv.take<C>(h * d.m * d.R);
-  w.Uh = cv.take<C>(h * d.n1 * d.R);
-  w.Vh = cv.take<C>(h * d.n2 * d.R);
+  w.Uh = d.fourier ? nullptr : cv.take<C>(h * d.n1 * d.R);
+  w.Vh = d.fourier ? nullptr : cv.take<C>(h * d.n2 * d.R);
   w.Sh = cv.take<C>(h * d.R);
   w.eig = cv.take<char>(eig_scratch_bytes(d.m, d.R, d.h));
   w.Aop = nullptr;
@@ -198,7 +204,8 @@ static int orth_block(const RbkDims& d, RbkWs<T>& w, int c, int nb, int block_id
   o.Qt = std::is_same<T, L>::value ? nullptr : (void*)w.Qt;
   o.splitk = w.splitk;
   o.splitk_elems = w.splitk_elems;
-  o.last_real = (d.n3 % 2 == 0) && d.h > 1;
+  o.k0 = d.k0;
+  o.nyq = (d.n3 % 2 == 0) ? d.n3 / 2 : -1;
   return orth_block_cols<L>(d.n1, d.b, d.m, d.h, o, c, nb, block_id, seed, s);
 }
 
@@ -290,9 +297,15 @@ static int deflated_passes(const RbkDims& d, RbkWs<double>& w, cudaStream_t s) {
 
 template <typename T, typename L>
 static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* Omega, T* U, T* S, T* V,
-                   double* sig, void* ws, cudaStream_t s, tsvd_info* info) {
+                   double* sig, void* ws, cudaStream_t s, tsvd_info* info, const cx_t<T>* Ahat = nullptr,
+                   cx_t<T>* Uhat = nullptr, cx_t<T>* Vhat = nullptr) {
   using C = cx_t<T>;
   RbkWs<T> w = carve_rbk<T, L>(ws, d);
+  if (d.fourier) {  // Fourier slices k0 .. k0+h-1 given and returned by the caller
+    w.Ah = const_cast<C*>(Ahat);
+    w.Uh = Uhat;
+    w.Vh = Vhat;
+  }
   const int n1 = d.n1, n2 = d.n2, n3 = d.n3, h = d.h, b = d.b, m = d.m, R = d.R;
   const long sQ = (long)n1 * m, sCH = (long)n2 * m, sO = (long)n2 * b;
   if (cudaMemsetAsync(w.counters, 0, 8 * sizeof(int), s) != cudaSuccess) return TSVD_ERR_CUDA;
@@ -307,8 +320,9 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
   {
     TSVD_STAGE("rfft", s);
     TSVD_TRY(launch_rfft3<T>(Om, w.Omh, (long)n2 * b, n3, s));
-    TSVD_TRY(launch_rfft3<T>(A, w.Ah, (long)n1 * n2, n3, s));
+    if (!d.fourier) TSVD_TRY(launch_rfft3<T>(A, w.Ah, (long)n1 * n2, n3, s));
   }
+  const C* Omh = w.Omh + (long)d.k0 * n2 * b;  // the test blocks of the slices processed here
 
   if (d.tc3) {  // tensor-core operands of X-hat and X-hat^T (split TF32; BF16 copy for the BF16 path)
     TSVD_STAGE("krylov_split", s);
@@ -323,7 +337,7 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
   const int b0 = std::min(b, m);
   {
     TSVD_STAGE((d.tc || d.tc3) ? "krylov_gemm_tc" : "krylov_gemm", s);
-    TSVD_TRY(basis_product<T>(d, w, w.Omh, b, sO, b0, s));
+    TSVD_TRY(basis_product<T>(d, w, Omh, b, sO, b0, s));
   }
   TSVD_TRY((to_orth<T, L>(w, d, b0, s)));
   TSVD_TRY((orth_block<T, L>(d, w, 0, b0, 0, p.seed, s)));
@@ -395,7 +409,7 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
                     w.splitk, w.splitk_elems * 2, s));
   TSVD_TRY(scale_columns_inv<T>(w.Vh, R, (long)n2 * R, n2, R, w.lam, h, s));
   }
-  {
+  if (!d.fourier) {
   // back to the spatial domain
   TSVD_STAGE("irfft", s);
   TSVD_TRY(launch_irfft3<T>(w.Uh, U, (long)n1 * R, n3, s));
@@ -452,6 +466,49 @@ extern "C" int tsvd_rbk(const void* A, int n1, int n2, int n3, const tsvd_params
                                   sigma_hat, ws, s, info);
   return rbk_run<float, float>((const float*)A, d, *params, (const float*)Omega, (float*)U, (float*)S, (float*)V,
                                sigma_hat, ws, s, info);
+}
+
+// Alg. 2 on a block of Fourier slices [k0, k0 + ns) of an n1 x n2 x n3 tensor
+// whose half spectrum the caller holds (the slice-sharded multi-GPU path:
+// each rank transforms its rows, an all-to-all regroups slices, each rank
+// calls this on its slices).  The test tensor is drawn and transformed whole
+// (as in tsvd_rbk, so every slice sees the same Omega-hat), and the outputs
+// stay in the Fourier domain.
+static int rbk_fourier_dims(int n1, int n2, int n3, int k0, int ns, const tsvd_params* p, RbkDims* d) {
+  TSVD_TRY(rbk_dims(n1, n2, n3, p, d));
+  if (k0 < 0 || ns < 1 || k0 + ns > d->hfull) return TSVD_ERR_INVALID_ARG;
+  d->k0 = k0;
+  d->h = ns;
+  d->fourier = 1;
+  return TSVD_OK;
+}
+
+extern "C" int tsvd_rbk_fourier_workspace_size(int n1, int n2, int n3, int k0, int ns, const tsvd_params* params,
+                                               size_t* bytes) {
+  if (!bytes) return TSVD_ERR_INVALID_ARG;
+  RbkDims d;
+  TSVD_TRY(rbk_fourier_dims(n1, n2, n3, k0, ns, params, &d));
+  *bytes = rbk_bytes(d, params);
+  return TSVD_OK;
+}
+
+extern "C" int tsvd_rbk_fourier(const void* Ahat, int n1, int n2, int n3, int k0, int ns, const tsvd_params* params,
+                                const void* Omega, void* Uhat, void* Vhat, double* sigma_hat, void* ws,
+                                size_t ws_bytes, void* stream, tsvd_info* info) {
+  RbkDims d;
+  TSVD_TRY(rbk_fourier_dims(n1, n2, n3, k0, ns, params, &d));
+  if (!Ahat || !Uhat || !Vhat || !sigma_hat || !ws) return TSVD_ERR_INVALID_ARG;
+  if (((uintptr_t)ws & 255) != 0) return TSVD_ERR_INVALID_ARG;
+  if (ws_bytes < rbk_bytes(d, params)) return TSVD_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (params->precision == TSVD_FP64)
+    return rbk_run<double, double>(nullptr, d, *params, (const double*)Omega, nullptr, nullptr, nullptr, sigma_hat,
+                                   ws, s, info, (const double2*)Ahat, (double2*)Uhat, (double2*)Vhat);
+  if (params->flags & TSVD_FLAG_FP64_QR)
+    return rbk_run<float, double>(nullptr, d, *params, (const float*)Omega, nullptr, nullptr, nullptr, sigma_hat, ws,
+                                  s, info, (const float2*)Ahat, (float2*)Uhat, (float2*)Vhat);
+  return rbk_run<float, float>(nullptr, d, *params, (const float*)Omega, nullptr, nullptr, nullptr, sigma_hat, ws, s,
+                               info, (const float2*)Ahat, (float2*)Uhat, (float2*)Vhat);
 }
 
 // ---------------------------------------------------------------------------
