@@ -207,6 +207,26 @@ def test_c2_full_size_fp32_sampled_slices(api, orc):
         assert abs(g - ref["err2"][j]) <= ERR_TOL * ref["err2"][j], (slices[j], g, ref["err2"][j])
 
 
+@pytest.mark.slow
+def test_c2_full_size_fp64_sampled_slices(api, orc):
+    """The FP64 path on the 512 x 512 x 64 workload: sigma-hat on sampled
+    Fourier slices (DC, interior, Nyquist) within 1e-10 of the oracle, and the
+    per-slice Fourier errors within 1e-3 of the oracle's."""
+    X = wl.make_c2(0).astype(np.float32).astype(np.float64)
+    om = wl.omega(512, 60, 64, seed=0)
+    U, S, V, sig, info = run_gpu(api, X, 50, 10, 4, "fp64", om)
+    slices = [0, 11, 32]
+    ref = orc.rtsvd_fourier(X, 50, 10, 4, omega=om, slices=slices)
+    rel = np.abs(sig[slices] - ref["sig"]) / ref["sig"]
+    assert rel.max() < SIG_TOL["fp64"], rel.max()
+    Xh = np.fft.rfft(X, axis=0)[slices]
+    Uh = np.fft.rfft(U, axis=0)[slices]
+    Vh = np.fft.rfft(V, axis=0)[slices]
+    for j in range(len(slices)):
+        g = np.linalg.norm(Xh[j] - (Uh[j] * sig[slices[j]]) @ Vh[j].conj().T) ** 2
+        assert abs(g - ref["err2"][j]) <= ERR_TOL * ref["err2"][j], (slices[j], g, ref["err2"][j])
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("n1,n2,n3,R,P,q", [(64, 64, 16, 10, 5, 2), (65, 129, 7, 6, 4, 3), (40, 33, 2, 4, 2, 1)])
 def test_alg1_against_oracle(api, orc, n1, n2, n3, R, P, q, precision):
