@@ -286,6 +286,36 @@ TSVD_API int tsvd_rbk_fourier(const void* Ahat, int n1, int n2, int n3, int k0, 
                               void* stream, tsvd_info* info);
 
 /*
+ * Data completion of Sec. 5, Ex. 3: the iteration X^(n) = L(C^(n)) (L the
+ * truncated T-SVD of Alg. 2 followed by the product below) and
+ * C^(n+1) = T .* M + (1 - T) .* X^(n), T the observation mask, M the data.
+ *
+ * tsvd_lowrank -- X = U * S * V^T from the spatial factors of tsvd_rbk:
+ *   U (n3, n1, R), S (n3, R) singular tubes, V (n3, n2, R); X out (n3, n1, n2);
+ *   per Fourier slice X_k = U_k diag(S_k) V_k^H (Alg. TP), then the inverse
+ *   transform.  FP64 or FP32; workspace from tsvd_lowrank_workspace_size.
+ * tsvd_sigma_tubes -- the f-diagonal tubes of S^power (power 1 or 1/2, any
+ *   positive power accepted) from the Fourier-domain singular values
+ *   sigma_hat (floor(n3/2)+1, R): tubes out (n3, R); ws holds
+ *   (floor(n3/2)+1) * R complex elements (16 or 8 bytes each).
+ * tsvd_fill_in -- C <- mask ? M : X element-wise over n elements (mask bytes
+ *   nonzero = observed) and *change2 = sum (C_new - C_old)^2 in FP64 (device
+ *   scalar); partial is a device scratch of 1024 doubles.
+ * tsvd_sqdiff -- *out = sum (A - B)^2 over n elements in FP64 (device scalar),
+ *   the squared error behind PSNR = 10 log10(peak^2 n / sum); partial as above.
+ * All are asynchronous on `stream`; argument errors return at once.
+ */
+TSVD_API int tsvd_lowrank_workspace_size(int n1, int n2, int n3, int R, int precision, size_t* bytes);
+TSVD_API int tsvd_lowrank(const void* U, const void* S, const void* V, int n1, int n2, int n3, int R, int precision,
+                          void* X, void* ws, size_t ws_bytes, void* stream);
+TSVD_API int tsvd_sigma_tubes(const double* sigma_hat, int R, int n3, double power, int precision, void* tubes,
+                              void* ws, size_t ws_bytes, void* stream);
+TSVD_API int tsvd_fill_in(void* C, const void* M, const uint8_t* mask, const void* X, long n, int precision,
+                          double* partial, double* change2, void* stream);
+TSVD_API int tsvd_sqdiff(const void* A, const void* B, long n, int precision, double* partial, double* out,
+                         void* stream);
+
+/*
  * tqr -- T-QR decomposition X = Q * R (Alg. TQR, Sec. 2): per non-redundant
  * Fourier slice the economy QR of X_k with p = min(n1, n2), the other slices
  * by conjugate symmetry, and the inverse transform of both factors.  The QR of

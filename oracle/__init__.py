@@ -45,6 +45,10 @@ def lib():
         L.orc_rtsvd.argtypes = [dp, i, i, i, i, i, i, i, dp, C.c_uint64, dp, dp, dp, dp]
         L.orc_reconstruct.argtypes = [dp, dp, dp, i, i, i, i, dp]
         L.orc_rtsvd_hat.argtypes = [dp, dp, i, i, i, i, i, i, i, dp, dp, dp, dp, ip]
+        L.orc_fill_in.argtypes = [dp, dp, C.POINTER(C.c_ubyte), dp, C.c_long]
+        L.orc_fill_in.restype = C.c_double
+        L.orc_psnr.argtypes = [dp, dp, C.c_long, C.c_double]
+        L.orc_psnr.restype = C.c_double
         L.orc_tqr.argtypes = [dp, i, i, i, dp, dp]
         L.orc_tpinv.argtypes = [dp, i, i, i, dp]
         L.orc_num_threads.argtypes = []
@@ -300,3 +304,17 @@ def tpinv(X):
     out = np.empty((n3, n2, n1))
     _check(lib().orc_tpinv(_dp(X), n1, n2, n3, _dp(out)), "tpinv")
     return out
+
+
+def fill_in(Cm, M, T, X):
+    """Ex. 3 fill-in: returns (C_new, sum (C_new - C_old)^2)."""
+    Cn = _f64(Cm).copy()
+    M, X = _f64(M), _f64(X)
+    T = np.ascontiguousarray(T, dtype=np.uint8)
+    ch = lib().orc_fill_in(_dp(Cn), _dp(M), T.ctypes.data_as(C.POINTER(C.c_ubyte)), _dp(X), Cn.size)
+    return Cn, ch
+
+
+def psnr(X, Y, peak=255.0):
+    X, Y = _f64(X), _f64(Y)
+    return lib().orc_psnr(_dp(X), _dp(Y), X.size, float(peak))

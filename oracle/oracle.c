@@ -785,3 +785,23 @@ int orc_tpinv(const double* X, int n1, int n2, int n3, double* Xp) {
   free(Ph);
   return 0;
 }
+
+/* ========================================================================== */
+/* Data completion, Sec. 5 Ex. 3: the fill-in C <- T .* M + (1 - T) .* X and   */
+/* the squared distance behind PSNR = 10 log10(peak^2 / MSE), MSE = ||.||^2/N. */
+/* ========================================================================== */
+double orc_fill_in(double* C, const double* M, const unsigned char* T, const double* X, long n) {
+  double change2 = 0;
+  for (long i = 0; i < n; ++i) {
+    const double c = T[i] ? M[i] : X[i];
+    change2 += (c - C[i]) * (c - C[i]);
+    C[i] = c;
+  }
+  return change2;
+}
+
+double orc_psnr(const double* X, const double* Y, long n, double peak) {
+  double s = 0;
+  for (long i = 0; i < n; ++i) s += (X[i] - Y[i]) * (X[i] - Y[i]);
+  return (s == 0) ? INFINITY : 10.0 * log10(peak * peak / (s / (double)n));
+}

@@ -88,6 +88,9 @@ int orc_reconstruct(const double* U, const double* S, const double* V, int n1, i
 int orc_tqr(const double* X, int n1, int n2, int n3, double* Q, double* R);
 /* Alg. mp: Moore-Penrose pseudoinverse Xp (n3,n2,n1) of X (n3,n1,n2). */
 int orc_tpinv(const double* X, int n1, int n2, int n3, double* Xp);
+/* Ex. 3: C <- T ? M : X element-wise, returns sum (C_new - C_old)^2; and the PSNR (Sec. 5) */
+double orc_fill_in(double* C, const double* M, const unsigned char* T, const double* X, long n);
+double orc_psnr(const double* X, const double* Y, long n, double peak);
 int orc_num_threads(void);
 
 #ifdef __cplusplus

@@ -68,6 +68,11 @@ SIGNATURES = {
     "tsvd_rbk_fourier_workspace_size": (_i, [_i, _i, _i, _i, _i, C.POINTER(TsvdParams), C.POINTER(_sz)]),
     "tsvd_rbk_fourier": (_i, [_vp, _i, _i, _i, _i, _i, C.POINTER(TsvdParams), _vp, _vp, _vp, _vp, _vp, _sz, _vp,
                               C.POINTER(TsvdInfo)]),
+    "tsvd_lowrank_workspace_size": (_i, [_i, _i, _i, _i, _i, C.POINTER(_sz)]),
+    "tsvd_lowrank": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _sz, _vp]),
+    "tsvd_sigma_tubes": (_i, [_vp, _i, _i, C.c_double, _i, _vp, _vp, _sz, _vp]),
+    "tsvd_fill_in": (_i, [_vp, _vp, _vp, _vp, _l, _i, _vp, _vp, _vp]),
+    "tsvd_sqdiff": (_i, [_vp, _vp, _l, _i, _vp, _vp, _vp]),
     "tqr_workspace_size": (_i, [_i, _i, _i, _i, C.POINTER(_sz)]),
     "tqr": (_i, [_vp, _i, _i, _i, _i, _vp, _vp, _vp, _sz, _vp, C.POINTER(TsvdInfo)]),
     "tpinv_workspace_size": (_i, [_i, _i, _i, _i, C.POINTER(_sz)]),

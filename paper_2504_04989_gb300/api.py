@@ -530,3 +530,73 @@ def rbk_fourier(Ahat, n3, k0, R, P=10, q=2, seed=0, precision="fp32", omega=None
     if return_info:
         return Uh, Vh, sig, {"status": info.status, "m_eff": info.m_eff, "dead_columns": info.dead_columns}
     return Uh, Vh, sig
+
+
+def lowrank(U, S, V, out=None, ws=None):
+    """X = U * S * V^T (n3, n1, n2) from tsvd_rbk's spatial factors U (n3, n1, R),
+    S (n3, R), V (n3, n2, R), fused in the Fourier domain."""
+    lib = _lib.load()
+    precision = _precision_of(U, None)
+    U, S, V = U.contiguous(), S.contiguous(), V.contiguous()
+    _need_cuda(U, S, V, dtype=U.dtype)
+    n3, n1, R = U.shape
+    n2 = V.shape[1]
+    nbytes = C.c_size_t()
+    _lib.check(lib.tsvd_lowrank_workspace_size(n1, n2, n3, R, _prec(precision), C.byref(nbytes)), "lowrank ws")
+    ws = _workspace(nbytes.value, U.device) if ws is None else ws
+    X = torch.empty((n3, n1, n2), dtype=U.dtype, device=U.device) if out is None else out
+    with torch.cuda.device(U.device):
+        _lib.check(lib.tsvd_lowrank(_ptr(U), _ptr(S), _ptr(V), n1, n2, n3, R, _prec(precision), _ptr(X), _ptr(ws),
+                                    nbytes.value, _stream(U.device)), "tsvd_lowrank")
+    return X
+
+
+def sigma_tubes(sig_hat, n3, power=1.0, dtype=torch.float32):
+    """Tubes (n3, R) of S^power from the Fourier singular values (h, R)."""
+    lib = _lib.load()
+    sig_hat = sig_hat.contiguous()
+    _need_cuda(sig_hat, dtype=torch.float64)
+    h, R = sig_hat.shape
+    if h != n3 // 2 + 1:
+        raise ValueError("sigma_tubes: %d slices for n3 = %d" % (h, n3))
+    pr = _lib.TSVD_FP64 if dtype == torch.float64 else _lib.TSVD_FP32
+    ws = _workspace(16 * h * R, sig_hat.device)
+    out = torch.empty((n3, R), dtype=dtype, device=sig_hat.device)
+    with torch.cuda.device(sig_hat.device):
+        _lib.check(lib.tsvd_sigma_tubes(_ptr(sig_hat), R, n3, float(power), pr, _ptr(out), _ptr(ws), ws.numel(),
+                                        _stream(sig_hat.device)), "tsvd_sigma_tubes")
+    return out
+
+
+def fill_in(Cm, M, mask, X, change2=None, partial=None):
+    """In place C <- mask ? M : X; returns the device FP64 scalar sum (dC)^2."""
+    lib = _lib.load()
+    _need_cuda(Cm, M, X, dtype=Cm.dtype)
+    if mask.dtype != torch.uint8 or not mask.is_cuda or mask.numel() != Cm.numel():
+        raise ValueError("mask must be a CUDA uint8 tensor with C's number of elements")
+    change2 = torch.empty((), dtype=torch.float64, device=Cm.device) if change2 is None else change2
+    partial = torch.empty(1024, dtype=torch.float64, device=Cm.device) if partial is None else partial
+    with torch.cuda.device(Cm.device):
+        _lib.check(lib.tsvd_fill_in(_ptr(Cm), _ptr(M), _ptr(mask), _ptr(X), Cm.numel(), _prec(_precision_of(Cm, None)),
+                                    _ptr(partial), _ptr(change2), _stream(Cm.device)), "tsvd_fill_in")
+    return change2
+
+
+def sqdiff(A, B, out=None, partial=None):
+    """Device FP64 scalar sum (A - B)^2."""
+    lib = _lib.load()
+    _need_cuda(A, B, dtype=A.dtype)
+    A, B = A.contiguous(), B.contiguous()
+    out = torch.empty((), dtype=torch.float64, device=A.device) if out is None else out
+    partial = torch.empty(1024, dtype=torch.float64, device=A.device) if partial is None else partial
+    with torch.cuda.device(A.device):
+        _lib.check(lib.tsvd_sqdiff(_ptr(A), _ptr(B), A.numel(), _prec(_precision_of(A, None)), _ptr(partial),
+                                   _ptr(out), _stream(A.device)), "tsvd_sqdiff")
+    return out
+
+
+def psnr(X, Y, peak=255.0):
+    """PSNR = 10 log10(peak^2 / MSE) dB (Sec. 5), MSE = ||X - Y||_F^2 / num(X)."""
+    import math
+    mse = sqdiff(X, Y).item() / X.numel()
+    return float("inf") if mse == 0 else 10.0 * math.log10(peak * peak / mse)

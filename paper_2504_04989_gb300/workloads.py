@@ -222,3 +222,55 @@ def make_c4(seed: int = 0, count: int = 256):
         X = low_tubal_rank(n1, n2, n3, np.linspace(10.0, 1.0, r), noise_std=1e-3, seed=seed * 100003 + t)
         items.append(dict(X=X, R=r, P=5, q=2))
     return items
+
+
+# ---------------------------------------------------------------------------
+# Completion (Sec. 5, Ex. 3 and Ex. 4): image-like tensors and missing-pixel
+# masks.  The Kodak images are not reproduced; an image-like tensor is a
+# full-spectrum tensor with slowly decaying singular values, shifted and
+# scaled to the 0..255 range of 8-bit pixels (n3 = 3 colour channels).
+# ---------------------------------------------------------------------------
+def make_image(n1: int = 256, n2: int = 256, n3: int = 3, decay: float = 1.2, seed: int = 0) -> np.ndarray:
+    """Image-like (n3, n1, n2) float64 tensor in [0, 255]: sigma_i = i^-decay
+    on every Fourier slice (Haar t-factors), mean 128, RMS contrast 40."""
+    r = min(n1, n2)
+    X = low_tubal_rank(n1, n2, n3, np.arange(1, r + 1, dtype=np.float64) ** -decay, seed=seed)
+    X = 128.0 + 40.0 * (X - X.mean()) / X.std()
+    return np.clip(X, 0.0, 255.0)
+
+
+def mask_random(shape, missing: float, seed: int = 0) -> np.ndarray:
+    """Observation mask (uint8, 1 = observed) with each pixel missing with
+    probability `missing` (Ex. 3: 70 %, Ex. 4: 80 %)."""
+    return (_rng(seed, 6).random(shape) >= missing).astype(np.uint8)
+
+
+def mask_lines(shape, spacing: int = 16, width: int = 2, seed: int = 0) -> np.ndarray:
+    """Structured mask: rows and columns of `width` pixels missing about every
+    `spacing` pixels (jittered), the same in every frontal slice (Ex. 3's
+    line patterns; a smaller spacing is the denser variant)."""
+    n3, n1, n2 = shape
+    rng = _rng(seed, 7)
+    m = np.ones((n1, n2), dtype=np.uint8)
+    for n, axis in ((n1, 0), (n2, 1)):
+        for start in range(int(rng.integers(0, spacing)), n, spacing):
+            lo = min(n, start + int(rng.integers(-spacing // 4, spacing // 4 + 1)) % n)
+            if axis == 0:
+                m[lo:lo + width, :] = 0
+            else:
+                m[:, lo:lo + width] = 0
+    return np.broadcast_to(m, shape).copy()
+
+
+def mask_circles(shape, count: int = 40, radius: float = 6.0, seed: int = 0) -> np.ndarray:
+    """Structured mask: `count` discs of the given radius missing at random
+    centres, the same in every frontal slice (Ex. 3's circle patterns; more
+    or larger discs are the denser variants)."""
+    n3, n1, n2 = shape
+    rng = _rng(seed, 8)
+    ii, jj = np.meshgrid(np.arange(n1), np.arange(n2), indexing="ij")
+    m = np.ones((n1, n2), dtype=np.uint8)
+    for _ in range(count):
+        ci, cj = rng.uniform(0, n1), rng.uniform(0, n2)
+        m[(ii - ci) ** 2 + (jj - cj) ** 2 <= radius * radius] = 0
+    return np.broadcast_to(m, shape).copy()

@@ -444,3 +444,30 @@ def test_qtrunc_against_numpy_sketch(orc):
         np.testing.assert_allclose(ro["sig"][k], s, rtol=1e-12)
     full = orc.rtsvd_fourier(X, R, P, q, omega=om)  # the full basis is at least as good (nested spans)
     assert np.all(full["err2"] <= ro["err2"] * (1 + 1e-12))
+
+
+# --------------------------------------------------------------------------- Ex. 3 fill-in and PSNR
+def test_fill_in_invariants(orc):
+    """C <- T .* M + (1 - T) .* X: observed entries equal M, the others X,
+    applying it twice changes nothing, and the reported change is the squared
+    distance of the old and new C (checked on entries chosen by hand)."""
+    r = np.random.default_rng(5)
+    M, X, C0 = r.standard_normal(200), r.standard_normal(200), r.standard_normal(200)
+    T = (r.random(200) < 0.3).astype(np.uint8)
+    C1, ch = orc.fill_in(C0, M, T, X)
+    assert np.array_equal(C1[T == 1], M[T == 1]) and np.array_equal(C1[T == 0], X[T == 0])
+    C2, ch2 = orc.fill_in(C1, M, T, X)
+    assert np.array_equal(C2, C1) and ch2 == 0.0
+    Cz, chz = orc.fill_in(np.zeros(3), np.array([1.0, 2.0, 3.0]), np.array([1, 0, 1], np.uint8),
+                          np.array([7.0, -2.0, 9.0]))
+    assert np.array_equal(Cz, [1.0, -2.0, 3.0]) and chz == 1.0 + 4.0 + 9.0
+
+
+def test_psnr_closed_forms(orc):
+    """PSNR of Sec. 5: a constant offset d gives 10 log10(255^2 / d^2); equal
+    images give +inf; scaling the error by 10 lowers the PSNR by 20 dB."""
+    X = np.random.default_rng(6).uniform(0, 255, (3, 8, 8))
+    assert abs(orc.psnr(X, X + 2.0) - 10 * np.log10(255.0 ** 2 / 4.0)) < 1e-12
+    assert orc.psnr(X, X) == np.inf
+    E = np.random.default_rng(7).standard_normal(X.shape)
+    assert abs(orc.psnr(X, X + E) - orc.psnr(X, X + 10 * E) - 20.0) < 1e-9
