@@ -34,7 +34,10 @@ struct EigScratch {
   double* Z;       // [batch][R][m] real eigenvectors of T (vector-contiguous)
   double* lu;      // [batch][5][m][R] inverse-iteration LU factors
   double* tnorm;   // [batch]
+  double2* Sg;     // packed own rows of the cluster reduction when they do not fit in shared memory
 };
+
+static bool hetrd_needs_global_rows(int m, int batch);
 
 static EigScratch carve_eig(void* base, int m, int R, int batch, size_t* bytes) {
   Carver cv(base);
@@ -48,6 +51,9 @@ static EigScratch carve_eig(void* base, int m, int R, int batch, size_t* bytes) 
   e.Z = cv.take<double>((size_t)batch * m * R);
   e.lu = cv.take<double>((size_t)batch * 5 * m * R);
   e.tnorm = cv.take<double>((size_t)batch);
+  // CL CTAs of a slice own at most m(m+1)/2 + CL m packed elements together (CL <= 8)
+  e.Sg = hetrd_needs_global_rows(m, batch) ? cv.take<double2>((size_t)batch * ((size_t)m * (m + 1) / 2 + 8 * (size_t)m))
+                                           : nullptr;
   if (bytes) *bytes = cv.bytes();
   return e;
 }
@@ -247,9 +253,10 @@ static size_t hetrd_smem_elems(int m, int CL) {
   for (int c = 0; c < CL; ++c) mx = std::max(mx, hs_rowbase(hs_own_rows(m, c, CL), c, CL));
   return (size_t)mx;
 }
-static size_t hetrd_smem_bytes(int m, int CL, int nt = HS_THREADS) {
+static size_t hetrd_smem_bytes(int m, int CL, int nt = HS_THREADS, bool global_rows = false) {
   const size_t vown = (size_t)(m + CL - 1) / CL;  // v at the own rows, compacted
-  const size_t el = (hetrd_smem_elems(m, CL) + 5 * (size_t)m + 2 * (size_t)nt + vown) * sizeof(double2);
+  const size_t rows = global_rows ? 0 : hetrd_smem_elems(m, CL);
+  const size_t el = (rows + 5 * (size_t)m + 2 * (size_t)nt + vown) * sizeof(double2);
   return el + (size_t)(m + 1) * sizeof(int);
 }
 
@@ -267,12 +274,14 @@ __device__ __forceinline__ int hs_seg(int t, int E, int L) { return min(t * L, E
 // the segment holding element e
 __device__ __forceinline__ int hs_owner(int e, int L) { return e / L; }
 
-template <int CL>
+template <int CL, bool GS>
 __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_smem(const double2* __restrict__ G, long ldg, long sG, int m,
                                                            int s_elems, EigScratch e) {
   extern __shared__ __align__(16) double2 hsm[];
-  double2* S = hsm;                            // own rows, packed
-  double2* bufV = S + s_elems;                 // [2][m] v of this and of the previous step
+  // own rows, packed: in shared memory, or (GS) in this CTA's private part of a
+  // global array, which stays L2-resident (only this CTA reads or writes it)
+  double2* S = GS ? e.Sg + (long)blockIdx.x * s_elems : hsm;
+  double2* bufV = GS ? hsm : S + s_elems;      // [2][m] v of this and of the previous step
   double2* bufW = bufV + 2 * m;                // [2][m] w
   double2* pv = bufW + 2 * m;                  // [m] this CTA's part of p
   double2* slotF = pv + m;                     // [T] partial of a thread's first (split) row / column
@@ -706,12 +715,14 @@ __device__ __forceinline__ dfl df_block_sum(dfl v, dfl* red) {
   return t;
 }
 
-template <int CL, int NT>
+template <int CL, int NT, bool GS>
 __global__ void __launch_bounds__(NT, 1) k_hetrd_df(const double2* __restrict__ G, long ldg, long sG, int m,
                                                             int s_elems, EigScratch e) {
   extern __shared__ __align__(16) cdf dsm[];
-  cdf* S = dsm;
-  cdf* bufV = S + s_elems;
+  // own rows, packed: in shared memory, or (GS) in this CTA's private part of a
+  // global array, which stays L2-resident (only this CTA reads or writes it)
+  cdf* S = GS ? (cdf*)e.Sg + (long)blockIdx.x * s_elems : dsm;
+  cdf* bufV = GS ? dsm : S + s_elems;
   cdf* bufW = bufV + 2 * m;
   cdf* pv = bufW + 2 * m;
   cdf* slotF = pv + m;
@@ -1871,24 +1882,30 @@ static int device_attr(cudaDeviceAttr a, int fallback) {
 // rows do not fit: the largest CL in {8,4,2,1} with batch * CL CTAs resident
 // at once (one per SM), at least 48 rows per CTA (else the per-step barriers
 // dominate) and the packed rows within the opt-in shared memory.
-static int hetrd_smem_cluster(int m, int batch, int nt) {
+static int hetrd_smem_cluster(int m, int batch, int nt, bool global_rows = false) {
   if (m < 2) return 0;
   const int sms = device_attr(cudaDevAttrMultiProcessorCount, 148);
   // the kernels' static arrays (up to about 1.3 KB) share the per-block limit with the dynamic part
   const size_t smax = (size_t)device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin, 232448) - 2048;
   for (int CL = 8; CL >= 1; CL >>= 1) {
     if (CL > 1 && ((long)batch * CL > sms || m / CL < 48)) continue;
-    if (hetrd_smem_bytes(m, CL, nt) <= smax) return CL;
+    if (hetrd_smem_bytes(m, CL, nt, global_rows) <= smax) return CL;
   }
   return 0;
 }
 
-template <int CL, bool DF>
+// the packed rows do not fit in shared memory for the double-float reduction
+// (the larger of the two): they go to a global array (EigScratch::Sg)
+static bool hetrd_needs_global_rows(int m, int batch) {
+  return m >= 2 && hetrd_smem_cluster(m, batch, 2 * HS_THREADS) == 0;
+}
+
+template <int CL, bool DF, bool GS>
 static int launch_hetrd_smem_t(const double2* G, long ldg, long sG, int m, int batch, const EigScratch& e,
                                cudaStream_t s) {
   constexpr int NT = DF ? 2 * HS_THREADS : HS_THREADS;
-  const size_t smem = hetrd_smem_bytes(m, CL, NT);
-  auto kern = DF ? k_hetrd_df<CL, NT> : k_hetrd_smem<CL>;
+  const size_t smem = hetrd_smem_bytes(m, CL, NT, GS);
+  auto kern = DF ? k_hetrd_df<CL, NT, GS> : k_hetrd_smem<CL, GS>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return TSVD_ERR_CUDA;
@@ -1913,14 +1930,14 @@ static int launch_hetrd_smem_t(const double2* G, long ldg, long sG, int m, int b
   return TSVD_OK;
 }
 
-template <bool DF>
+template <bool DF, bool GS>
 static int launch_hetrd_smem(int CL, const double2* G, long ldg, long sG, int m, int batch, const EigScratch& e,
                              cudaStream_t s) {
   switch (CL) {
-    case 8: return launch_hetrd_smem_t<8, DF>(G, ldg, sG, m, batch, e, s);
-    case 4: return launch_hetrd_smem_t<4, DF>(G, ldg, sG, m, batch, e, s);
-    case 2: return launch_hetrd_smem_t<2, DF>(G, ldg, sG, m, batch, e, s);
-    default: return launch_hetrd_smem_t<1, DF>(G, ldg, sG, m, batch, e, s);
+    case 8: return launch_hetrd_smem_t<8, DF, GS>(G, ldg, sG, m, batch, e, s);
+    case 4: return launch_hetrd_smem_t<4, DF, GS>(G, ldg, sG, m, batch, e, s);
+    case 2: return launch_hetrd_smem_t<2, DF, GS>(G, ldg, sG, m, batch, e, s);
+    default: return launch_hetrd_smem_t<1, DF, GS>(G, ldg, sG, m, batch, e, s);
   }
 }
 
@@ -1933,11 +1950,18 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
   EigScratch e = carve_eig(scratch, m, R, batch, nullptr);
   // FP32 path (C = float2): double-float reduction (twice the threads); FP64 path: FP64
   constexpr bool kDoubleFloat = std::is_same<C, float2>::value;
-  const int CLs = hetrd_smem_cluster(m, batch, kDoubleFloat ? 2 * HS_THREADS : HS_THREADS);
-  const int hv32 = (kDoubleFloat && CLs > 0) ? 1 : 0;  // Householder vectors stored as float2
+  const int NTh = kDoubleFloat ? 2 * HS_THREADS : HS_THREADS;
+  const int CLs = hetrd_smem_cluster(m, batch, NTh);
+  // rows too large for shared memory: the same double-float cluster reduction on
+  // rows kept in L2 (the FP64 path keeps its FP64 L2 kernel below)
+  const int CLg = (kDoubleFloat && CLs == 0 && e.Sg) ? hetrd_smem_cluster(m, batch, NTh, true) : 0;
+  const int hv32 = (kDoubleFloat && (CLs > 0 || CLg > 0)) ? 1 : 0;  // Householder vectors stored as float2
   if (CLs > 0) {
     TSVD_STAGE("eig_hetrd", s);
-    TSVD_TRY((launch_hetrd_smem<kDoubleFloat>(CLs, G, ldg, sG, m, batch, e, s)));
+    TSVD_TRY((launch_hetrd_smem<kDoubleFloat, false>(CLs, G, ldg, sG, m, batch, e, s)));
+  } else if (CLg > 0) {
+    TSVD_STAGE("eig_hetrd", s);
+    TSVD_TRY((launch_hetrd_smem<kDoubleFloat, true>(CLg, G, ldg, sG, m, batch, e, s)));
   } else {
     TSVD_STAGE("eig_hetrd", s);
     const size_t smem = (2 + 16) * (size_t)m * sizeof(double2);  // v, p and 16 warps' partials
