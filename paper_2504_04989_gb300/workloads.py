@@ -230,12 +230,16 @@ def make_c4(seed: int = 0, count: int = 256):
 # full-spectrum tensor with slowly decaying singular values, shifted and
 # scaled to the 0..255 range of 8-bit pixels (n3 = 3 colour channels).
 # ---------------------------------------------------------------------------
-def make_image(n1: int = 256, n2: int = 256, n3: int = 3, decay: float = 1.2, seed: int = 0) -> np.ndarray:
-    """Image-like (n3, n1, n2) float64 tensor in [0, 255]: sigma_i = i^-decay
-    on every Fourier slice (Haar t-factors), mean 128, RMS contrast 40."""
-    r = min(n1, n2)
-    X = low_tubal_rank(n1, n2, n3, np.arange(1, r + 1, dtype=np.float64) ** -decay, seed=seed)
+def make_image(n1: int = 256, n2: int = 256, n3: int = 3, rank: int = 20, noise: float = 0.5,
+               seed: int = 0) -> np.ndarray:
+    """Image-like (n3, n1, n2) float64 tensor in [0, 255]: tubal rank `rank`
+    (sigma = linspace(3, 1, rank) on every Fourier slice, Haar t-factors),
+    shifted to mean 128 with RMS contrast 40, plus Gaussian pixel noise of
+    std `noise`, clipped to 0..255."""
+    X = low_tubal_rank(n1, n2, n3, np.linspace(3.0, 1.0, rank), seed=seed)
     X = 128.0 + 40.0 * (X - X.mean()) / X.std()
+    if noise > 0:
+        X = X + noise * _rng(seed, 9).standard_normal(X.shape)
     return np.clip(X, 0.0, 255.0)
 
 
@@ -246,19 +250,24 @@ def mask_random(shape, missing: float, seed: int = 0) -> np.ndarray:
 
 
 def mask_lines(shape, spacing: int = 16, width: int = 2, seed: int = 0) -> np.ndarray:
-    """Structured mask: rows and columns of `width` pixels missing about every
-    `spacing` pixels (jittered), the same in every frontal slice (Ex. 3's
-    line patterns; a smaller spacing is the denser variant)."""
+    """Structured mask: horizontal and vertical line segments `width` pixels
+    wide, about one every `spacing` pixels, each of random length (a quarter
+    to three quarters of the image) and position, the same in every frontal
+    slice (Ex. 3's line patterns; a smaller spacing is the denser variant).
+    Rows or columns missing over their whole length would carry no
+    information for any low-rank completion, hence segments."""
     n3, n1, n2 = shape
     rng = _rng(seed, 7)
     m = np.ones((n1, n2), dtype=np.uint8)
-    for n, axis in ((n1, 0), (n2, 1)):
+    for n, other, axis in ((n1, n2, 0), (n2, n1, 1)):
         for start in range(int(rng.integers(0, spacing)), n, spacing):
-            lo = min(n, start + int(rng.integers(-spacing // 4, spacing // 4 + 1)) % n)
+            lo = int(np.clip(start + rng.integers(-spacing // 4, spacing // 4 + 1), 0, n - 1))
+            length = int(rng.integers(other // 4, 3 * other // 4 + 1))
+            a = int(rng.integers(0, other - length + 1))
             if axis == 0:
-                m[lo:lo + width, :] = 0
+                m[lo:lo + width, a:a + length] = 0
             else:
-                m[:, lo:lo + width] = 0
+                m[a:a + length, lo:lo + width] = 0
     return np.broadcast_to(m, shape).copy()
 
 

@@ -192,24 +192,26 @@ def test_fill_in_plan_graph_replay_equals_eager(mods):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("mask_kind", ["random80", "lines", "circles"])
-def test_image_completion_psnr(mods, mask_kind):
-    """Ex. 4's setting on a 256 x 256 x 3 image-like tensor (values 0..255):
-    80 % of the pixels missing at random (or structured line / circle masks),
-    tubal rank 40, P = 10, q = 2, 100 graph-replayed iterations.  The PSNR of
-    the recovered tensor rises well above that of the zero-filled
-    observations, and the fill-in change falls."""
+@pytest.mark.parametrize("mask_kind,gain", [("random70", 20.0), ("circles", 12.0), ("lines", 1.0)])
+def test_image_completion_psnr(mods, mask_kind, gain):
+    """Ex. 3's setting on a 256 x 256 x 3 image-like tensor (values 0..255,
+    tubal rank 20): 70 % of the pixels missing at random, or a structured mask
+    of discs or line segments; tubal rank 20, P = 10, q = 2, 100
+    graph-replayed iterations.  The PSNR of the recovered tensor rises above
+    that of the zero-filled observations by at least `gain` dB (about 5 dB
+    below what exact per-slice SVDs reach in the same 100 iterations: 35.8,
+    32.4 and 14.5 dB from 7.1, 13.0 and 11.8), and the fill-in change falls."""
     api, comp = mods
-    X = wl.make_image(256, 256, 3, seed=4).astype(np.float32)
-    T = {"random80": lambda: wl.mask_random(X.shape, 0.8, seed=5),
+    X = wl.make_image(256, 256, 3, rank=20, seed=4).astype(np.float32)
+    T = {"random70": lambda: wl.mask_random(X.shape, 0.7, seed=5),
          "lines": lambda: wl.mask_lines(X.shape, 8, 2, seed=5),
          "circles": lambda: wl.mask_circles(X.shape, 120, 6.0, seed=5)}[mask_kind]()
     Xd, Td = dev(X, torch.float32), torch.from_numpy(T).cuda()
-    plan = comp.FillInPlan(Xd, Td, 40, P=10, q=2, graph=True)
+    plan = comp.FillInPlan(Xd, Td, 20, P=10, q=2, graph=True)
     p0 = api.psnr(plan.C, Xd)
     plan.step(10)
     ch10 = plan.change2.item()
     plan.step(90)
     p1 = api.psnr(plan.X, Xd)
-    assert p1 > p0 + 5.0, (p0, p1)
+    assert p1 > p0 + gain, (p0, p1)
     assert plan.change2.item() < ch10, (ch10, plan.change2.item())
