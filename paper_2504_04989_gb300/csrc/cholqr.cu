@@ -471,6 +471,9 @@ int orth_block_cols(int n1, int b, int m, int h, const OrthWs& w, int c, int nb,
                            : 1e-5;
   const double dead_rel = std::is_same<L, double>::value ? 1e-12 : 1e-7;
   for (int pass = 0; pass < 3; ++pass) {
+    // a Gram-Schmidt projection before every pass: without the third, blocks
+    // whose new directions are tiny next to the old ones (exact low rank in
+    // FP32, the fast-decaying spectra of Sec. 5 Ex. 1 in FP64) lose accuracy
     if (c > 0) {
       TSVD_STAGE("orth_cgs", s);
       TSVD_TRY(cgemm<CL>(gemm('H', 'N', c, nb, n1, 1.0, Q, m, sQ, W, b, sW, 0.0, P, nb, sP, h), w.splitk, sk, s));

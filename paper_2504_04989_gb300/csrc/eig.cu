@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(512) k_hetrd(double2* __restrict__ G, long ldg
 //   p = 2 A^{(j)} v,  w = p - (v^H p) v
 // ---------------------------------------------------------------------------
 constexpr int HS_THREADS = 256;
+constexpr int HS_U_GLOBAL = 4;  // row-store elements a thread loads before using them, rows in L2
 
 __host__ __device__ __forceinline__ int hs_own_rows(int m, int c, int CL) { return (c < m) ? (m - 1 - c) / CL + 1 : 0; }
 __host__ __device__ __forceinline__ int hs_rowbase(int q, int c, int CL) { return q * (c + 1) + CL * q * (q - 1) / 2; }
@@ -276,7 +277,7 @@ __device__ __forceinline__ int hs_owner(int e, int L) { return e / L; }
 
 template <int CL, bool GS>
 __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_smem(const double2* __restrict__ G, long ldg, long sG, int m,
-                                                           int s_elems, EigScratch e) {
+                                                           int s_elems, EigScratch e, int b0) {
   extern __shared__ __align__(16) double2 hsm[];
   // own rows, packed: in shared memory, or (GS) in this CTA's private part of a
   // global array, which stays L2-resident (only this CTA reads or writes it)
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_smem(const double2* __r
   __shared__ double red[2 * (HS_THREADS / 32)];
   cg::cluster_group cluster = cg::this_cluster();
   const int c = (CL > 1) ? (int)cluster.block_rank() : 0;
-  const int b = blockIdx.x / CL;
+  const int b = b0 + (int)blockIdx.x / CL;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = HS_THREADS / 32;
   G += (long)b * sG;
@@ -717,12 +718,13 @@ __device__ __forceinline__ dfl df_block_sum(dfl v, dfl* red) {
 
 template <int CL, int NT, bool GS>
 __global__ void __launch_bounds__(NT, 1) k_hetrd_df(const double2* __restrict__ G, long ldg, long sG, int m,
-                                                            int s_elems, EigScratch e) {
+                                                            int s_elems, EigScratch e, int b0) {
   extern __shared__ __align__(16) cdf dsm[];
   // own rows, packed: in shared memory, or (GS) in this CTA's private part of a
   // global array, which stays L2-resident (only this CTA reads or writes it)
   cdf* S = GS ? (cdf*)e.Sg + (long)blockIdx.x * s_elems : dsm;
   cdf* bufV = GS ? dsm : S + s_elems;
+  constexpr int HS_U = HS_U_GLOBAL;
   cdf* bufW = bufV + 2 * m;
   cdf* pv = bufW + 2 * m;
   cdf* slotF = pv + m;
@@ -735,7 +737,7 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df(const double2* __restrict__ 
   __shared__ dfl s_vinv; // its normalisation
   cg::cluster_group cluster = cg::this_cluster();
   const int c = (CL > 1) ? (int)cluster.block_rank() : 0;
-  const int b = blockIdx.x / CL;
+  const int b = b0 + (int)blockIdx.x / CL;  // slice (launches may cover a range of slices from b0)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = NT / 32;
   G += (long)b * sG;
@@ -843,21 +845,55 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df(const double2* __restrict__ 
             int g = g0 + CL * i;
             int k = j + 1 + (e0 - Pi);
             cdf* row = S + hs_rowbase(q0 + i, c, CL);
-            cdf vg = vp[g], wg = wp[g];
-            for (int el = e0; el < e1; ++el) {
-              cdf a = cdf_lag(row[k], vg, wg, vp[k], wp[k]);
-              if (k == g) {
-                a.ih = 0.f;
-                a.il = 0.f;
+            if constexpr (GS) {
+              // HS_U elements at a time: their addresses first, then independent loads
+              // (several row-store accesses in flight per thread), then the updates
+              for (int el = e0; el < e1; el += HS_U) {
+                cdf* p[HS_U];
+                int kk[HS_U], gg[HS_U];
+  #pragma unroll
+                for (int u = 0; u < HS_U; ++u) {
+                  p[u] = row + k;
+                  kk[u] = k;
+                  gg[u] = g;
+                  if (++k > g) {
+                    row += g + 1;
+                    g += CL;
+                    k = j + 1;
+                  }
+                }
+                cdf a[HS_U];
+  #pragma unroll
+                for (int u = 0; u < HS_U; ++u)
+                  if (el + u < e1) a[u] = *p[u];
+  #pragma unroll
+                for (int u = 0; u < HS_U; ++u)
+                  if (el + u < e1) {
+                    cdf x = cdf_lag(a[u], vp[gg[u]], wp[gg[u]], vp[kk[u]], wp[kk[u]]);
+                    if (kk[u] == gg[u]) {
+                      x.ih = 0.f;
+                      x.il = 0.f;
+                    }
+                    *p[u] = x;
+                  }
               }
-              row[k] = a;
-              if (++k > g) {
-                row += g + 1;
-                g += CL;
-                k = j + 1;
-                if (el + 1 < e1) {
-                  vg = vp[g];
-                  wg = wp[g];
+            } else {
+              cdf vg = vp[g], wg = wp[g];
+              for (int el = e0; el < e1; ++el) {
+                cdf a = cdf_lag(row[k], vg, wg, vp[k], wp[k]);
+                if (k == g) {
+                  a.ih = 0.f;
+                  a.il = 0.f;
+                }
+                row[k] = a;
+                if (++k > g) {
+                  row += g + 1;
+                  g += CL;
+                  k = j + 1;
+                  if (el + 1 < e1) {
+                    vg = vp[g];
+                    wg = wp[g];
+                  }
                 }
               }
             }
@@ -912,7 +948,9 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df(const double2* __restrict__ 
         if (i == 0) vi = cdf_add(vi, am);
         vi = cdf_scale(vi, vinv);
         v[j + 1 + i] = vi;
-        if (c == 0) Hv32[(long)j * m + j + 1 + i] = make_float2(vi.rh, vi.ih);  // read by the FP32 back-transform
+        // read by the FP32 back-transform after this kernel: evict-first, so the
+        // row store keeps the L2
+        if (c == 0) __stcs(Hv32 + (long)j * m + j + 1 + i, make_float2(vi.rh, vi.ih));
       }
     }
     __syncthreads();
@@ -938,24 +976,66 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df(const double2* __restrict__ 
         int g = g0 + CL * i;
         int k = j + 1 + (e0 - Pi);
         const cdf* row = S + hs_rowbase(q0 + i, c, CL);
-        bool whole = (e0 == Pi), first = true;
-        cdf acc = cdf_zero();
-        for (int el = e0; el < e1; ++el) {
-          cdf_fma(acc, row[k], v[k]);
-          if (++k > g) {
-            if (whole) pv[g] = acc;
-            else slotF[tid] = acc;
-            first = false;
-            whole = true;
-            acc = cdf_zero();
-            row += g + 1;
-            g += CL;
-            k = j + 1;
+        if constexpr (GS) {
+          bool whole = (e0 == Pi), first = true, pending = false;
+          cdf acc = cdf_zero();
+          for (int el = e0; el < e1; el += HS_U) {
+            const cdf* p[HS_U];
+            int kk[HS_U], gend[HS_U];  // gend: the row an element ends, else -1
+  #pragma unroll
+            for (int u = 0; u < HS_U; ++u) {
+              p[u] = row + k;
+              kk[u] = k;
+              gend[u] = -1;
+              if (++k > g) {
+                gend[u] = g;
+                row += g + 1;
+                g += CL;
+                k = j + 1;
+              }
+            }
+            cdf a[HS_U];
+  #pragma unroll
+            for (int u = 0; u < HS_U; ++u)
+              if (el + u < e1) a[u] = *p[u];
+  #pragma unroll
+            for (int u = 0; u < HS_U; ++u)
+              if (el + u < e1) {
+                cdf_fma(acc, a[u], v[kk[u]]);
+                pending = gend[u] < 0;
+                if (!pending) {
+                  if (whole) pv[gend[u]] = acc;
+                  else slotF[tid] = acc;
+                  first = false;
+                  whole = true;
+                  acc = cdf_zero();
+                }
+              }
           }
-        }
-        if (k != j + 1) {
-          if (first) slotF[tid] = acc;
-          else slotL[tid] = acc;
+          if (pending) {
+            if (first) slotF[tid] = acc;
+            else slotL[tid] = acc;
+          }
+        } else {
+          bool whole = (e0 == Pi), first = true;
+          cdf acc = cdf_zero();
+          for (int el = e0; el < e1; ++el) {
+            cdf_fma(acc, row[k], v[k]);
+            if (++k > g) {
+              if (whole) pv[g] = acc;
+              else slotF[tid] = acc;
+              first = false;
+              whole = true;
+              acc = cdf_zero();
+              row += g + 1;
+              g += CL;
+              k = j + 1;
+            }
+          }
+          if (k != j + 1) {
+            if (first) slotF[tid] = acc;
+            else slotL[tid] = acc;
+          }
         }
       }
       __syncthreads();
@@ -999,34 +1079,85 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df(const double2* __restrict__ 
         int cnt = CP[k + 1] - CP[k];
         int q = hs_qfirst(k, c, CL) + o;
         int g = c + CL * q, base = hs_rowbase(q, c, CL);
-        bool whole = (o == 0), first = true;
-        cdf acc = cdf_zero();
-        for (int el = e0; el < e1; ++el) {
-          cdf_fmac(acc, S[base + k], vown[q]);
-          base += g + 1;
-          g += CL;
-          ++q;
-          if (++o == cnt) {
-            if (whole) pv[k] = cdf_add(pv[k], acc);
-            else slotF[tid] = acc;
-            first = false;
-            whole = true;
-            acc = cdf_zero();
-            if (el + 1 < e1) {
-              do {
-                ++k;
-              } while (CP[k + 1] == CP[k]);
-              cnt = CP[k + 1] - CP[k];
-              q = hs_qfirst(k, c, CL);
-              g = c + CL * q;
-              base = hs_rowbase(q, c, CL);
-              o = 0;
+        if constexpr (GS) {
+          bool whole = (o == 0), first = true, pending = false;
+          cdf acc = cdf_zero();
+          for (int el = e0; el < e1; el += HS_U) {
+            int addr[HS_U], qq[HS_U], kend[HS_U];  // kend: the column an element ends, else -1
+  #pragma unroll
+            for (int u = 0; u < HS_U; ++u) {
+              addr[u] = base + k;
+              qq[u] = q;
+              kend[u] = -1;
+              base += g + 1;
+              g += CL;
+              ++q;
+              if (++o == cnt) {
+                kend[u] = k;
+                if (el + u + 1 < e1) {
+                  do {
+                    ++k;
+                  } while (CP[k + 1] == CP[k]);
+                  cnt = CP[k + 1] - CP[k];
+                  q = hs_qfirst(k, c, CL);
+                  g = c + CL * q;
+                  base = hs_rowbase(q, c, CL);
+                  o = 0;
+                }
+              }
+            }
+            cdf a[HS_U];
+  #pragma unroll
+            for (int u = 0; u < HS_U; ++u)
+              if (el + u < e1) a[u] = S[addr[u]];
+  #pragma unroll
+            for (int u = 0; u < HS_U; ++u)
+              if (el + u < e1) {
+                cdf_fmac(acc, a[u], vown[qq[u]]);
+                pending = kend[u] < 0;
+                if (!pending) {
+                  if (whole) pv[kend[u]] = cdf_add(pv[kend[u]], acc);
+                  else slotF[tid] = acc;
+                  first = false;
+                  whole = true;
+                  acc = cdf_zero();
+                }
+              }
+          }
+          if (pending) {
+            if (first) slotF[tid] = acc;
+            else slotL[tid] = acc;
+          }
+        } else {
+          bool whole = (o == 0), first = true;
+          cdf acc = cdf_zero();
+          for (int el = e0; el < e1; ++el) {
+            cdf_fmac(acc, S[base + k], vown[q]);
+            base += g + 1;
+            g += CL;
+            ++q;
+            if (++o == cnt) {
+              if (whole) pv[k] = cdf_add(pv[k], acc);
+              else slotF[tid] = acc;
+              first = false;
+              whole = true;
+              acc = cdf_zero();
+              if (el + 1 < e1) {
+                do {
+                  ++k;
+                } while (CP[k + 1] == CP[k]);
+                cnt = CP[k + 1] - CP[k];
+                q = hs_qfirst(k, c, CL);
+                g = c + CL * q;
+                base = hs_rowbase(q, c, CL);
+                o = 0;
+              }
             }
           }
-        }
-        if (o != cnt && o != 0) {
-          if (first) slotF[tid] = acc;
-          else slotL[tid] = acc;
+          if (o != cnt && o != 0) {
+            if (first) slotF[tid] = acc;
+            else slotL[tid] = acc;
+          }
         }
       }
       __syncthreads();
@@ -1902,7 +2033,7 @@ static bool hetrd_needs_global_rows(int m, int batch) {
 
 template <int CL, bool DF, bool GS>
 static int launch_hetrd_smem_t(const double2* G, long ldg, long sG, int m, int batch, const EigScratch& e,
-                               cudaStream_t s) {
+                               cudaStream_t s, int b0 = 0) {
   constexpr int NT = DF ? 2 * HS_THREADS : HS_THREADS;
   const size_t smem = hetrd_smem_bytes(m, CL, NT, GS);
   auto kern = DF ? k_hetrd_df<CL, NT, GS> : k_hetrd_smem<CL, GS>;
@@ -1922,7 +2053,7 @@ static int launch_hetrd_smem_t(const double2* G, long ldg, long sG, int m, int b
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, kern, G, ldg, sG, m, (int)hetrd_smem_elems(m, CL), e) != cudaSuccess) {
+  if (cudaLaunchKernelEx(&cfg, kern, G, ldg, sG, m, (int)hetrd_smem_elems(m, CL), e, b0) != cudaSuccess) {
     cudaGetLastError();
     return TSVD_ERR_CUDA;
   }
@@ -1932,12 +2063,12 @@ static int launch_hetrd_smem_t(const double2* G, long ldg, long sG, int m, int b
 
 template <bool DF, bool GS>
 static int launch_hetrd_smem(int CL, const double2* G, long ldg, long sG, int m, int batch, const EigScratch& e,
-                             cudaStream_t s) {
+                             cudaStream_t s, int b0 = 0) {
   switch (CL) {
-    case 8: return launch_hetrd_smem_t<8, DF, GS>(G, ldg, sG, m, batch, e, s);
-    case 4: return launch_hetrd_smem_t<4, DF, GS>(G, ldg, sG, m, batch, e, s);
-    case 2: return launch_hetrd_smem_t<2, DF, GS>(G, ldg, sG, m, batch, e, s);
-    default: return launch_hetrd_smem_t<1, DF, GS>(G, ldg, sG, m, batch, e, s);
+    case 8: return launch_hetrd_smem_t<8, DF, GS>(G, ldg, sG, m, batch, e, s, b0);
+    case 4: return launch_hetrd_smem_t<4, DF, GS>(G, ldg, sG, m, batch, e, s, b0);
+    case 2: return launch_hetrd_smem_t<2, DF, GS>(G, ldg, sG, m, batch, e, s, b0);
+    default: return launch_hetrd_smem_t<1, DF, GS>(G, ldg, sG, m, batch, e, s, b0);
   }
 }
 
@@ -1960,6 +2091,8 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
     TSVD_STAGE("eig_hetrd", s);
     TSVD_TRY((launch_hetrd_smem<kDoubleFloat, false>(CLs, G, ldg, sG, m, batch, e, s)));
   } else if (CLg > 0) {
+    // one launch over all slices: measured faster than waves sized to keep each
+    // wave's rows in L2 (the pass is bound by its instructions, not by L2 misses)
     TSVD_STAGE("eig_hetrd", s);
     TSVD_TRY((launch_hetrd_smem<kDoubleFloat, true>(CLg, G, ldg, sG, m, batch, e, s)));
   } else {
