@@ -36,8 +36,13 @@ C2 = dict(name="image-like 512x512x64 fp32, sigma_i=i^-1.5 full rank, R=50 P=10 
 METRIC = "rank-R T-SVD approximations/s"
 DF_FMA_INSTR = 15  # FP32 instructions per double-float multiply-add (TwoProduct, cross terms, TwoSum, renormalisation)
 # DRAM bytes per launch of a kernel from an ncu capture, valid only while the
-# source file the capture was taken on is unchanged (sha256 prefix of that file).
-NCU_TRAFFIC = {}
+# source file the capture was taken on is unchanged (sha256 prefix of that
+# file); reported as null otherwise.  eig_hetrd: the double-float
+# tridiagonalisation with its rows in L2 for m = 480 on 65 Fourier slices (the
+# eigen-problem of the 2048 x 2048 x 128 workload, captured on a 512 x 512 x 128
+# tensor with the same R, P, q, whose eigen-problem has the same sizes).
+NCU_TRAFFIC = {"eig_hetrd": {"src": "paper_2504_04989_gb300/csrc/eig.cu", "sha16": "ada16423b47d6aa3",
+                             "bytes_per_launch": 6.425457e9 + 10.678448e9}}
 
 
 def peaks_file():
@@ -298,11 +303,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched-count", type=int, default=256,
                     help="tensors of the uneven batch timed after the main workload (0: skip)")
+    ap.add_argument("--n", type=int, default=2048,
+                    help="n1 = n2 of the main workload (smaller cases for profiling; n3, R, P, q unchanged)")
+    ap.add_argument("--quick", action="store_true",
+                    help="only the main path (and its end-to-end and stage times): no other paths, peaks, "
+                         "t-products or batch")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     d = dict(WORKLOAD)
+    if args.n != 2048:
+        d.update(n1=args.n, n2=args.n, name=d["name"].replace("2048x2048", "%dx%d" % (args.n, args.n)))
     d["m"] = min((d["q"] + 1) * (d["R"] + d["P"]), d["n1"], d["n2"])
     if args.impl == "reference":
         return run_reference(args, d, rank, world)
@@ -318,7 +330,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    X = wl.make_c3(seed=rank)                       # float32 (n3, n1, n2), 2.1 GB
+    X = wl.make_c3(seed=rank, n=d["n1"])             # float32 (n3, n1, n2), 2.1 GB at n = 2048
     Xd = torch.from_numpy(X).to(dev)
     if args.precision == "fp64":
         Xd = Xd.double()
@@ -383,14 +395,14 @@ def main():
     dom = max(stages, key=stages.get)
     pk = peaks_file()
     props = torch.cuda.get_device_properties(dev)
-    alu = measure_alu_peaks(torch, dev, stream)
+    alu = measure_alu_peaks(torch, dev, stream) if not args.quick else \
+        {"fp64": None, "fp32": None, "tf32": None, "double_float": None}
 
     def roofline_of(stage):
         work = algorithmic(stage, d, args.precision)
         t = stages[stage] * 1e-3
         if "flops" in work:
-            fp64_stage = args.precision == "fp64" or (stage == "eig_hetrd" and d["m"] > 320)
-            if fp64_stage:
+            if args.precision == "fp64":
                 peak, src = alu["fp64"], "measured here: cuBLAS FP64 GEMM"
             elif stage == "eig_hetrd":
                 peak, src = alu["double_float"], "measured FP32 GEMM rate / 15 instructions per double-float FMA x 2"
@@ -400,7 +412,7 @@ def main():
                 peak, src = alu["fp32"], "measured here: cuBLAS FP32 GEMM (no TF32)"
             a = work["flops"] / t / 1e12
             return {"kernel": stage, "bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s",
-                    "frac": a / peak, "traffic": ncu_traffic(stage), "peak_source": src}
+                    "frac": a / peak if peak else None, "traffic": ncu_traffic(stage), "peak_source": src}
         if "bytes" in work:
             a = work["bytes"] / t / 1e9
             return {"kernel": stage, "bound": "hbm", "achieved": a, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -413,7 +425,7 @@ def main():
     roof["stages"] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in r.items()
                           if kk in ("bound", "achieved", "peak", "unit", "frac")}
                       for k in stages for r in [roofline_of(k)] if r}
-    roof["measured_peaks_tflops"] = {k: round(v, 2) for k, v in alu.items()}
+    roof["measured_peaks_tflops"] = {k: (round(v, 2) if v else None) for k, v in alu.items()}
     roof["sms"] = props.multi_processor_count
 
     # reconstruction errors: this path, the other mixed path, the configuration's
@@ -440,6 +452,18 @@ def main():
         torch.cuda.empty_cache()
 
     X32 = Xd if Xd.dtype == torch.float32 else Xd.float()
+    if args.quick:  # the main path only
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "T-SVD/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                              "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                              "data": "synthetic", "config": {"workload": d["name"], "precision": args.precision},
+                              "e2e": {"value": e2e_value, "unit": "T-SVD/s", "h2d_bytes_per_step": h2d,
+                                      "d2h_bytes_per_step": d2h},
+                              "gpu_launches": launches_timed, "roofline": roof, "paths": paths}), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     for prec in ("tf32", "bf16", "fp32"):
         if prec != args.precision:
             time_path(prec, prec, 3, X32)
