@@ -454,10 +454,60 @@ template int repair_dead<float2>(float2*, long, long, int, int, int, const uint3
 // succeed for any W; the next two passes restore orthogonality to rounding
 // level), each pass preceded by a classical Gram-Schmidt projection against
 // Q_{<i}; dependent columns are then replaced.
+// The FP32 block step with its block Gram and its W R^-1 on tcgen05 (split
+// TF32: FP32-level accuracy): each complex product X Y is real(X) E(Y)^T with
+// the expanded real form E of the thin factor (tc_gemm.cu).  The Gram-Schmidt
+// projections stay on the SIMT GEMM: as long-K products with two 128-column
+// output tiles they stream their split operands twice, measured slower than
+// the SIMT kernel (which runs them at about half of the FP32 peak).
+static int orth_block_tc(int n1, int b, int m, int h, const OrthWs& w, int c, int nb, int block_id, uint64_t seed,
+                         cudaStream_t s) {
+  const OrthTc& t = *w.tc;
+  float2* Q = (float2*)w.Q;
+  float2* W = (float2*)w.W;
+  float2* P = (float2*)w.P;
+  float2* Gs = (float2*)w.G;
+  float2* Mi = (float2*)w.Minv;
+  const long sQ = (long)n1 * m, sW = (long)n1 * b, sP = (long)m * b, sG = (long)b * b;
+  const long sWT = (long)b * t.ldq2, sWr = (long)n1 * t.ldw2, sE = 2L * b * t.ldq2;
+  const size_t sk = 2 * w.splitk_elems;
+  for (int pass = 0; pass < 3; ++pass) {
+    if (c > 0) {
+      TSVD_STAGE("orth_cgs", s);
+      TSVD_TRY(cgemm<float2>(gemm('H', 'N', c, nb, n1, 1.0, Q, m, sQ, W, b, sW, 0.0, P, nb, sP, h), w.splitk, sk, s));
+      TSVD_TRY(cgemm<float2>(gemm('N', 'N', n1, nb, c, -1.0, Q, m, sQ, P, nb, sP, 1.0, W, b, sW, h), w.splitk, sk, s));
+    }
+    {
+      TSVD_STAGE("orth_gram", s);  // G = W^H W: conj(W^T) against E(W) in the conjugating form
+      TSVD_TRY(split_transpose_ld(W, n1, nb, b, sW, h, t.WThi, t.WTlo, t.ldq2, sWT, s));
+      TSVD_TRY(expand_thin_split(W, b, sW, n1, nb, t.Ehi, t.Elo, t.ldq2, sE, h, 1, s));
+      TSVD_TRY(tc_gemm_split(t.WThi, t.WTlo, t.ldq2, sWT, nb, t.Ehi, t.Elo, t.ldq2, sE, 2 * nb, 2 * n1, (float*)Gs,
+                             2L * b, 2L * sG, h, t.err, s));
+    }
+    {
+      TSVD_STAGE("orth_chol", s);
+      TSVD_TRY(chol_inv<float2>(Gs, b, sG, Mi, b, sG, nb, h, pass == 0 ? 1e-5 : 0.0, 1e-7, w.dead, s));
+    }
+    {
+      TSVD_STAGE("orth_trsm", s);  // W R^-1, the last pass straight into its columns of Q
+      TSVD_TRY(split_rows((const float*)W, 2L * b, t.Whi, t.Wlo, t.ldw2, 2 * nb, (long)h * n1, s));
+      TSVD_TRY(expand_thin_split(Mi, b, sG, nb, nb, t.Ehi, t.Elo, t.ldw2, sE, h, 0, s));
+      float* out = (pass < 2) ? (float*)W : (float*)(Q + c);
+      TSVD_TRY(tc_gemm_split(t.Whi, t.Wlo, t.ldw2, sWr, n1, t.Ehi, t.Elo, t.ldw2, sE, 2 * nb, 2 * nb, out,
+                             pass < 2 ? 2L * b : 2L * m, pass < 2 ? 2L * sW : 2L * sQ, h, t.err, s));
+    }
+  }
+  TSVD_STAGE("orth_repair", s);
+  return repair_dead<float2>(Q, m, sQ, n1, c, nb, w.dead, h, seed, block_id, w.dead_count, w.k0, w.nyq, s);
+}
+
 template <typename L>
 int orth_block_cols(int n1, int b, int m, int h, const OrthWs& w, int c, int nb, int block_id, uint64_t seed,
                     cudaStream_t s) {
   using CL = cx_t<L>;
+  if constexpr (std::is_same<L, float>::value) {
+    if (w.tc) return orth_block_tc(n1, b, m, h, w, c, nb, block_id, seed, s);
+  }
   const long sQ = (long)n1 * m, sW = (long)n1 * b, sP = (long)m * b, sG = (long)b * b;
   CL* Q = (CL*)w.Q;
   CL* W = (CL*)w.W;

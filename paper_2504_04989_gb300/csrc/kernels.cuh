@@ -118,6 +118,16 @@ int repair_dead(C* Q, long ldq, long sQ, int n1, int c, int nb, const uint32_t* 
 // [c, c + nb); dependent columns are replaced (repair_dead, counted in
 // *dead_count).  P (m x b), G and Minv (b x b) are scratch; when Qt is set the
 // block is also converted to FP32 there (L = double with FP32 GEMM data).
+// Split-TF32 tensor-core operands of the FP32 block orthonormalisation (its
+// block Gram and W R^-1 on tcgen05 instead of the SIMT GEMMs); per slice:
+struct OrthTc {
+  float *WThi, *WTlo;  // W^T: b rows of 2 n1 floats (leading dim ldq2)
+  float *Whi, *Wlo;    // W as real rows: n1 rows of 2 b floats (leading dim ldw2)
+  float *Ehi, *Elo;    // expanded real forms of the thin factors: 2b rows (leading dim <= ldq2)
+  long ldq2, ldw2;
+  int* err;            // set by a tcgen05 pipeline wait that timed out
+};
+
 struct OrthWs {
   void* Q;
   void* W;
@@ -131,6 +141,7 @@ struct OrthWs {
   size_t splitk_elems;  // in double2 elements
   int k0;               // Fourier slice index of problem 0
   int nyq;              // index of the (real) Nyquist slice, n3/2 for an even n3, else -1
+  const OrthTc* tc;     // FP32: products on tcgen05 (split TF32), or nullptr for the SIMT GEMMs
 };
 template <typename L>
 int orth_block_cols(int n1, int b, int m, int h, const OrthWs& w, int c, int nb, int block_id, uint64_t seed,
@@ -148,13 +159,21 @@ int expand_thin(const float2* Y, long ldy, long sy, int K, int N, void* E, long 
                 bool bf16, cudaStream_t s);
 // rows x cols FP32 rows (leading dim ldx) copied to BF16 or FP32 rows of leading dim ldy (zero padded)
 int copy_rows(const float* x, long ldx, void* y, long ldy, int cols, long rows, bool bf16, cudaStream_t s);
-// split TF32: C = A B^T with A = Ahi + Alo, B = Bhi + Blo (hi*hi + hi*lo + lo*hi), FP32-level accuracy
+// split TF32: C = alpha A B^T + beta C with A = Ahi + Alo, B = Bhi + Blo (hi*hi + hi*lo + lo*hi),
+// FP32-level accuracy
 int tc_gemm_split(const float* Ahi, const float* Alo, long lda, long sA, int M, const float* Bhi, const float* Blo,
-                  long ldb, long sB, int N, int K, float* C, long ldc, long sC, int batch, int* err, cudaStream_t s);
+                  long ldb, long sB, int N, int K, float* C, long ldc, long sC, int batch, int* err, cudaStream_t s,
+                  float alpha = 1.0f, float beta = 0.0f);
 // FP32 rows -> hi (nearest TF32) / lo rows of leading dim ldy, padding zeroed
 int split_rows(const float* x, long ldx, float* hi, float* lo, long ldy, int cols, long rows, cudaStream_t s);
+// columns [0, cols) of FP32 rows -> hi / lo rows (leading dim ldy); other columns untouched
+int split_block(const float* x, long ldx, float* hi, float* lo, long ldy, int cols, long rows, cudaStream_t s);
 // per slice complex X (rows x cols) -> X^T as real rows of 2 rows floats (leading dim ldt), hi / lo
 int split_transpose(const float2* X, int rows, int cols, int batch, float* hi, float* lo, long ldt, cudaStream_t s);
+// the same for a strided block (leading dim ldx, batch stride sx) into rows of leading dim ldt, batch stride st
+// (padding columns are not touched)
+int split_transpose_ld(const float2* X, int rows, int cols, long ldx, long sx, int batch, float* hi, float* lo,
+                       long ldt, long st, cudaStream_t s);
 // expand_thin into FP32 hi / lo parts
 int expand_thin_split(const float2* Y, long ldy, long sy, int K, int N, float* Eh, float* El, long lde, long se,
                       int batch, int mode, cudaStream_t s);

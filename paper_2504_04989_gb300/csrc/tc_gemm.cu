@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
                                                     const __grid_constant__ CUtensorMap tmB,
                                                     const __grid_constant__ CUtensorMap tmA2,
                                                     const __grid_constant__ CUtensorMap tmB2, float* __restrict__ C,
-                                                    long ldc, long sC, int M, int N, int nk, int* __restrict__ err) {
+                                                    long ldc, long sC, int M, int N, int nk, int* __restrict__ err,
+                                                    float alpha, float beta) {
   constexpr bool BF16 = MODE == 1, SPLIT = MODE == 2;
   constexpr int STAGES = tc_stages<MODE>(), NOPS = tc_ops<MODE>();
   extern __shared__ unsigned char tc_raw[];
@@ -216,7 +217,10 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int col = n0 + c0 + j;
-          if (col < N) crow[col] = __uint_as_float(r[j]);
+          if (col < N) {
+            const float v = alpha * __uint_as_float(r[j]);  // C = alpha A B^T + beta C
+            crow[col] = (beta != 0.0f) ? fmaf(beta, crow[col], v) : v;
+          }
         }
       }
     }
@@ -279,14 +283,15 @@ bool tc_gemm_supported(const void* A, long lda, long sA, const void* B, long ldb
 
 template <int MODE>
 static int tc_launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& ta2, const CUtensorMap& tb2,
-                     float* C, long ldc, long sC, int M, int N, int nk, int batch, int* err, cudaStream_t s) {
+                     float* C, long ldc, long sC, int M, int N, int nk, int batch, int* err, cudaStream_t s,
+                     float alpha = 1.0f, float beta = 0.0f) {
   dim3 grid(cdiv(N, TC_BN), cdiv(M, TC_BM), batch);
   if (cudaFuncSetAttribute(k_tc_gemm<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<MODE>()) !=
       cudaSuccess) {
     cudaGetLastError();
     return TSVD_ERR_CUDA;
   }
-  k_tc_gemm<MODE><<<grid, 128, tc_smem<MODE>(), s>>>(ta, tb, ta2, tb2, C, ldc, sC, M, N, nk, err);
+  k_tc_gemm<MODE><<<grid, 128, tc_smem<MODE>(), s>>>(ta, tb, ta2, tb2, C, ldc, sC, M, N, nk, err, alpha, beta);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }
@@ -305,7 +310,8 @@ int tc_gemm(const void* A, long lda, long sA, int M, const void* B, long ldb, lo
 }
 
 int tc_gemm_split(const float* Ahi, const float* Alo, long lda, long sA, int M, const float* Bhi, const float* Blo,
-                  long ldb, long sB, int N, int K, float* C, long ldc, long sC, int batch, int* err, cudaStream_t s) {
+                  long ldb, long sB, int N, int K, float* C, long ldc, long sC, int batch, int* err, cudaStream_t s,
+                  float alpha, float beta) {
   if (M <= 0 || N <= 0 || batch <= 0) return TSVD_OK;
   if (!tc_gemm_supported(Ahi, lda, sA, Bhi, ldb, sB, batch, false) ||
       !tc_gemm_supported(Alo, lda, sA, Blo, ldb, sB, batch, false))
@@ -315,7 +321,7 @@ int tc_gemm_split(const float* Ahi, const float* Alo, long lda, long sA, int M, 
   TSVD_TRY(make_map(&tb, Bhi, N, K, ldb, sB, batch, false));
   TSVD_TRY(make_map(&ta2, Alo, M, K, lda, sA, batch, false));
   TSVD_TRY(make_map(&tb2, Blo, N, K, ldb, sB, batch, false));
-  return tc_launch<2>(ta, tb, ta2, tb2, C, ldc, sC, M, N, (K + 31) / 32, batch, err, s);
+  return tc_launch<2>(ta, tb, ta2, tb2, C, ldc, sC, M, N, (K + 31) / 32, batch, err, s, alpha, beta);
 }
 
 // ---------------------------------------------------------------------------
@@ -441,19 +447,42 @@ int split_rows(const float* x, long ldx, float* hi, float* lo, long ldy, int col
 // per slice: complex X (rows x cols, interleaved, leading dim cols) transposed
 // to XT (cols x rows complex = real rows of 2 rows floats, leading dim ldt),
 // split into hi / lo; 32 x 32 complex tiles through shared memory
-__global__ void k_split_transpose(const float2* __restrict__ X, int rows, int cols, float* __restrict__ hi,
-                                  float* __restrict__ lo, long ldt) {
+// columns [0, cols) of FP32 rows (leading dim ldx) -> hi (nearest TF32) / lo rows of leading dim ldy;
+// the other columns of the destination rows are left as they are
+__global__ void k_split_block(const float* __restrict__ x, long ldx, float* __restrict__ hi, float* __restrict__ lo,
+                              long ldy, int cols, long rows) {
+  const long total = rows * cols;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const long r = i / cols;
+    const long c = i % cols;
+    const float v = x[r * ldx + c];
+    const float h = tf32_hi(v);
+    hi[r * ldy + c] = h;
+    lo[r * ldy + c] = v - h;
+  }
+}
+
+int split_block(const float* x, long ldx, float* hi, float* lo, long ldy, int cols, long rows, cudaStream_t s) {
+  const long total = rows * cols;
+  if (total <= 0) return TSVD_OK;
+  k_split_block<<<(unsigned)std::min<long>(cdiv(total, 256), 8192), 256, 0, s>>>(x, ldx, hi, lo, ldy, cols, rows);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
+__global__ void k_split_transpose(const float2* __restrict__ X, int rows, int cols, long ldx, long sx,
+                                  float* __restrict__ hi, float* __restrict__ lo, long ldt, long st) {
   __shared__ float2 t[32][33];
   const int b = blockIdx.z;
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  const float2* Xb = X + (long)b * rows * cols;
+  const float2* Xb = X + (long)b * sx;
   for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
     const int r = r0 + rr, c = c0 + threadIdx.x;
-    t[rr][threadIdx.x] = (r < rows && c < cols) ? Xb[(long)r * cols + c] : make_float2(0.f, 0.f);
+    t[rr][threadIdx.x] = (r < rows && c < cols) ? Xb[(long)r * ldx + c] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  float* hb = hi + (long)b * cols * ldt;
-  float* lb = lo + (long)b * cols * ldt;
+  float* hb = hi + (long)b * st;
+  float* lb = lo + (long)b * st;
   for (int cc = threadIdx.y; cc < 32; cc += blockDim.y) {
     const int c = c0 + cc, r = r0 + threadIdx.x;
     if (c < cols && r < rows) {
@@ -479,7 +508,17 @@ int split_transpose(const float2* X, int rows, int cols, int batch, float* hi, f
       return TSVD_ERR_CUDA;
   }
   dim3 grid(cdiv(cols, 32), cdiv(rows, 32), batch), block(32, 8);
-  k_split_transpose<<<grid, block, 0, s>>>(X, rows, cols, hi, lo, ldt);
+  k_split_transpose<<<grid, block, 0, s>>>(X, rows, cols, cols, (long)rows * cols, hi, lo, ldt, (long)cols * ldt);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
+int split_transpose_ld(const float2* X, int rows, int cols, long ldx, long sx, int batch, float* hi, float* lo,
+                       long ldt, long st, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0 || batch <= 0) return TSVD_OK;
+  if (batch > 65535) return TSVD_ERR_UNSUPPORTED;
+  dim3 grid(cdiv(cols, 32), cdiv(rows, 32), batch), block(32, 8);
+  k_split_transpose<<<grid, block, 0, s>>>(X, rows, cols, ldx, sx, hi, lo, ldt, st);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }

@@ -185,6 +185,7 @@ static int tqr_factor(const TqrDims& d, TqrWs<T>& w, const cx_t<T>* M, cudaStrea
   o.splitk_elems = w.splitk_elems;
   o.k0 = 0;
   o.nyq = (d.n3 % 2 == 0) ? d.n3 / 2 : -1;
+  o.tc = nullptr;
   for (int c = 0; c < p; c += b) {
     const int nb = std::min(b, p - c);
     TSVD_TRY(copy_cx<C>(M + c, Nc, (long)Mr * Nc, w.W, b, (long)Mr * b, Mr, nb, h, s));

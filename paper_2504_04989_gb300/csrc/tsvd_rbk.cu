@@ -38,6 +38,7 @@ struct RbkDims {
   int k0;       // first Fourier slice processed (h slices from k0 on)
   int fourier;  // the caller passes the Fourier slices (tsvd_rbk_fourier): no transforms here
   int tc;    // basis-building products on tcgen05 in one pass: 0 none, 1 TF32, 2 BF16
+  int tco;   // FP32 block orthonormalisation with its Gram and W R^-1 on tcgen05 (split TF32)
   int tc3;   // FP32-accurate products on tcgen05 (split TF32): FP32 data unless TSVD_FLAG_SIMT
   int alg1;  // Alg. 1 (power iteration, last block only) instead of Alg. 2
   int mp;    // basis columns used by the projection: m, or R+P with TSVD_FLAG_QTRUNC
@@ -62,6 +63,9 @@ static int rbk_dims(int n1, int n2, int n3, const tsvd_params* p, RbkDims* d) {
   d->tc = (p->precision == TSVD_MIXED_TF32) ? 1 : (p->precision == TSVD_MIXED_BF16) ? 2 : 0;
   d->alg1 = (p->flags & TSVD_FLAG_ALG1) ? 1 : 0;
   d->tc3 = (p->precision != TSVD_FP64 && !(p->flags & TSVD_FLAG_SIMT)) ? 1 : 0;
+  // measured: faster from n1 ~ 1024 on (2048 x 2048 x 128: 13.4 -> 7.8 ms); at n1 = 512 the SIMT
+  // kernels win (0.64 -> 1.18 ms), the blocks being too small to fill the tensor-core tiles
+  d->tco = (d->tc3 && !(p->flags & TSVD_FLAG_FP64_QR) && n1 >= 1024) ? 1 : 0;
   if (p->flags & TSVD_FLAG_SIMT) d->tc = 0;
   long m = (long)(d->alg1 ? 1 : p->q + 1) * d->b;
   m = std::min<long>(m, std::min(n1, n2));
@@ -119,6 +123,7 @@ struct RbkWs {
   double2* T1;    // C^H Um (h x n2 x R)
   double2* CpH;   // projected C^H (h x n2 x mp)
   int* acc;       // accepted count per slice
+  OrthTc otc;     // tcgen05 operands of the FP32 block orthonormalisation (d.tco)
   size_t bytes;
 };
 
@@ -170,6 +175,19 @@ static RbkWs<T> carve_rbk(void* base, const RbkDims& d) {
     w.tc_err = cv.take<int>(4);
     if (d.tc == 2) w.Aop = cv.take<uint16_t>(h * d.n1 * w.lda);
   }
+  w.otc = OrthTc{};
+  if (d.tco) {
+    OrthTc& t = w.otc;
+    t.ldq2 = (2L * d.n1 + 7) / 8 * 8;
+    t.ldw2 = (2L * d.b + 7) / 8 * 8;
+    t.WThi = cv.take<float>(h * d.b * t.ldq2);
+    t.WTlo = cv.take<float>(h * d.b * t.ldq2);
+    t.Whi = cv.take<float>(h * d.n1 * t.ldw2);
+    t.Wlo = cv.take<float>(h * d.n1 * t.ldw2);
+    t.Ehi = cv.take<float>(h * 2 * (size_t)d.b * t.ldq2);
+    t.Elo = cv.take<float>(h * 2 * (size_t)d.b * t.ldq2);
+    t.err = w.tc_err;
+  }
   w.splitk_elems = 8 * h * (size_t)d.m * std::max(d.b, 64);
   w.splitk = cv.take<double2>(w.splitk_elems);
   w.lamF = nullptr;
@@ -206,6 +224,7 @@ static int orth_block(const RbkDims& d, RbkWs<T>& w, int c, int nb, int block_id
   o.splitk_elems = w.splitk_elems;
   o.k0 = d.k0;
   o.nyq = (d.n3 % 2 == 0) ? d.n3 / 2 : -1;
+  o.tc = d.tco ? &w.otc : nullptr;
   return orth_block_cols<L>(d.n1, d.b, d.m, d.h, o, c, nb, block_id, seed, s);
 }
 

@@ -253,3 +253,14 @@ def test_alg1_against_oracle(api, orc, n1, n2, n3, R, P, q, precision):
     e1 = api.tsvd_error(dev(Xin, dt), U1, S1, V1).item()
     e2 = api.tsvd_error(dev(Xin, dt), U2, S2, V2).item()
     assert e2 <= e1 * (1 + (1e-10 if precision == "fp64" else 1e-4)), (e1, e2)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
+def test_tensor_core_orthonormalisation_shapes(api, orc, precision):
+    """From n1 = 1024 on, the FP32 block orthonormalisation runs its block Gram
+    and W R^-1 on tcgen05 (split TF32): parity with the oracle on every slice
+    of a 1040 x 300 x 6 tensor (ragged tiles: n1 not a multiple of 128,
+    b = 30 and a last block of 30 columns)."""
+    X = wl.low_tubal_rank(1040, 300, 6, np.arange(1, 301) ** -1.0, noise_std=1e-4, seed=77)
+    om = wl.omega(300, 30, 6, seed=78)
+    check_against_oracle(api, orc, X, 20, 10, 2, precision, omega=om, sig_floor=1e-6)
