@@ -280,7 +280,31 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_rfft3_fft(const T* __restric
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long e0 = (long)blockIdx.x * TT;
   for (int p = threadIdx.x; p < n; p += blockDim.x) tw[p] = twiddle<T>(p, n, -1);
-  {
+  if (sizeof(T) == 4 && (plane & 3) == 0 && ((uintptr_t)X & 15) == 0 && e0 + TT <= plane) {
+    // whole tile, FP32: 16-byte loads of four consecutive tubes, FFT_LOADS in flight per thread
+    const int q4 = TT / 4, total = n * q4;
+    for (int base = threadIdx.x; base < total; base += FFT_LOADS * blockDim.x) {
+      float4 v[FFT_LOADS];
+#pragma unroll
+      for (int u = 0; u < FFT_LOADS; ++u) {
+        const int idx = base + u * blockDim.x;
+        const int t = idx / q4, e = 4 * (idx - t * q4);
+        v[u] = (idx < total) ? __ldg((const float4*)(X + (long)t * plane + e0 + e)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < FFT_LOADS; ++u) {
+        const int idx = base + u * blockDim.x;
+        if (idx < total) {
+          const int t = idx / q4, e = 4 * (idx - t * q4);
+          T* d = itile + t * LD + e;
+          d[0] = (T)v[u].x;
+          d[1] = (T)v[u].y;
+          d[2] = (T)v[u].z;
+          d[3] = (T)v[u].w;
+        }
+      }
+    }
+  } else {
     // FFT_LOADS independent loads in flight per thread (memory-level parallelism)
     const int total = n * TT;
     for (int base = threadIdx.x; base < total; base += FFT_LOADS * blockDim.x) {
@@ -323,10 +347,20 @@ __global__ void __launch_bounds__(FFT_WARPS * 32) k_rfft3_fft(const T* __restric
     __syncwarp();
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < h * TT; idx += blockDim.x) {
-    const int k = idx / TT, e = idx - k * TT;
-    const long ge = e0 + e;
-    if (ge < plane) Xh[(long)k * plane + ge] = otile[k * LD + e];
+  if (sizeof(T) == 4 && (plane & 1) == 0 && ((uintptr_t)Xh & 15) == 0 && e0 + TT <= plane) {
+    // whole tile, FP32: 16-byte stores of two consecutive complex values
+    const int q2 = TT / 2;
+    for (int idx = threadIdx.x; idx < h * q2; idx += blockDim.x) {
+      const int k = idx / q2, e = 2 * (idx - k * q2);
+      const C a = otile[k * LD + e], c = otile[k * LD + e + 1];
+      *(float4*)(Xh + (long)k * plane + e0 + e) = make_float4((float)a.x, (float)a.y, (float)c.x, (float)c.y);
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < h * TT; idx += blockDim.x) {
+      const int k = idx / TT, e = idx - k * TT;
+      const long ge = e0 + e;
+      if (ge < plane) Xh[(long)k * plane + ge] = otile[k * LD + e];
+    }
   }
 }
 
