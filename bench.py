@@ -504,7 +504,7 @@ def main():
                                  ("256x20x100*20x256x100", 256, 20, 256, 100)):
         fl = 8.0 * a1 * a2 * a4 * (a3 // 2 + 1)
         row = {}
-        for prec in ("fp64", "fp32", "tf32", "bf16"):
+        for prec in ("fp64", "fp32", "tf32x3", "tf32", "bf16"):
             dt = torch.float64 if prec == "fp64" else torch.float32
             A = torch.randn(a3, a1, a2, device=dev, dtype=dt)
             B = torch.randn(a3, a2, a4, device=dev, dtype=dt)

@@ -53,7 +53,9 @@ typedef enum {
   TSVD_FP32 = 1,       /* FFT, complex GEMMs and the block orthonormalisation in FP32 (FP32
                           accumulation); the Gram of C and the small eigen-solve in FP64 */
   TSVD_MIXED_TF32 = 2, /* Krylov products on tcgen05 TF32, FP32 accumulation; rest as TSVD_FP32 */
-  TSVD_MIXED_BF16 = 3  /* Krylov products on tcgen05 BF16, FP32 accumulation; rest as TSVD_FP32 */
+  TSVD_MIXED_BF16 = 3, /* Krylov products on tcgen05 BF16, FP32 accumulation; rest as TSVD_FP32 */
+  TSVD_SPLIT_TF32 = 4  /* tprod only: float arrays, the slice products on tcgen05 in split TF32
+                          (x = hi + lo, hi*hi + hi*lo + lo*hi, operands carried to ~22 bits) */
 } tsvd_precision;
 
 /* ---- parameters of Alg. 2 (Sec. 3): target tubal rank R, oversampling P,

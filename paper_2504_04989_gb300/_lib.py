@@ -10,13 +10,14 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtsvd.so")
 
-TSVD_FP64, TSVD_FP32, TSVD_MIXED_TF32, TSVD_MIXED_BF16 = 0, 1, 2, 3
+TSVD_FP64, TSVD_FP32, TSVD_MIXED_TF32, TSVD_MIXED_BF16, TSVD_SPLIT_TF32 = 0, 1, 2, 3, 4
 TSVD_FLAG_FP64_QR = 1
 TSVD_FLAG_ALG1 = 2
 TSVD_FLAG_SIMT = 4
 TSVD_FLAG_QTRUNC = 8
 TSVD_FLAG_DEFLATE = 16
-PRECISIONS = {"fp64": TSVD_FP64, "fp32": TSVD_FP32, "tf32": TSVD_MIXED_TF32, "bf16": TSVD_MIXED_BF16}
+PRECISIONS = {"fp64": TSVD_FP64, "fp32": TSVD_FP32, "tf32": TSVD_MIXED_TF32, "bf16": TSVD_MIXED_BF16,
+              "tf32x3": TSVD_SPLIT_TF32}
 
 ERRORS = {0: "ok", -1: "invalid argument", -2: "workspace too small", -3: "CUDA failure",
           -4: "unsupported size or mode", -5: "eigen solve did not converge",

@@ -12,7 +12,8 @@ import torch
 
 from . import _lib
 
-_DT = {"fp64": torch.float64, "fp32": torch.float32, "tf32": torch.float32, "bf16": torch.float32}
+_DT = {"fp64": torch.float64, "fp32": torch.float32, "tf32": torch.float32, "bf16": torch.float32,
+       "tf32x3": torch.float32}
 
 
 def _prec(precision):

@@ -17,12 +17,12 @@ namespace tsvd {
 
 static int check_prec(int precision) {
   if (precision == TSVD_FP64 || precision == TSVD_FP32) return TSVD_OK;
-  if (precision == TSVD_MIXED_TF32 || precision == TSVD_MIXED_BF16) return TSVD_ERR_UNSUPPORTED;
+  if (precision >= TSVD_MIXED_TF32 && precision <= TSVD_SPLIT_TF32) return TSVD_ERR_UNSUPPORTED;
   return TSVD_ERR_INVALID_ARG;
 }
 
 static int check_prec_fwd(int precision) {
-  if (precision >= TSVD_FP64 && precision <= TSVD_MIXED_BF16) return TSVD_OK;
+  if (precision >= TSVD_FP64 && precision <= TSVD_SPLIT_TF32) return TSVD_OK;
   return TSVD_ERR_INVALID_ARG;
 }
 
@@ -95,15 +95,18 @@ static int tprod_run(const T* A, const T* B, T* Cout, int n1, int n2, int n4, in
 // Tensor-core forward: the slice products as one real GEMM per slice,
 // real(A_k) (n1 x 2n2) times E(B_k)^T, E(B_k) (2n4 x 2n2) the expanded real
 // form of B_k; the interleaved complex product comes out directly.
+// MODE 0: one TF32 pass, 1: BF16, 2: split TF32 (hi*hi + hi*lo + lo*hi, operands to ~22 bits)
 struct TprodTcWs {
   float2 *Ah, *Bh, *Ch;
-  void* Aop;  // operand copy (BF16, or FP32 with padded rows) or null
+  void* Aop;  // operand copy (BF16, FP32 with padded rows, or the TF32 hi part) or null
+  float* Alo; // split TF32: the lo part of the operand
   void* E;
+  float* Elo; // split TF32: the lo part of the expanded B
   int* err;
   long lda, lde;
   size_t bytes;
 };
-static TprodTcWs carve_tprod_tc(void* base, int n1, int n2, int n4, int n3, bool bf16) {
+static TprodTcWs carve_tprod_tc(void* base, int n1, int n2, int n4, int n3, int mode) {
   Carver cv(base);
   const size_t h = n3 / 2 + 1;
   TprodTcWs w;
@@ -113,17 +116,20 @@ static TprodTcWs carve_tprod_tc(void* base, int n1, int n2, int n4, int n3, bool
   w.Ah = cv.take<float2>(h * n1 * n2);
   w.Bh = cv.take<float2>(h * n2 * n4);
   w.Ch = cv.take<float2>(h * n1 * n4);
-  const bool copy = bf16 || (k2 % 4 != 0);
+  const bool copy = mode != 0 || (k2 % 4 != 0);
   w.Aop = copy ? cv.take<float>(h * n1 * w.lda) : nullptr;  // big enough for either element type
+  w.Alo = (mode == 2) ? cv.take<float>(h * n1 * w.lda) : nullptr;
   w.E = cv.take<float>(h * 2 * (size_t)n4 * w.lde);
+  w.Elo = (mode == 2) ? cv.take<float>(h * 2 * (size_t)n4 * w.lde) : nullptr;
   w.err = cv.take<int>(4);
   w.bytes = cv.bytes();
   return w;
 }
 
-static int tprod_tc_run(const float* A, const float* B, float* Cout, int n1, int n2, int n4, int n3, bool bf16,
+static int tprod_tc_run(const float* A, const float* B, float* Cout, int n1, int n2, int n4, int n3, int mode,
                         void* ws, cudaStream_t s) {
-  TprodTcWs w = carve_tprod_tc(ws, n1, n2, n4, n3, bf16);
+  const bool bf16 = mode == 1;
+  TprodTcWs w = carve_tprod_tc(ws, n1, n2, n4, n3, mode);
   const int h = n3 / 2 + 1;
   const long k2 = 2L * n2;
   {
@@ -133,17 +139,28 @@ static int tprod_tc_run(const float* A, const float* B, float* Cout, int n1, int
   }
   {
     TSVD_STAGE("tprod_expand", s);
-    TSVD_TRY(expand_thin(w.Bh, n4, (long)n2 * n4, n2, n4, w.E, w.lde, 2L * n4 * w.lde, h, 0, bf16, s));
-    if (w.Aop)  // BF16 operand, or FP32 rows padded to 16 bytes
-      TSVD_TRY(copy_rows((const float*)w.Ah, k2, w.Aop, w.lda, (int)k2, (long)h * n1, bf16, s));
+    if (mode == 2) {  // hi / lo parts of both operands
+      TSVD_TRY(expand_thin_split(w.Bh, n4, (long)n2 * n4, n2, n4, (float*)w.E, w.Elo, w.lde, 2L * n4 * w.lde, h, 0,
+                                 s));
+      TSVD_TRY(split_rows((const float*)w.Ah, k2, (float*)w.Aop, w.Alo, w.lda, (int)k2, (long)h * n1, s));
+    } else {
+      TSVD_TRY(expand_thin(w.Bh, n4, (long)n2 * n4, n2, n4, w.E, w.lde, 2L * n4 * w.lde, h, 0, bf16, s));
+      if (w.Aop)  // BF16 operand, or FP32 rows padded to 16 bytes
+        TSVD_TRY(copy_rows((const float*)w.Ah, k2, w.Aop, w.lda, (int)k2, (long)h * n1, bf16, s));
+    }
     if (cudaMemsetAsync(w.err, 0, sizeof(int), s) != cudaSuccess) return TSVD_ERR_CUDA;
   }
   {
     TSVD_STAGE("tprod_gemm_tc", s);
     const void* Aop = w.Aop ? w.Aop : (const void*)w.Ah;
     const long lda = w.Aop ? w.lda : k2;
-    TSVD_TRY(tc_gemm(Aop, lda, (long)n1 * lda, n1, w.E, w.lde, 2L * n4 * w.lde, 2 * n4, (int)k2, (float*)w.Ch,
-                     2L * n4, 2L * n1 * n4, h, bf16, w.err, s));
+    if (mode == 2)
+      TSVD_TRY(tc_gemm_split((const float*)w.Aop, w.Alo, w.lda, (long)n1 * w.lda, n1, (const float*)w.E, w.Elo,
+                             w.lde, 2L * n4 * w.lde, 2 * n4, (int)k2, (float*)w.Ch, 2L * n4, 2L * n1 * n4, h, w.err,
+                             s));
+    else
+      TSVD_TRY(tc_gemm(Aop, lda, (long)n1 * lda, n1, w.E, w.lde, 2L * n4 * w.lde, 2 * n4, (int)k2, (float*)w.Ch,
+                       2L * n4, 2L * n1 * n4, h, bf16, w.err, s));
   }
   {
     TSVD_STAGE("tprod_irfft", s);
@@ -271,7 +288,7 @@ extern "C" int tprod_workspace_size(int n1, int n2, int n4, int n3, int precisio
   TSVD_TRY(check_prec_fwd(precision));
   if (precision == TSVD_FP64) *bytes = carve_tprod<double>(nullptr, n1, n2, n4, n3).bytes;
   else if (precision == TSVD_FP32) *bytes = carve_tprod<float>(nullptr, n1, n2, n4, n3).bytes;
-  else *bytes = carve_tprod_tc(nullptr, n1, n2, n4, n3, precision == TSVD_MIXED_BF16).bytes;
+  else *bytes = carve_tprod_tc(nullptr, n1, n2, n4, n3, precision - TSVD_MIXED_TF32).bytes;
   return TSVD_OK;
 }
 
@@ -286,7 +303,8 @@ extern "C" int tprod(const void* A, const void* B, void* C, int n1, int n2, int 
     return tprod_run<double>((const double*)A, (const double*)B, (double*)C, n1, n2, n4, n3, ws, s);
   if (precision == TSVD_FP32)
     return tprod_run<float>((const float*)A, (const float*)B, (float*)C, n1, n2, n4, n3, ws, s);
-  return tprod_tc_run((const float*)A, (const float*)B, (float*)C, n1, n2, n4, n3, precision == TSVD_MIXED_BF16, ws,
+  // TF32 (mode 0), BF16 (1), split TF32 (2) on tcgen05
+  return tprod_tc_run((const float*)A, (const float*)B, (float*)C, n1, n2, n4, n3, precision - TSVD_MIXED_TF32, ws,
                       s);
 }
 

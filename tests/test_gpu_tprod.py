@@ -139,3 +139,26 @@ def test_tprod_tensor_core(api, orc, n1, n2, n4, n3, precision, tol):
     # and element-wise against the scale of the summands
     scale = np.sqrt(n2 * n3) * np.max(np.abs(A32)) * np.max(np.abs(B32))
     assert np.max(np.abs(C - ref)) < 10 * tol * scale
+
+
+@pytest.mark.parametrize("n1,n2,n4,n3", [(128, 128, 64, 4), (200, 130, 150, 7), (256, 512, 65, 16)])
+def test_tprod_split_tf32_tensor_core(api, orc, n1, n2, n4, n3):
+    """The split-TF32 t-product ("tf32x3": x = hi + lo, hi*hi + hi*lo + lo*hi on
+    tcgen05) against the oracle, in the form of the TF32 / BF16 test above: a
+    normwise relative error of 2e-5 (one TF32 pass: 3e-3), element-wise 10x
+    that against the scale of the summands.  It is not held to the FP32 SIMT
+    bound: its operands carry ~22 bits and the tensor-core accumulation of the
+    three partial products loses a few more (measured: 9e-6 relative at the
+    worst element of the 256 x 512 x 65 x 16 case)."""
+    A, B = rand(n3, n1, n2), rand(n3, n2, n4)
+    A32, B32 = A.astype(np.float32), B.astype(np.float32)
+    with api.profile() as pr:
+        C = api.tprod(dev(A32, torch.float32), dev(B32, torch.float32), "tf32x3")
+        torch.cuda.synchronize()
+    assert "tprod_gemm_tc" in pr.stages
+    C = C.cpu().numpy()
+    ref = orc.tprod(A32.astype(np.float64), B32.astype(np.float64))
+    rel = np.linalg.norm((C - ref).ravel()) / np.linalg.norm(ref.ravel())
+    assert rel < 2e-5, rel
+    scale = np.sqrt(n2 * n3) * np.max(np.abs(A32)) * np.max(np.abs(B32))
+    assert np.max(np.abs(C - ref)) < 10 * 2e-5 * scale
