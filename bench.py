@@ -410,7 +410,7 @@ def main():
                 peak, src = alu["tf32"], "measured here: cuBLAS TF32 GEMM"
             elif stage in ("orth_gram", "orth_trsm") and d["n1"] >= 1024:
                 # tcgen05 in split TF32 from n1 = 1024 on: three TF32 products per FP32-accurate one
-                peak, src = alu["tf32"] / 3, "measured here: cuBLAS TF32 GEMM / 3 (split TF32)"
+                peak, src = alu["tf32"] and alu["tf32"] / 3, "measured here: cuBLAS TF32 GEMM / 3 (split TF32)"
             else:
                 peak, src = alu["fp32"], "measured here: cuBLAS FP32 GEMM (no TF32)"
             a = work["flops"] / t / 1e12

@@ -1235,6 +1235,304 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df(const double2* __restrict__ 
   }
 }
 
+// ---------------------------------------------------------------------------
+// One-pass double-float reduction with the rows in global memory (L2): the
+// same steps as k_hetrd_df (the update of step j-1 applied lazily in step j),
+// but its three sweeps of the trailing triangle (the pending rank-2 update,
+// the row and the column matrix-vector passes) become one.  Warps take strips
+// of HF_SR consecutive own rows and walk them 32 columns at a time, lane l on
+// column k0 + l (512-byte coalesced loads); each element is updated, stored
+// once and used twice:
+//   row part     p_g += a_gk v_k              (k <= g; lane-local over the
+//                                              strip, reduced across lanes once
+//                                              per strip)
+//   column part  p_k += conj(a_gk) v_g        (k < g; the lane's column, summed
+//                                              over the strip's rows, added to a
+//                                              warp-private partial of p)
+// The warp partials are summed per column after the sweep.  Strips go to
+// warps in snake order (w, 2 NW - 1 - w, 2 NW + w, ...) since their lengths
+// grow with the row index.
+// ---------------------------------------------------------------------------
+constexpr int HF_SR = 4;  // own rows per strip
+
+static size_t hetrd_df1_smem_bytes(int m, int nt) {
+  return (size_t)(5 + nt / 32) * (size_t)m * sizeof(double2);  // v[2], w[2], p, warp partials [NW]
+}
+
+template <int CL, int NT>
+__global__ void __launch_bounds__(NT, 1) k_hetrd_df1(const double2* __restrict__ G, long ldg, long sG, int m,
+                                                     int s_elems, EigScratch e, int b0) {
+  extern __shared__ __align__(16) cdf dsm[];
+  constexpr int NW = NT / 32;
+  static_assert(HF_SR == 4, "the row-sum reduction below is written for strips of four rows");
+  cdf* S = (cdf*)e.Sg + (long)blockIdx.x * s_elems;  // own rows, packed, private to this CTA
+  cdf* bufV = dsm;                                   // [2][m] v of this and of the previous step
+  cdf* bufW = bufV + 2 * m;                          // [2][m] w
+  cdf* pv = bufW + 2 * m;                            // [m] this CTA's part of p
+  cdf* cpart = pv + m;                               // [NW][m] column parts of p, one per warp
+  __shared__ dfl red[NW];
+  __shared__ int s_exp;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int c = (CL > 1) ? (int)cluster.block_rank() : 0;
+  const int b = b0 + (int)blockIdx.x / CL;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  G += (long)b * sG;
+  float2* Hv32 = (float2*)e.Hv + (long)b * m * m;
+  const int nq = hs_own_rows(m, c, CL);
+
+  // power-of-two scale from the largest diagonal entry (identical in every CTA)
+  {
+    double mx = 0;
+    for (int i = tid; i < m; i += NT) mx = fmax(mx, fabs(__ldcg(G + (long)i * ldg + i).x));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ double wmx[NW];
+    if (lane == 0) wmx[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0;
+      for (int w = 0; w < NW; ++w) t = fmax(t, wmx[w]);
+      int ex = 0;
+      if (t > 0 && isfinite(t)) frexp(t, &ex);
+      s_exp = ex;
+    }
+    __syncthreads();
+  }
+  const int ex = s_exp;
+  for (int q = warp; q < nq; q += NW) {
+    const int g = c + CL * q;
+    const double2* src = G + (long)g * ldg;
+    cdf* dst = S + hs_rowbase(q, c, CL);
+    for (int k = lane; k <= g; k += 32) {
+      const double2 x = __ldcg(src + k);
+      dst[k] = cdf_from(make_double2(ldexp(x.x, -ex), ldexp(x.y, -ex)));
+    }
+  }
+  for (int i = tid; i < (5 + NW) * m; i += NT) bufV[i] = cdf_zero();
+  if (CL > 1) cluster.sync();
+  else __syncthreads();
+
+  for (int j = 0; j < m - 1; ++j) {
+    const int cur = j & 1;
+    cdf* v = bufV + cur * m;
+    cdf* w = bufW + cur * m;
+    const cdf* vp = bufV + (cur ^ 1) * m;
+    const cdf* wp = bufW + (cur ^ 1) * m;
+    const bool lag = j > 0;
+    // column j of A^(j) (the pending update applied) to every CTA's v; the diagonal d_j
+    {
+      const cdf vpj = vp[j], wpj = wp[j];
+      for (int q = hs_qfirst(j, c, CL) + tid; q < nq; q += NT) {
+        const int g = c + CL * q;
+        cdf a = S[hs_rowbase(q, c, CL) + j];
+        if (lag) a = cdf_lag(a, vp[g], wp[g], vpj, wpj);
+#pragma unroll
+        for (int rr = 0; rr < CL; ++rr) {
+          cdf* dst = (CL > 1) ? cluster.map_shared_rank(v, rr) : v;
+          dst[g] = a;
+        }
+      }
+      if (tid == 0 && (j % CL) == c) {
+        const cdf sj = S[hs_rowbase((j - c) / CL, c, CL) + j];
+        dfl t = cre(sj);
+        t = df_fma(t, df_neg(cre(vpj)), cre(wpj));
+        t = df_fma(t, df_neg(cim(vpj)), cim(wpj));
+        t = df_fma(t, df_neg(cre(vpj)), cre(wpj));
+        t = df_fma(t, df_neg(cim(vpj)), cim(wpj));
+        e.d[(long)b * m + j] = ldexp(df_to(t), ex);
+      }
+    }
+    if (CL > 1) cluster.sync();
+    else __syncthreads();
+    const int n = m - j - 1;
+    // the reflector: |x|^2 by the whole block (fixed order, so both CTAs agree), then every
+    // thread forms -alpha = e^{i arg x0} |x| and 1 / sqrt(2 |x| (|x| + |x0|)) itself
+    {
+      const cdf x0 = v[j + 1];
+      dfl t{0.f, 0.f};
+      for (int i = tid; i < n; i += NT) {
+        const cdf x = v[j + 1 + i];
+        t = df_fma(t, cre(x), cre(x));
+        t = df_fma(t, cim(x), cim(x));
+      }
+      const dfl nrm2d = df_block_sum(t, red);
+      cdf am = cdf_zero();  // -alpha
+      dfl vinv{0.f, 0.f};
+      if (nrm2d.hi > 0.f) {
+        const dfl nrm = df_sqrt_nodiv(nrm2d);
+        const dfl ax2 = df_fma(df_fma(dfl{0.f, 0.f}, cre(x0), cre(x0)), cim(x0), cim(x0));
+        dfl phr{1.f, 0.f}, phi{0.f, 0.f}, ax0{0.f, 0.f};
+        if (ax2.hi > 0.f) {
+          const dfl iax = df_rsqrt(ax2);  // 1 / |x0|
+          ax0 = df_mul(ax2, iax);
+          phr = df_mul(cre(x0), iax);
+          phi = df_mul(cim(x0), iax);
+        }
+        am = cdf_make(df_mul(phr, nrm), df_mul(phi, nrm));
+        vinv = df_rsqrt(df_mul(df_add(nrm, nrm), df_add(nrm, ax0)));
+      }
+      if (tid == 0 && c == 0) {
+        const double2 al = cdf_to(am);
+        e.alpha[(long)b * m + j] = make_double2(-ldexp(al.x, ex), -ldexp(al.y, ex));
+      }
+      for (int i = tid; i < n; i += NT) {
+        cdf vi = v[j + 1 + i];
+        if (i == 0) vi = cdf_add(vi, am);
+        vi = cdf_scale(vi, vinv);
+        v[j + 1 + i] = vi;
+        // read by the FP32 back-transform after this kernel: evict-first, so the
+        // row store keeps the L2
+        if (c == 0) __stcs(Hv32 + (long)j * m + j + 1 + i, make_float2(vi.rh, vi.ih));
+      }
+    }
+    __syncthreads();
+
+    // the sweep: pending update, store, row and column parts of p = A^(j) v
+    const int q0 = hs_qfirst(j, c, CL);
+    const int nstrip = (max(0, nq - q0) + HF_SR - 1) / HF_SR;
+    cdf* cp = cpart + warp * m;
+    for (int s0 = 0; s0 < nstrip; s0 += NW) {
+      const int s = s0 + (((s0 / NW) & 1) ? NW - 1 - warp : warp);  // snake order
+      if (s >= nstrip) continue;
+      const int qs = q0 + s * HF_SR;
+      int gr[HF_SR];
+      cdf* rowp[HF_SR];
+#pragma unroll
+      for (int r = 0; r < HF_SR; ++r) {
+        const int q = min(qs + r, nq - 1);
+        gr[r] = (qs + r < nq) ? c + CL * q : -1;  // -1: no row (past the last own row)
+        rowp[r] = S + hs_rowbase(q, c, CL);
+      }
+      const int glast = c + CL * min(qs + HF_SR - 1, nq - 1);
+      cdf racc[HF_SR];
+#pragma unroll
+      for (int r = 0; r < HF_SR; ++r) racc[r] = cdf_zero();
+      for (int k0 = j + 1; k0 <= glast; k0 += 32) {
+        const int k = k0 + lane;
+        cdf a[HF_SR];
+#pragma unroll
+        for (int r = 0; r < HF_SR; ++r)
+          if (k <= gr[r]) a[r] = rowp[r][k];
+        if (k <= glast) {
+          const cdf vk = v[k];
+          cdf vpk = cdf_zero(), wpk = cdf_zero();
+          if (lag) {
+            vpk = vp[k];
+            wpk = wp[k];
+          }
+          cdf cacc = cdf_zero();
+#pragma unroll
+          for (int r = 0; r < HF_SR; ++r) {
+            if (k <= gr[r]) {
+              const int g = gr[r];
+              cdf x = a[r];
+              if (lag) {
+                x = cdf_lag(x, vp[g], wp[g], vpk, wpk);
+                if (k == g) {
+                  x.ih = 0.f;
+                  x.il = 0.f;
+                }
+                rowp[r][k] = x;
+              }
+              cdf_fma(racc[r], x, vk);
+              if (k < g) cdf_fmac(cacc, x, v[g]);
+            }
+          }
+          if (k < glast) cp[k] = cdf_add(cp[k], cacc);
+        }
+      }
+      // row sums across the lanes: halve the rows twice (lanes 16-31 keep rows 2, 3; then
+      // lanes with bit 3 set keep the odd row), then a 3-level butterfly; lane l ends with
+      // row l / 8
+      {
+        const bool u16 = (lane & 16) != 0, u8 = (lane & 8) != 0;
+        cdf k0v = u16 ? racc[2] : racc[0], k1v = u16 ? racc[3] : racc[1];
+        const cdf s0v = u16 ? racc[0] : racc[2], s1v = u16 ? racc[1] : racc[3];
+        k0v = cdf_add(k0v, cdf_shfl_xor(s0v, 16));
+        k1v = cdf_add(k1v, cdf_shfl_xor(s1v, 16));
+        cdf kk = u8 ? k1v : k0v;
+        const cdf ss = u8 ? k0v : k1v;
+        kk = cdf_add(kk, cdf_shfl_xor(ss, 8));
+        for (int o = 4; o > 0; o >>= 1) kk = cdf_add(kk, cdf_shfl_xor(kk, o));
+        const int r = lane >> 3;
+        int gsel = gr[0];
+#pragma unroll
+        for (int rr = 1; rr < HF_SR; ++rr)
+          if (r == rr) gsel = gr[rr];
+        if ((lane & 7) == 0 && gsel >= 0) pv[gsel] = kk;
+      }
+    }
+    __syncthreads();
+    // p of this CTA: its rows' row parts plus every warp's column parts; the partials are
+    // cleared for the next step as they are read
+    for (int k = j + 1 + tid; k < m; k += NT) {
+      cdf sacc = (k % CL == c) ? pv[k] : cdf_zero();
+      for (int w2 = 0; w2 < NW; ++w2) {
+        sacc = cdf_add(sacc, cpart[w2 * m + k]);
+        cpart[w2 * m + k] = cdf_zero();
+      }
+      pv[k] = sacc;
+    }
+    if (CL > 1) cluster.sync();
+    else __syncthreads();
+    // p = 2 sum of the parts; K = Re(v^H p); w = p - K v
+    dfl kp{0.f, 0.f};
+    for (int i = j + 1 + tid; i < m; i += NT) {
+      cdf pi = cdf_zero();
+#pragma unroll
+      for (int rr = 0; rr < CL; ++rr) {
+        const cdf* src = (CL > 1) ? cluster.map_shared_rank(pv, rr) : pv;
+        pi = cdf_add(pi, src[i]);
+      }
+      pi = cdf_make(dfl{2.f * pi.rh, 2.f * pi.rl}, dfl{2.f * pi.ih, 2.f * pi.il});
+      w[i] = pi;
+      const cdf vi = v[i];
+      kp = df_fma(kp, cre(vi), cre(pi));
+      kp = df_fma(kp, cim(vi), cim(pi));
+    }
+    const dfl K = df_block_sum(kp, red);
+    const dfl nK = df_neg(K);
+    for (int i = j + 1 + tid; i < m; i += NT) {
+      const cdf vi = v[i];
+      cdf wi = w[i];
+      wi = cdf_make(df_fma(cre(wi), cre(vi), nK), df_fma(cim(wi), cim(vi), nK));
+      w[i] = wi;
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && ((m - 1) % CL) == c) {
+    const cdf sl = S[hs_rowbase((m - 1 - c) / CL, c, CL) + m - 1];
+    dfl t = cre(sl);
+    if (m > 1) {
+      const cdf vq = bufV[((m - 2) & 1) * m + m - 1], wq = bufW[((m - 2) & 1) * m + m - 1];
+      t = df_fma(t, df_neg(cre(vq)), cre(wq));
+      t = df_fma(t, df_neg(cim(vq)), cim(wq));
+      t = df_fma(t, df_neg(cre(vq)), cre(wq));
+      t = df_fma(t, df_neg(cim(vq)), cim(wq));
+    }
+    e.d[(long)b * m + m - 1] = ldexp(df_to(t), ex);
+  }
+  __threadfence();
+  if (CL > 1) cluster.sync();
+  else __syncthreads();
+  if (c == 0 && tid == 0) {
+    double2 dl = make_double2(1, 0);
+    e.delta[(long)b * m] = dl;
+    double tn = 0;
+    for (int jj = 0; jj < m - 1; ++jj) {
+      const double2 a = __ldcg(e.alpha + (long)b * m + jj);
+      const double aa = sqrt(cabs2(a));
+      e.f[(long)b * m + jj] = aa;
+      if (aa > 0) dl = cmul(dl, cscale(a, 1.0 / aa));
+      e.delta[(long)b * m + jj + 1] = dl;
+    }
+    for (int jj = 0; jj < m; ++jj) {
+      const double fl = (jj > 0) ? e.f[(long)b * m + jj - 1] : 0.0, fr = (jj < m - 1) ? e.f[(long)b * m + jj] : 0.0;
+      tn = fmax(tn, fabs(__ldcg(e.d + (long)b * m + jj)) + fl + fr);
+    }
+    e.tnorm[b] = tn;
+  }
+}
+
 // Number of eigenvalues below x of the symmetric tridiagonal (d, f) (scaled
 // to norm ~1): sign changes of the Sturm sequence P_0 = 1, P_1 = d_0 - x,
 // P_i = (d_{i-1} - x) P_{i-1} - f_{i-2}^2 P_{i-2}, i.e. negative ratios
@@ -2072,6 +2370,58 @@ static int launch_hetrd_smem(int CL, const double2* G, long ldg, long sG, int m,
   }
 }
 
+// the one-pass reduction with rows in L2 (k_hetrd_df1): same cluster sizes as the
+// sweep kernels; 0 when its per-warp partials of p do not fit in shared memory
+constexpr int HF_THREADS = 2 * HS_THREADS;
+static int hetrd_df1_cluster(int m, int batch) {
+  if (m < 2) return 0;
+  const size_t smax = (size_t)device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin, 232448) - 2048;
+  if (hetrd_df1_smem_bytes(m, HF_THREADS) > smax) return 0;
+  const int sms = device_attr(cudaDevAttrMultiProcessorCount, 148);
+  for (int CL = 8; CL >= 2; CL >>= 1)
+    if ((long)batch * CL <= sms && m / CL >= 48) return CL;
+  return 1;
+}
+
+template <int CL>
+static int launch_hetrd_df1_t(const double2* G, long ldg, long sG, int m, int batch, const EigScratch& e,
+                              cudaStream_t s) {
+  const size_t smem = hetrd_df1_smem_bytes(m, HF_THREADS);
+  auto kern = k_hetrd_df1<CL, HF_THREADS>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return TSVD_ERR_CUDA;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(batch * CL);
+  cfg.blockDim = dim3(HF_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, kern, G, ldg, sG, m, (int)hetrd_smem_elems(m, CL), e, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return TSVD_ERR_CUDA;
+  }
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
+static int launch_hetrd_df1(int CL, const double2* G, long ldg, long sG, int m, int batch, const EigScratch& e,
+                            cudaStream_t s) {
+  switch (CL) {
+    case 8: return launch_hetrd_df1_t<8>(G, ldg, sG, m, batch, e, s);
+    case 4: return launch_hetrd_df1_t<4>(G, ldg, sG, m, batch, e, s);
+    case 2: return launch_hetrd_df1_t<2>(G, ldg, sG, m, batch, e, s);
+    default: return launch_hetrd_df1_t<1>(G, ldg, sG, m, batch, e, s);
+  }
+}
+
 template <typename C>
 int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double* lam, C* U, long ldu, long sU,
                   void* scratch, int* status, cudaStream_t s) {
@@ -2094,7 +2444,9 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
     // one launch over all slices: measured faster than waves sized to keep each
     // wave's rows in L2 (the pass is bound by its instructions, not by L2 misses)
     TSVD_STAGE("eig_hetrd", s);
-    TSVD_TRY((launch_hetrd_smem<kDoubleFloat, true>(CLg, G, ldg, sG, m, batch, e, s)));
+    const int CL1 = hetrd_df1_cluster(m, batch);
+    if (CL1 > 0) TSVD_TRY(launch_hetrd_df1(CL1, G, ldg, sG, m, batch, e, s));
+    else TSVD_TRY((launch_hetrd_smem<kDoubleFloat, true>(CLg, G, ldg, sG, m, batch, e, s)));
   } else {
     TSVD_STAGE("eig_hetrd", s);
     const size_t smem = (2 + 16) * (size_t)m * sizeof(double2);  // v, p and 16 warps' partials
