@@ -684,6 +684,29 @@ __device__ __forceinline__ void cdf_fmac(cdf& acc, cdf a, cdf b) {
   const dfl xi[2] = {cre(a), df_neg(cim(a))}, yi[2] = {cim(b), cre(b)};
   acc = cdf_make(df_dot<2>(cre(acc), xr, yr), df_dot<2>(cim(acc), xi, yi));
 }
+// acc += a b and acc += conj(a) b with acc kept unnormalised: the high words
+// carry the running sums, the low words every rounding error (the loop of
+// df_dot without its final renormalisation, which cdf_add does later)
+__device__ __forceinline__ void df_acc(float& s, float& e, float xh, float xl, float yh, float yl) {
+  const float p = xh * yh;
+  float pe = fmaf(xh, yh, -p);
+  pe = fmaf(xh, yl, fmaf(xl, yh, pe));
+  const float t = s + p, bb = t - s;
+  e += ((s - (t - bb)) + (p - bb)) + pe;
+  s = t;
+}
+__device__ __forceinline__ void cdf_fma_acc(cdf& acc, cdf a, cdf b) {
+  df_acc(acc.rh, acc.rl, a.rh, a.rl, b.rh, b.rl);
+  df_acc(acc.rh, acc.rl, -a.ih, -a.il, b.ih, b.il);
+  df_acc(acc.ih, acc.il, a.rh, a.rl, b.ih, b.il);
+  df_acc(acc.ih, acc.il, a.ih, a.il, b.rh, b.rl);
+}
+__device__ __forceinline__ void cdf_fmac_acc(cdf& acc, cdf a, cdf b) {
+  df_acc(acc.rh, acc.rl, a.rh, a.rl, b.rh, b.rl);
+  df_acc(acc.rh, acc.rl, a.ih, a.il, b.ih, b.il);
+  df_acc(acc.ih, acc.il, a.rh, a.rl, b.ih, b.il);
+  df_acc(acc.ih, acc.il, -a.ih, -a.il, b.rh, b.rl);
+}
 // a - vg conj(wk) - wg conj(vk)
 __device__ __forceinline__ cdf cdf_lag(cdf a, cdf vg, cdf wg, cdf vk, cdf wk) {
   const dfl xr[4] = {df_neg(cre(vg)), df_neg(cim(vg)), df_neg(cre(wg)), df_neg(cim(wg))};
@@ -1249,19 +1272,24 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df(const double2* __restrict__ 
 //   column part  p_k += conj(a_gk) v_g        (k < g; the lane's column, summed
 //                                              over the strip's rows, added to a
 //                                              warp-private partial of p)
-// The warp partials are summed per column after the sweep.  Strips go to
-// warps in snake order (w, 2 NW - 1 - w, 2 NW + w, ...) since their lengths
-// grow with the row index.
+// The warp partials are summed per column after the sweep.  The strips go to
+// the warps by a schedule fixed for every step in the prologue: longest first
+// to the least loaded warp, which balances the sweep to about one short strip
+// and keeps every sum in a fixed order.
 // ---------------------------------------------------------------------------
 constexpr int HF_SR = 4;  // own rows per strip
 
-static size_t hetrd_df1_smem_bytes(int m, int nt) {
-  return (size_t)(5 + nt / 32) * (size_t)m * sizeof(double2);  // v[2], w[2], p, warp partials [NW]
+// strips of the sweep of one CTA (the most of any CTA of a cluster of CL)
+static int hetrd_df1_strips(int m, int CL) { return (hs_own_rows(m, 0, CL) + HF_SR - 1) / HF_SR; }
+// v[2], w[2], p, the warp partials [NW]; with `sched`, the strip schedule [m-1][strips] after them
+static size_t hetrd_df1_smem_bytes(int m, int nt, int CL = 1, bool sched = false) {
+  const size_t base = (size_t)(5 + nt / 32) * (size_t)m * sizeof(double2);
+  return sched ? base + (((size_t)(m - 1) * hetrd_df1_strips(m, CL) + 15) & ~(size_t)15) : base;
 }
 
 template <int CL, int NT>
 __global__ void __launch_bounds__(NT, 1) k_hetrd_df1(const double2* __restrict__ G, long ldg, long sG, int m,
-                                                     int s_elems, EigScratch e, int b0) {
+                                                     int s_elems, EigScratch e, int use_sched) {
   extern __shared__ __align__(16) cdf dsm[];
   constexpr int NW = NT / 32;
   static_assert(HF_SR == 4, "the row-sum reduction below is written for strips of four rows");
@@ -1270,15 +1298,48 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df1(const double2* __restrict__
   cdf* bufW = bufV + 2 * m;                          // [2][m] w
   cdf* pv = bufW + 2 * m;                            // [m] this CTA's part of p
   cdf* cpart = pv + m;                               // [NW][m] column parts of p, one per warp
+  uint8_t* sched = (uint8_t*)(cpart + NW * m);       // [m-1][NSM] the warp of every strip of every step
   __shared__ dfl red[NW];
   __shared__ int s_exp;
   cg::cluster_group cluster = cg::this_cluster();
   const int c = (CL > 1) ? (int)cluster.block_rank() : 0;
-  const int b = b0 + (int)blockIdx.x / CL;
+  const int b = (int)blockIdx.x / CL;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   G += (long)b * sG;
   float2* Hv32 = (float2*)e.Hv + (long)b * m * m;
   const int nq = hs_own_rows(m, c, CL);
+  const int NSM = (hs_own_rows(m, 0, CL) + HF_SR - 1) / HF_SR;
+
+  // The strip schedule of every step, fixed before the first (so the column parts are
+  // summed in the same order on every run): longest strip first to the least loaded
+  // warp (lowest index on ties), a strip costing its 32-column chunks x 4 rows plus one
+  // for its row-sum reduction.  Without room for it, the warps take the strips in snake
+  // order (w, 2 NW - 1 - w, 2 NW + w, ...).
+  if (use_sched) {
+    for (int jj = tid; jj < m - 1; jj += NT) {
+      const int q0j = hs_qfirst(jj, c, CL);
+      const int nsj = (max(0, nq - q0j) + HF_SR - 1) / HF_SR;
+      int load[NW];
+#pragma unroll
+      for (int w2 = 0; w2 < NW; ++w2) load[w2] = 0;
+      for (int t = 0; t < nsj; ++t) {
+        const int sj = nsj - 1 - t;
+        const int glast = c + CL * min(q0j + sj * HF_SR + HF_SR - 1, nq - 1);
+        const int cost = ((glast - jj) + 31) / 32 * HF_SR + 1;
+        int wb = 0, lb = load[0];
+#pragma unroll
+        for (int w2 = 1; w2 < NW; ++w2)
+          if (load[w2] < lb) {
+            lb = load[w2];
+            wb = w2;
+          }
+#pragma unroll
+        for (int w2 = 0; w2 < NW; ++w2)
+          if (w2 == wb) load[w2] += cost;
+        sched[jj * NSM + sj] = (uint8_t)wb;
+      }
+    }
+  }
 
   // power-of-two scale from the largest diagonal entry (identical in every CTA)
   {
@@ -1390,9 +1451,29 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df1(const double2* __restrict__
     const int q0 = hs_qfirst(j, c, CL);
     const int nstrip = (max(0, nq - q0) + HF_SR - 1) / HF_SR;
     cdf* cp = cpart + warp * m;
-    for (int s0 = 0; s0 < nstrip; s0 += NW) {
-      const int s = s0 + (((s0 / NW) & 1) ? NW - 1 - warp : warp);  // snake order
-      if (s >= nstrip) continue;
+    const uint8_t* own = sched + j * NSM;
+    unsigned mine = 0;  // this warp's strips among s0 .. s0 + 31 (with the schedule)
+    for (int s0 = 0, it = 0; s0 < nstrip;) {
+      int s;
+      if (use_sched) {
+        if (it == 0) {
+          const int sl = s0 + lane;
+          mine = __ballot_sync(0xffffffffu, sl < nstrip && own[sl] == warp);
+        }
+        if (mine == 0) {  // the next group of 32 strips
+          s0 += 32;
+          it = 0;
+          continue;
+        }
+        const int bit = 31 - __clz(mine);
+        mine &= ~(1u << bit);
+        s = s0 + bit;
+        it = 1;
+      } else {
+        s = s0 + (((s0 / NW) & 1) ? NW - 1 - warp : warp);  // snake order
+        s0 += NW;
+        if (s >= nstrip) continue;
+      }
       const int qs = q0 + s * HF_SR;
       int gr[HF_SR];
       cdf* rowp[HF_SR];
@@ -1433,8 +1514,8 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df1(const double2* __restrict__
                 }
                 rowp[r][k] = x;
               }
-              cdf_fma(racc[r], x, vk);
-              if (k < g) cdf_fmac(cacc, x, v[g]);
+              cdf_fma_acc(racc[r], x, vk);
+              if (k < g) cdf_fmac_acc(cacc, x, v[g]);
             }
           }
           if (k < glast) cp[k] = cdf_add(cp[k], cacc);
@@ -2386,7 +2467,9 @@ static int hetrd_df1_cluster(int m, int batch) {
 template <int CL>
 static int launch_hetrd_df1_t(const double2* G, long ldg, long sG, int m, int batch, const EigScratch& e,
                               cudaStream_t s) {
-  const size_t smem = hetrd_df1_smem_bytes(m, HF_THREADS);
+  const size_t smax = (size_t)device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin, 232448) - 2048;
+  const int use_sched = hetrd_df1_smem_bytes(m, HF_THREADS, CL, true) <= smax ? 1 : 0;
+  const size_t smem = hetrd_df1_smem_bytes(m, HF_THREADS, CL, use_sched != 0);
   auto kern = k_hetrd_df1<CL, HF_THREADS>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
@@ -2404,7 +2487,7 @@ static int launch_hetrd_df1_t(const double2* G, long ldg, long sG, int m, int ba
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, kern, G, ldg, sG, m, (int)hetrd_smem_elems(m, CL), e, 0) != cudaSuccess) {
+  if (cudaLaunchKernelEx(&cfg, kern, G, ldg, sG, m, (int)hetrd_smem_elems(m, CL), e, use_sched) != cudaSuccess) {
     cudaGetLastError();
     return TSVD_ERR_CUDA;
   }

@@ -108,6 +108,24 @@ def test_mixed_ragged_shapes(api, orc, n1, n2, n3, R, P, q, precision):
     check_against_oracle(api, orc, X, R, P, q, precision, omega=om, sig_floor=1e-6)
 
 
+@pytest.mark.parametrize("n1,n2,n3,R,P,q,precision", [
+    (480, 480, 32, 100, 20, 3, "fp32"),   # m = 480 on 17 slices: clusters of 8 CTAs
+    (400, 410, 38, 90, 10, 3, "tf32"),    # m = 400 on 20 slices: clusters of 4
+    (340, 340, 158, 75, 10, 3, "fp32"),   # m = 340 on 80 slices: one CTA per slice
+])
+def test_l2_row_tridiagonalisation_shapes(api, orc, n1, n2, n3, R, P, q, precision):
+    """Eigen-problems whose packed rows do not fit in a cluster's shared memory:
+    the one-sweep double-float reduction with the rows in L2, at three of the
+    cluster sizes it takes (the 2048 x 2048 x 128 test covers clusters of 2),
+    and bitwise the same on a second run (its sums have a fixed order)."""
+    X = wl.low_tubal_rank(n1, n2, n3, np.arange(1, min(n1, n2) + 1) ** -1.0, noise_std=1e-4, seed=n1 + n3)
+    om = wl.omega(n2, R + P, n3, seed=9)
+    sig, _, _, _, _ = check_against_oracle(api, orc, X, R, P, q, precision, omega=om, sig_floor=1e-6)
+    again = run_gpu(api, X.astype(np.float32).astype(np.float64), R, P, q, precision,
+                    om.astype(np.float32).astype(np.float64))
+    np.testing.assert_array_equal(again[3], sig)
+
+
 @pytest.mark.parametrize("n1,n2,n3,R,P,q", [
     (70, 90, 1, 5, 3, 2),     # n3 = 1: the matrix block Krylov method
     (40, 33, 2, 4, 2, 1),     # only DC and Nyquist slices
