@@ -572,10 +572,10 @@ __global__ void __launch_bounds__(HS_THREADS, 1) k_hetrd_smem(const double2* __r
 // (about 2^-47 ||G|| per operation) is far below what the FP32 path's
 // accuracy needs; the FP64 path keeps k_hetrd_smem.
 // ---------------------------------------------------------------------------
-struct dfl {
+struct __align__(8) dfl {
   float hi, lo;
 };
-struct cdf {  // complex double-float, 16 bytes like double2
+struct __align__(16) cdf {  // complex double-float, 16 bytes like double2 (one 16-byte access)
   float rh, rl, ih, il;
 };
 
@@ -1546,12 +1546,16 @@ __global__ void __launch_bounds__(NT, 1) k_hetrd_df1(const double2* __restrict__
     // p of this CTA: its rows' row parts plus every warp's column parts; the partials are
     // cleared for the next step as they are read
     for (int k = j + 1 + tid; k < m; k += NT) {
-      cdf sacc = (k % CL == c) ? pv[k] : cdf_zero();
-      for (int w2 = 0; w2 < NW; ++w2) {
-        sacc = cdf_add(sacc, cpart[w2 * m + k]);
-        cpart[w2 * m + k] = cdf_zero();
-      }
-      pv[k] = sacc;
+      cdf part[NW];  // all loads first, then a pairwise sum (fixed order), then the clearing
+#pragma unroll
+      for (int w2 = 0; w2 < NW; ++w2) part[w2] = cpart[w2 * m + k];
+#pragma unroll
+      for (int h = NW / 2; h > 0; h >>= 1)
+#pragma unroll
+        for (int w2 = 0; w2 < h; ++w2) part[w2] = cdf_add(part[w2], part[w2 + h]);
+#pragma unroll
+      for (int w2 = 0; w2 < NW; ++w2) cpart[w2 * m + k] = cdf_zero();
+      pv[k] = (k % CL == c) ? cdf_add(pv[k], part[0]) : part[0];
     }
     if (CL > 1) cluster.sync();
     else __syncthreads();
@@ -2593,7 +2597,10 @@ int herm_eig_topR(double2* G, long ldg, long sG, int m, int R, int batch, double
     size_t smem_co = (size_t)R * m * (kDoubleFloat ? sizeof(float) : sizeof(double));
     using CoKernel = void (*)(int, int, EigScratch, const double*);
     CoKernel co = kDoubleFloat ? (CoKernel)k_cluster_orth<float, true> : (CoKernel)k_cluster_orth<double, true>;
-    if (smem_co > 180 * 1024) {  // vectors stay in global memory
+    // the kernel's static arrays (the cluster Gram and its reductions) take about 17 KB of the
+    // per-block limit
+    const size_t smax_co = (size_t)device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin, 232448) - 20 * 1024;
+    if (smem_co > smax_co) {  // vectors stay in global memory
       co = k_cluster_orth<double, false>;
       smem_co = 0;
     }
