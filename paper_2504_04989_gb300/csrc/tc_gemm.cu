@@ -3,10 +3,12 @@
 // A and B K-major (K contiguous), TF32 (FP32 storage) or BF16 operands, FP32
 // accumulation in tensor memory.
 //
-// One CTA computes a 128 x 128 tile.  Operand tiles of 128 rows x 128 bytes
-// of K are staged by TMA (128-byte swizzle) through a 4-stage ring of shared
+// One CTA computes a 128 x BN tile, BN = 128, or (TF32 and BF16) 256 when
+// N > 128 (a product with N in (128, 256], as the Krylov products' 2b real
+// columns, then reads each row panel of A once).  Operand tiles of 128 (A) and BN (B) rows x 128
+// bytes of K are staged by TMA (128-byte swizzle) through a ring of shared
 // buffers guarded by mbarriers; one thread issues tcgen05.mma (4 per stage,
-// 32 bytes of K each) into a 128-column TMEM accumulator and commits each
+// 32 bytes of K each) into a BN-column TMEM accumulator and commits each
 // stage back to the producer; all four warps then read the accumulator with
 // tcgen05.ld and store it.  Every wait is bounded: on a timeout the kernel
 // records an error flag instead of hanging.
@@ -31,15 +33,16 @@
 namespace tsvd {
 
 constexpr int TC_BM = 128;
-constexpr int TC_BN = 128;
-constexpr int TC_TILE_BYTES = 128 * 128;  // 128 rows x 128 bytes of K
-// MODE 0: TF32, 1: BF16, 2: split TF32
-template <int MODE>
+constexpr int TC_A_BYTES = TC_BM * 128;  // 128 rows x 128 bytes of K
+// MODE 0: TF32, 1: BF16, 2: split TF32; BN: 128 or 256 columns per tile
+template <int BN>
+constexpr int tc_b_bytes() { return BN * 128; }
+template <int MODE, int BN>
+constexpr int tc_stage_bytes() { return (MODE == 2 ? 2 : 1) * (TC_A_BYTES + tc_b_bytes<BN>()); }  // A, B[, A lo, B lo]
+template <int MODE, int BN>
 constexpr int tc_stages() { return MODE == 2 ? 3 : 4; }
-template <int MODE>
-constexpr int tc_ops() { return MODE == 2 ? 4 : 2; }  // operand tiles per stage
-template <int MODE>
-constexpr int tc_smem() { return tc_stages<MODE>() * tc_ops<MODE>() * TC_TILE_BYTES + 1024 + 256; }
+template <int MODE, int BN>
+constexpr int tc_smem() { return tc_stages<MODE, BN>() * tc_stage_bytes<MODE, BN>() + 1024 + 256; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -87,11 +90,12 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
 }
 
 // instruction descriptor: D FP32, A/B TF32 (kind::tf32) or BF16 (kind::f16),
-// both K-major, M = 128, N = TC_BN
-template <bool BF16>
+// both K-major, M = 128, N = BN
+template <bool BF16, int BN>
 __device__ __forceinline__ uint32_t instr_desc() {
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "M = 128 takes N in [16, 256], a multiple of 16");
   const uint32_t fmt = BF16 ? 1u : 2u;
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
 }
 
 template <bool BF16>
@@ -113,7 +117,7 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-template <int MODE>
+template <int MODE, int BN>
 __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmB,
                                                     const __grid_constant__ CUtensorMap tmA2,
@@ -121,15 +125,20 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
                                                     long ldc, long sC, int M, int N, int nk, int* __restrict__ err,
                                                     float alpha, float beta) {
   constexpr bool BF16 = MODE == 1, SPLIT = MODE == 2;
-  constexpr int STAGES = tc_stages<MODE>(), NOPS = tc_ops<MODE>();
+  constexpr int STAGES = tc_stages<MODE, BN>(), SB = tc_stage_bytes<MODE, BN>();
+  static_assert(tc_smem<MODE, BN>() <= 227 * 1024, "the stages must fit the opt-in shared memory of a CTA");
+  constexpr int BB = tc_b_bytes<BN>();
   extern __shared__ unsigned char tc_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
-  auto tile = [&](int s, int o) { return base + (s * NOPS + o) * TC_TILE_BYTES; };  // o: A, B, A lo, B lo
-  uint64_t* bars = (uint64_t*)(base + STAGES * NOPS * TC_TILE_BYTES);  // full[S], empty[S], done
+  // o: A, B, A lo, B lo (every offset a multiple of 1024 bytes)
+  auto tile = [&](int s, int o) {
+    return base + s * SB + (o & 1) * TC_A_BYTES + (o >> 1) * (TC_A_BYTES + BB);
+  };
+  uint64_t* bars = (uint64_t*)(base + STAGES * SB);  // full[S], empty[S], done
   uint32_t* tslot = (uint32_t*)(bars + 2 * STAGES + 1);
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int n0 = blockIdx.x * TC_BN, m0 = blockIdx.y * TC_BM, bz = blockIdx.z;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * TC_BM, bz = blockIdx.z;
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
   constexpr int KE = BF16 ? 64 : 32;  // elements per 128 bytes of K
 
@@ -144,7 +153,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(TC_BN));
+                 "r"(BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -160,7 +169,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
         s_fail = 1;
         break;
       }
-      mbar_expect_tx(full0 + 8 * s, NOPS * TC_TILE_BYTES);
+      mbar_expect_tx(full0 + 8 * s, SB);
       tma_load_3d(smem_u32(tile(s, 0)), &tmA, kb * KE, m0, bz, full0 + 8 * s);
       tma_load_3d(smem_u32(tile(s, 1)), &tmB, kb * KE, n0, bz, full0 + 8 * s);
       if (SPLIT) {
@@ -170,7 +179,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
       issued = kb + 1;
     }
   } else if (tid == 32) {  // MMA issuer
-    const uint32_t idesc = instr_desc<BF16>();
+    const uint32_t idesc = instr_desc<BF16, BN>();
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES, round = kb / STAGES;
       if (!mbar_wait(full0 + 8 * s, round & 1)) {
@@ -204,7 +213,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
     const int row = m0 + warp * 32 + lane;
     float* crow = C + (long)bz * sC + (long)row * ldc;
 #pragma unroll 1
-    for (int c0 = 0; c0 < TC_BN; c0 += 16) {
+    for (int c0 = 0; c0 < BN; c0 += 16) {
       uint32_t r[16];
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -235,7 +244,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
   }
 }
 
@@ -257,14 +266,16 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-// rows x K (elements) per batch, row stride ld, batch stride sb (elements)
-static int make_map(CUtensorMap* tm, const void* ptr, int rows, int K, long ld, long sb, int batch, bool bf16) {
+// rows x K (elements) per batch, row stride ld, batch stride sb (elements); boxes of
+// box_rows rows x 128 bytes of K
+static int make_map(CUtensorMap* tm, const void* ptr, int rows, int K, long ld, long sb, int batch, bool bf16,
+                    int box_rows = TC_BM) {
   auto enc = get_encode();
   if (!enc) return TSVD_ERR_CUDA;
   const size_t es = bf16 ? 2 : 4;
   cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)batch};
   cuuint64_t strides[2] = {(cuuint64_t)(ld * es), (cuuint64_t)(sb * es)};
-  cuuint32_t box[3] = {(cuuint32_t)(128 / es), (cuuint32_t)TC_BM, 1};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)ptr, dims,
                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -281,32 +292,39 @@ bool tc_gemm_supported(const void* A, long lda, long sA, const void* B, long ldb
   return batch <= 65535;
 }
 
-template <int MODE>
+template <int MODE, int BN>
 static int tc_launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& ta2, const CUtensorMap& tb2,
                      float* C, long ldc, long sC, int M, int N, int nk, int batch, int* err, cudaStream_t s,
                      float alpha = 1.0f, float beta = 0.0f) {
-  dim3 grid(cdiv(N, TC_BN), cdiv(M, TC_BM), batch);
-  if (cudaFuncSetAttribute(k_tc_gemm<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<MODE>()) !=
+  dim3 grid(cdiv(N, BN), cdiv(M, TC_BM), batch);
+  if (cudaFuncSetAttribute(k_tc_gemm<MODE, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<MODE, BN>()) !=
       cudaSuccess) {
     cudaGetLastError();
     return TSVD_ERR_CUDA;
   }
-  k_tc_gemm<MODE><<<grid, 128, tc_smem<MODE>(), s>>>(ta, tb, ta2, tb2, C, ldc, sC, M, N, nk, err, alpha, beta);
+  k_tc_gemm<MODE, BN><<<grid, 128, tc_smem<MODE, BN>(), s>>>(ta, tb, ta2, tb2, C, ldc, sC, M, N, nk, err, alpha,
+                                                               beta);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }
+// tile width: 256 columns when N > 128 (one tile row covers the whole of N <= 256)
+static int tc_bn(int N) { return N > 128 ? 256 : 128; }
 
 int tc_gemm(const void* A, long lda, long sA, int M, const void* B, long ldb, long sB, int N, int K, float* C, long ldc,
             long sC, int batch, bool bf16, int* err, cudaStream_t s) {
   if (M <= 0 || N <= 0 || batch <= 0) return TSVD_OK;
   if (!tc_gemm_supported(A, lda, sA, B, ldb, sB, batch, bf16)) return TSVD_ERR_UNSUPPORTED;
   CUtensorMap ta, tb;
+  const int bn = tc_bn(N);
   TSVD_TRY(make_map(&ta, A, M, K, lda, sA, batch, bf16));
-  TSVD_TRY(make_map(&tb, B, N, K, ldb, sB, batch, bf16));
+  TSVD_TRY(make_map(&tb, B, N, K, ldb, sB, batch, bf16, bn));
   const int kelem = bf16 ? 64 : 32;
   const int nk = (K + kelem - 1) / kelem;
-  if (bf16) return tc_launch<1>(ta, tb, ta, tb, C, ldc, sC, M, N, nk, batch, err, s);
-  return tc_launch<0>(ta, tb, ta, tb, C, ldc, sC, M, N, nk, batch, err, s);
+  if (bf16)
+    return bn == 256 ? tc_launch<1, 256>(ta, tb, ta, tb, C, ldc, sC, M, N, nk, batch, err, s)
+                     : tc_launch<1, 128>(ta, tb, ta, tb, C, ldc, sC, M, N, nk, batch, err, s);
+  return bn == 256 ? tc_launch<0, 256>(ta, tb, ta, tb, C, ldc, sC, M, N, nk, batch, err, s)
+                   : tc_launch<0, 128>(ta, tb, ta, tb, C, ldc, sC, M, N, nk, batch, err, s);
 }
 
 int tc_gemm_split(const float* Ahi, const float* Alo, long lda, long sA, int M, const float* Bhi, const float* Blo,
@@ -316,12 +334,14 @@ int tc_gemm_split(const float* Ahi, const float* Alo, long lda, long sA, int M, 
   if (!tc_gemm_supported(Ahi, lda, sA, Bhi, ldb, sB, batch, false) ||
       !tc_gemm_supported(Alo, lda, sA, Blo, ldb, sB, batch, false))
     return TSVD_ERR_UNSUPPORTED;
+  // split TF32 keeps 128-column tiles: with four operand tiles per stage a 256-column tile
+  // leaves room for two stages only, which measured slower
   CUtensorMap ta, tb, ta2, tb2;
   TSVD_TRY(make_map(&ta, Ahi, M, K, lda, sA, batch, false));
   TSVD_TRY(make_map(&tb, Bhi, N, K, ldb, sB, batch, false));
   TSVD_TRY(make_map(&ta2, Alo, M, K, lda, sA, batch, false));
   TSVD_TRY(make_map(&tb2, Blo, N, K, ldb, sB, batch, false));
-  return tc_launch<2>(ta, tb, ta2, tb2, C, ldc, sC, M, N, (K + 31) / 32, batch, err, s, alpha, beta);
+  return tc_launch<2, 128>(ta, tb, ta2, tb2, C, ldc, sC, M, N, (K + 31) / 32, batch, err, s, alpha, beta);
 }
 
 // ---------------------------------------------------------------------------

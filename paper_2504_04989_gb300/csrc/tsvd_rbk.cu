@@ -106,7 +106,8 @@ struct RbkWs {
   void* eig;
   void* Aop;      // one-pass BF16 operand: X-hat as real rows of 2 n2, padded
   float* Ahi;     // split TF32 operands: X-hat as real rows (leading dim lda) ...
-  float* Alo;
+  float* Alo;     //   (the FP32 path; the TF32 path reads X-hat itself, or a padded copy in Ahi)
+  bool adirect;   // TF32 path: X-hat's own rows are the basis product's operand
   float* AThi;    // ... and X-hat^T (per slice n2 x n1 complex) as real rows (leading dim ldt)
   float* ATlo;
   long lda, ldt;
@@ -165,9 +166,10 @@ static RbkWs<T> carve_rbk(void* base, const RbkDims& d) {
   w.lda = (2L * d.n2 + 7) / 8 * 8;
   w.ldt = (2L * d.n1 + 7) / 8 * 8;
   w.lde = std::max(w.lda, w.ldt);
+  w.adirect = false;
   if (d.tc3) {
-    w.Ahi = cv.take<float>(h * d.n1 * w.lda);
-    w.Alo = cv.take<float>(h * d.n1 * w.lda);
+    if (d.tc != 2) w.Ahi = cv.take<float>(h * d.n1 * w.lda);
+    if (d.tc == 0) w.Alo = cv.take<float>(h * d.n1 * w.lda);
     w.AThi = cv.take<float>(h * d.n2 * w.ldt);
     w.ATlo = cv.take<float>(h * d.n2 * w.ldt);
     w.Eh = cv.take<float>(h * 2 * (size_t)d.b * w.lde);
@@ -251,10 +253,12 @@ static int basis_product(const RbkDims& d, RbkWs<T>& w, const cx_t<T>* Y, long l
       return tc_gemm(w.Aop, w.lda, (long)n1 * w.lda, n1, w.Eh, w.lde, se, 2 * nb, 2 * n2, (float*)w.Wt, 2L * b,
                      2L * sW, h, true, w.tc_err, s);
     }
-    if (d.tc == 1) {  // one TF32 pass on the TF32-rounded X-hat
+    if (d.tc == 1) {  // one TF32 pass on X-hat (its rows, or their padded copy)
       TSVD_TRY(expand_thin(Y, ldy, sy, n2, nb, w.Eh, w.lde, se, h, 0, false, s));
-      return tc_gemm(w.Ahi, w.lda, (long)n1 * w.lda, n1, w.Eh, w.lde, se, 2 * nb, 2 * n2, (float*)w.Wt, 2L * b,
-                     2L * sW, h, false, w.tc_err, s);
+      const float* Ar = w.adirect ? (const float*)w.Ah : w.Ahi;
+      const long la = w.adirect ? 2L * n2 : w.lda;
+      return tc_gemm(Ar, la, (long)n1 * la, n1, w.Eh, w.lde, se, 2 * nb, 2 * n2, (float*)w.Wt, 2L * b, 2L * sW, h,
+                     false, w.tc_err, s);
     }
     if (d.tc3) {
       TSVD_TRY(expand_thin_split(Y, ldy, sy, n2, nb, w.Eh, w.El, w.lde, se, h, 0, s));
@@ -347,7 +351,12 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
     TSVD_STAGE("krylov_split", s);
     if (cudaMemsetAsync(w.tc_err, 0, sizeof(int), s) != cudaSuccess) return TSVD_ERR_CUDA;
     if constexpr (std::is_same<T, float>::value) {
-      TSVD_TRY(split_rows((const float*)w.Ah, 2L * n2, w.Ahi, w.Alo, w.lda, 2 * n2, (long)h * n1, s));
+      // the one TF32 pass of the basis products reads X-hat's FP32 rows as they are (the tensor
+      // cores drop the low 13 mantissa bits) when their layout suits TMA, else a padded copy
+      w.adirect = d.tc == 1 && tc_gemm_supported(w.Ah, 2L * n2, 2L * n1 * n2, w.Eh, w.lde, 2L * b * w.lde, h, false);
+      if (d.tc == 0) TSVD_TRY(split_rows((const float*)w.Ah, 2L * n2, w.Ahi, w.Alo, w.lda, 2 * n2, (long)h * n1, s));
+      else if (d.tc == 1 && !w.adirect)
+        TSVD_TRY(copy_rows((const float*)w.Ah, 2L * n2, w.Ahi, w.lda, 2 * n2, (long)h * n1, false, s));
       TSVD_TRY(split_transpose((const float2*)w.Ah, n1, n2, h, w.AThi, w.ATlo, w.ldt, s));
       if (d.tc == 2) TSVD_TRY(copy_rows((const float*)w.Ah, 2L * n2, w.Aop, w.lda, 2 * n2, (long)h * n1, true, s));
     }
