@@ -132,6 +132,122 @@ __global__ void __launch_bounds__(256) k_cgemm(GemmArgs g, C* __restrict__ ws, i
   }
 }
 
+// FP32 (float2) products other than the Hermitian form: 128 x 64 tiles, each
+// of the 256 threads holding an 8 x 4 complex register tile (rows 8 ty .. +7,
+// columns 4 tx .. +3), read from shared memory in 16-byte pieces: 6 loads per
+// 128 FMAs instead of 8 per 64.  Rows of the staged tiles are padded by 16
+// bytes, which keeps the 16-byte reads aligned and spreads the transposed
+// stores of consecutive k over distinct banks.  Same staging, split-K and
+// epilogue as k_cgemm.
+constexpr int WBM = 128, WBN = 64, WBK = 8, WPAD = 2;
+
+template <bool AH, bool BH>
+__global__ void __launch_bounds__(256, 2) k_cgemm_w(GemmArgs g, float2* __restrict__ ws, int ksplit, int kchunk,
+                                                    int tiles_m) {
+  constexpr int NA = WBM * WBK / 256, NB = WBN * WBK / 256;  // staged elements per thread
+  __shared__ __align__(16) float2 As[2][WBK][WBM + WPAD];
+  __shared__ __align__(16) float2 Bs[2][WBK][WBN + WPAD];
+  const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+  const int bi = blockIdx.z / ksplit, kz = blockIdx.z % ksplit;
+  const int m0 = tm * WBM, n0 = tn * WBN;
+  const float2* __restrict__ A = (const float2*)g.A + (long)bi * g.sA;
+  const float2* __restrict__ B = (const float2*)g.B + (long)bi * g.sB;
+  const int kb = kz * kchunk, ke = min(g.K, kb + kchunk);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float2 acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  float2 ra[NA], rb[NB];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int t = 0; t < NA; ++t) {
+      const int idx = tid + 256 * t;
+      int mm, kk;
+      if (!AH) { kk = idx % WBK; mm = idx / WBK; }
+      else { mm = idx % WBM; kk = idx / WBM; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      float2 v = make_float2(0.f, 0.f);
+      if (gm < g.M && gk < ke) v = AH ? cconj(A[(long)gk * g.lda + gm]) : A[(long)gm * g.lda + gk];
+      ra[t] = v;
+    }
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const int idx = tid + 256 * t;
+      int nn, kk;
+      if (!BH) { nn = idx % WBN; kk = idx / WBN; }
+      else { kk = idx % WBK; nn = idx / WBK; }
+      const int gn = n0 + nn, gk = k0 + kk;
+      float2 v = make_float2(0.f, 0.f);
+      if (gn < g.N && gk < ke) v = BH ? cconj(B[(long)gn * g.ldb + gk]) : B[(long)gk * g.ldb + gn];
+      rb[t] = v;
+    }
+  };
+  auto stash = [&](int st) {
+#pragma unroll
+    for (int t = 0; t < NA; ++t) {
+      const int idx = tid + 256 * t;
+      if (!AH) As[st][idx % WBK][idx / WBK] = ra[t];
+      else As[st][idx / WBM][idx % WBM] = ra[t];
+    }
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const int idx = tid + 256 * t;
+      if (!BH) Bs[st][idx / WBN][idx % WBN] = rb[t];
+      else Bs[st][idx % WBK][idx / WBK] = rb[t];
+    }
+  };
+  if (kb < ke) fetch(kb);
+  int st = 0;
+  for (int k0 = kb; k0 < ke; k0 += WBK) {
+    stash(st);
+    __syncthreads();  // stage st complete; the stage written next was last read before this barrier
+    if (k0 + WBK < ke) fetch(k0 + WBK);
+#pragma unroll
+    for (int kk = 0; kk < WBK; ++kk) {
+      float2 a[8], b[4];
+      const float4* ap = reinterpret_cast<const float4*>(&As[st][kk][8 * ty]);
+      const float4* bp = reinterpret_cast<const float4*>(&Bs[st][kk][4 * tx]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 x = ap[u];
+        a[2 * u] = make_float2(x.x, x.y);
+        a[2 * u + 1] = make_float2(x.z, x.w);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const float4 x = bp[u];
+        b[2 * u] = make_float2(x.x, x.y);
+        b[2 * u + 1] = make_float2(x.z, x.w);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+    }
+    st ^= 1;
+  }
+  float2* __restrict__ Cm = (float2*)g.C + (long)bi * g.sC;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int gm = m0 + 8 * ty + i;
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + 4 * tx + j;
+      if (gn >= g.N) continue;
+      if (ksplit > 1) {
+        ws[(((long)kz * g.batch + bi) * g.M + gm) * g.N + gn] = acc[i][j];
+      } else {
+        float2 r = cscale(acc[i][j], (float)g.alpha);
+        if (g.beta != 0.0) r = cadd(r, cscale(Cm[(long)gm * g.ldc + gn], (float)g.beta));
+        Cm[(long)gm * g.ldc + gn] = r;
+      }
+    }
+  }
+}
+
 template <typename C>
 __global__ void k_splitk_reduce(const C* __restrict__ ws, int ksplit, GemmArgs g) {
   using R = typename GemmCfg<C>::R;
@@ -173,11 +289,46 @@ __global__ void k_mirror_lower(C* __restrict__ Cm, long ldc, long sC, int n, int
   }
 }
 
+// k_cgemm_w over the FP32 product g: split-K until about two waves of two CTAs per SM
+static int cgemm_wide(const GemmArgs& g, float2* ws, size_t splitk_elems, cudaStream_t s) {
+  const long tiles = (long)cdiv(g.M, WBM) * cdiv(g.N, WBN) * g.batch;
+  int ks = (int)std::max(1L, std::min(16L, (4L * 152 + tiles - 1) / tiles));
+  ks = std::min(ks, std::max(1, g.K / 64));
+  if (!ws) ks = 1;
+  while (ks > 1 && (size_t)ks * g.batch * g.M * g.N > splitk_elems) --ks;
+  while (ks > 1 && (long)ks * g.batch > 65535) --ks;
+  int kchunk = (g.K + ks - 1) / ks;
+  kchunk = (kchunk + WBK - 1) / WBK * WBK;
+  if (kchunk == 0) kchunk = WBK;
+  ks = std::max(1, (g.K + kchunk - 1) / kchunk);
+  const int tiles_m = cdiv(g.M, WBM), tiles_n = cdiv(g.N, WBN);
+  dim3 grid(tiles_m * tiles_n, 1, g.batch * ks);
+  const bool ah = (g.opA == 'H'), bh = (g.opB == 'H');
+  if (!ah && !bh) k_cgemm_w<false, false><<<grid, 256, 0, s>>>(g, ws, ks, kchunk, tiles_m);
+  else if (ah && !bh) k_cgemm_w<true, false><<<grid, 256, 0, s>>>(g, ws, ks, kchunk, tiles_m);
+  else if (!ah && bh) k_cgemm_w<false, true><<<grid, 256, 0, s>>>(g, ws, ks, kchunk, tiles_m);
+  else k_cgemm_w<true, true><<<grid, 256, 0, s>>>(g, ws, ks, kchunk, tiles_m);
+  TSVD_LAUNCHED();
+  if (ks > 1) {
+    const long total = (long)g.batch * g.M * g.N;
+    k_splitk_reduce<float2><<<std::min<long>(cdiv(total, 256), 4096), 256, 0, s>>>(ws, ks, g);
+    TSVD_LAUNCHED();
+  }
+  return TSVD_OK;
+}
+
 template <typename C>
 static int cgemm_impl(const GemmArgs& g, void* splitk_ws, size_t splitk_elems, cudaStream_t s, int herm) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return TSVD_OK;
   if (g.batch > 65535) return TSVD_ERR_UNSUPPORTED;
   if (g.beta != 0.0 && g.beta != 1.0) return TSVD_ERR_INVALID_ARG;
+  if constexpr (std::is_same<C, float2>::value) {
+    // the wide tiles where they fill the GPU (two CTAs per SM), directly or by splitting a long K;
+    // smaller products keep the 64 x 64 tiles (measured faster there)
+    const long wtiles = (long)cdiv(g.M, WBM) * cdiv(g.N, WBN) * g.batch;
+    if (!herm && g.K > 0 && (wtiles >= 2L * 152 || (g.K >= 1024 && splitk_ws)))
+      return cgemm_wide(g, (float2*)splitk_ws, splitk_ws ? splitk_elems : 0, s);
+  }
   int ks = (g.K > 0) ? choose_ksplit(g.M, g.N, g.K, g.batch, splitk_ws ? splitk_elems : 0) : 1;
   constexpr int BK = GemmCfg<C>::BK;
   int kchunk = (g.K + ks - 1) / ks;
