@@ -41,8 +41,8 @@ DF_FMA_INSTR = 15  # FP32 instructions per double-float multiply-add (TwoProduct
 # tridiagonalisation with its rows in L2 for m = 480 on 65 Fourier slices (the
 # eigen-problem of the 2048 x 2048 x 128 workload, captured on a 512 x 512 x 128
 # tensor with the same R, P, q, whose eigen-problem has the same sizes).
-NCU_TRAFFIC = {"eig_hetrd": {"src": "paper_2504_04989_gb300/csrc/eig.cu", "sha16": "ada16423b47d6aa3",
-                             "bytes_per_launch": 6.437174e9 + 10.665910e9}}
+NCU_TRAFFIC = {"eig_hetrd": {"src": "paper_2504_04989_gb300/csrc/eig.cu", "sha16": "6cdc60faafe65bcc",
+                             "bytes_per_launch": 5.819092e9 + 11.789736e9}}
 
 
 def peaks_file():

@@ -57,10 +57,11 @@ __global__ void __launch_bounds__(NTHR) k_chol_inv(const GC* __restrict__ G, lon
   G += (long)b * sG;
   Mo += (long)b * sM;
   if (tid < nb) dg[tid] = G[(long)tid * ldg + tid].x;
-  // row of packed index p: largest i with rb(i) + i <= p (closed form, then corrected)
+  // row of packed index p: largest i with rb(i) + i <= p (closed form in FP32 -- GB300's FP64
+  // unit is narrow -- then corrected exactly)
   auto row_of = [&](int p) {
-    const double q = 2.0 * nb + 1.0;
-    int i = (int)((q - sqrt(q * q - 8.0 * p)) * 0.5);
+    const float q = 2.0f * nb + 1.0f;
+    int i = (int)((q - sqrtf(fmaxf(q * q - 8.0f * p, 0.0f))) * 0.5f);
     i = max(0, min(i, nb - 1));
     while (i > 0 && rb(i) + i > p) --i;
     while (i + 1 < nb && rb(i + 1) + i + 1 <= p) ++i;
