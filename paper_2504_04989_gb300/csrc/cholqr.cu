@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(NTHR) k_chol_inv(const GC* __restrict__ G, lon
   const int pw0 = 32 * EPT * warp, pw1 = min(pw0 + 32 * EPT, np) - 1;
   const int wrow0 = (pw0 < np) ? row_of(pw0) : nb, wrow1 = (pw0 < np) ? row_of(pw1) : -1;
   // owned entries: (row, column) (-1 if none), packed offset and value
-  int ei[EPT], ek[EPT], eo[EPT];
+  int ei[EPT], ek[EPT];  // the packed offset of entry e is pw0 + 32 e + lane (a constant per e)
   GC v[EPT];
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
@@ -85,7 +85,6 @@ __global__ void __launch_bounds__(NTHR) k_chol_inv(const GC* __restrict__ G, lon
     }
     ei[e] = i;
     ek[e] = k;
-    eo[e] = (p < np) ? p : 0;
     v[e] = (p < np) ? G[(long)i * ldg + k] : GC{Rt(0), Rt(0)};
   }
   __syncthreads();
@@ -101,7 +100,7 @@ __global__ void __launch_bounds__(NTHR) k_chol_inv(const GC* __restrict__ G, lon
   for (int e = 0; e < EPT; ++e) {
     if (ei[e] >= 0 && ei[e] == ek[e]) v[e].x += sft;
     if (ei[e] == 0) {  // row 0 is final
-      S[eo[e]] = v[e];
+      S[pw0 + 32 * e + lane] = v[e];
       if (ek[e] == 0) pivot(0, v[e].x);
     }
   }
@@ -125,7 +124,7 @@ __global__ void __launch_bounds__(NTHR) k_chol_inv(const GC* __restrict__ G, lon
         t.y = fma(ay, c.x, t.y);
         if (i > j) v[e] = t;
         if (i == j + 1) {  // row j+1 is final
-          S[eo[e]] = v[e];
+          S[pw0 + 32 * e + lane] = v[e];
           if (k == i) pivot(i, v[e].x);
         }
       }
@@ -224,6 +223,12 @@ int chol_inv(const GC* G, long ldg, long sG, GC* M, long ldm, long sM, int nb, i
   if (np <= 2 * 512) return go(k_chol_inv<GC, 2, 512>, 512);
   if (np <= 4 * 512) return go(k_chol_inv<GC, 4, 512>, 512);
   if (np <= 8 * 512) return go(k_chol_inv<GC, 8, 512>, 512);
+  // larger Grams up to 8192 packed entries (90 < nb <= 127), FP32: 1024 threads with 8 entries
+  // each rather than 17 on 512 (each warp's chain of a step halves and twice the warps hide it;
+  // FP64 spills at 1024 x 8)
+  if constexpr (std::is_same<GC, float2>::value)
+    if (np <= 8 * 1024) return go(k_chol_inv<GC, 8, 1024>, 1024);
+  static_assert(17 * 512 >= 128 * 129 / 2, "the last variant covers every nb <= 128");
   return go(k_chol_inv<GC, 17, 512>, 512);
 }
 template int chol_inv<double2>(const double2*, long, long, double2*, long, long, int, int, double, double, uint32_t*,
