@@ -466,6 +466,23 @@ template int repair_dead<float2>(float2*, long, long, int, int, int, const uint3
 // projections stay on the SIMT GEMM: as long-K products with two 128-column
 // output tiles they stream their split operands twice, measured slower than
 // the SIMT kernel (which runs them at about half of the FP32 peak).
+// G = W^H W from the real Gram P = W_d W_d^T of the de-interleaved columns (row 2c of W_d the
+// real parts of column c, row 2c+1 the imaginary parts):
+//   G_ij = P[2i][2j] + P[2i+1][2j+1] + i (P[2i][2j+1] - P[2i+1][2j])
+__global__ void k_gram_from_real(const float* __restrict__ P, long ldp, long sp, int nb, float2* __restrict__ G,
+                                 long ldg, long sG, int batch) {
+  const long total = (long)batch * nb * nb;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int j = idx % nb;
+    const long r = idx / nb;
+    const int i = r % nb;
+    const int b = r / nb;
+    const float* p0 = P + (long)b * sp + (long)(2 * i) * ldp + 2 * j;
+    const float* p1 = p0 + ldp;
+    G[(long)b * sG + (long)i * ldg + j] = make_float2(p0[0] + p1[1], p0[1] - p1[0]);
+  }
+}
+
 static int orth_block_tc(int n1, int b, int m, int h, const OrthWs& w, int c, int nb, int block_id, uint64_t seed,
                          cudaStream_t s) {
   const OrthTc& t = *w.tc;
@@ -484,11 +501,18 @@ static int orth_block_tc(int n1, int b, int m, int h, const OrthWs& w, int c, in
       TSVD_TRY(cgemm<float2>(gemm('N', 'N', n1, nb, c, -1.0, Q, m, sQ, P, nb, sP, 1.0, W, b, sW, h), w.splitk, sk, s));
     }
     {
-      TSVD_STAGE("orth_gram", s);  // G = W^H W: conj(W^T) against E(W) in the conjugating form
-      TSVD_TRY(split_transpose_ld(W, n1, nb, b, sW, h, t.WThi, t.WTlo, t.ldq2, sWT, s));
-      TSVD_TRY(expand_thin_split(W, b, sW, n1, nb, t.Ehi, t.Elo, t.ldq2, sE, h, 1, s));
-      TSVD_TRY(tc_gemm_split(t.WThi, t.WTlo, t.ldq2, sWT, nb, t.Ehi, t.Elo, t.ldq2, sE, 2 * nb, 2 * n1, (float*)Gs,
-                             2L * b, 2L * sG, h, t.err, s));
+      // G = W^H W through the real Gram of W's de-interleaved columns (K = n1; 2 nb x 2 nb outputs,
+      // kept in Elo until the Cholesky has read G)
+      TSVD_STAGE("orth_gram", s);
+      const long ldd = t.ldq2 / 2;  // >= n1, a multiple of 4 (16-byte rows)
+      float* Pr = t.Elo;
+      TSVD_TRY(split_deinterleave(W, n1, nb, b, sW, h, t.WThi, t.WTlo, ldd, sWT, s));
+      TSVD_TRY(tc_gemm_split(t.WThi, t.WTlo, ldd, sWT, 2 * nb, t.WThi, t.WTlo, ldd, sWT, 2 * nb, n1, Pr, 2L * b,
+                             4L * b * b, h, t.err, s));
+      const long total = (long)h * nb * nb;
+      k_gram_from_real<<<(unsigned)std::min<long>(cdiv(total, 256), 4096), 256, 0, s>>>(Pr, 2L * b, 4L * b * b, nb,
+                                                                                       Gs, b, sG, h);
+      TSVD_LAUNCHED();
     }
     {
       TSVD_STAGE("orth_chol", s);

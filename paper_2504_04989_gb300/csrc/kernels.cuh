@@ -174,6 +174,11 @@ int split_transpose(const float2* X, int rows, int cols, int batch, float* hi, f
 // (padding columns are not touched)
 int split_transpose_ld(const float2* X, int rows, int cols, long ldx, long sx, int batch, float* hi, float* lo,
                        long ldt, long st, cudaStream_t s);
+// per slice the columns c of a complex X (rows x cols, leading dim ldx, batch stride sx) as real
+// rows 2c (real parts) and 2c+1 (imaginary parts) of length rows, split into hi / lo (leading dim
+// ldt, batch stride st; padding not touched)
+int split_deinterleave(const float2* X, int rows, int cols, long ldx, long sx, int batch, float* hi, float* lo,
+                       long ldt, long st, cudaStream_t s);
 // expand_thin into FP32 hi / lo parts
 int expand_thin_split(const float2* Y, long ldy, long sy, int K, int N, float* Eh, float* El, long lde, long se,
                       int batch, int mode, cudaStream_t s);

@@ -543,6 +543,45 @@ int split_transpose_ld(const float2* X, int rows, int cols, long ldx, long sx, i
   return TSVD_OK;
 }
 
+// per slice: the columns of a complex X (rows x cols, leading dim ldx) as real rows of
+// length `rows`: row 2c the real parts of column c, row 2c+1 the imaginary parts, split
+// into hi / lo (leading dim ldt, batch stride st); 32 x 32 complex tiles through shared memory
+__global__ void k_split_deinterleave(const float2* __restrict__ X, int rows, int cols, long ldx, long sx,
+                                     float* __restrict__ hi, float* __restrict__ lo, long ldt, long st) {
+  __shared__ float2 t[32][33];
+  const int b = blockIdx.z;
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const float2* Xb = X + (long)b * sx;
+  for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+    const int r = r0 + rr, c = c0 + threadIdx.x;
+    t[rr][threadIdx.x] = (r < rows && c < cols) ? Xb[(long)r * ldx + c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float* hb = hi + (long)b * st;
+  float* lb = lo + (long)b * st;
+  for (int cc = threadIdx.y; cc < 32; cc += blockDim.y) {
+    const int c = c0 + cc, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) {
+      const float2 v = t[threadIdx.x][cc];
+      const float hx = tf32_hi(v.x), hy = tf32_hi(v.y);
+      hb[(long)(2 * c) * ldt + r] = hx;
+      hb[(long)(2 * c + 1) * ldt + r] = hy;
+      lb[(long)(2 * c) * ldt + r] = v.x - hx;
+      lb[(long)(2 * c + 1) * ldt + r] = v.y - hy;
+    }
+  }
+}
+
+int split_deinterleave(const float2* X, int rows, int cols, long ldx, long sx, int batch, float* hi, float* lo,
+                       long ldt, long st, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0 || batch <= 0) return TSVD_OK;
+  if (batch > 65535) return TSVD_ERR_UNSUPPORTED;
+  dim3 grid(cdiv(cols, 32), cdiv(rows, 32), batch), block(32, 8);
+  k_split_deinterleave<<<grid, block, 0, s>>>(X, rows, cols, ldx, sx, hi, lo, ldt, st);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
 // expanded real form (as expand_thin, FP32) split into hi / lo; same tiling
 __global__ void __launch_bounds__(256) k_expand_split(const float2* __restrict__ Y, long ldy, long sy, int K, int N,
                                                       float* __restrict__ Eh, float* __restrict__ El, long lde,
