@@ -466,21 +466,31 @@ template int repair_dead<float2>(float2*, long, long, int, int, int, const uint3
 // projections stay on the SIMT GEMM: as long-K products with two 128-column
 // output tiles they stream their split operands twice, measured slower than
 // the SIMT kernel (which runs them at about half of the FP32 peak).
-// G = W^H W from the real Gram P = W_d W_d^T of the de-interleaved columns (row 2c of W_d the
-// real parts of column c, row 2c+1 the imaginary parts):
-//   G_ij = P[2i][2j] + P[2i+1][2j+1] + i (P[2i][2j+1] - P[2i+1][2j])
-__global__ void k_gram_from_real(const float* __restrict__ P, long ldp, long sp, int nb, float2* __restrict__ G,
-                                 long ldg, long sG, int batch) {
-  const long total = (long)batch * nb * nb;
+// X^H Y (rows x cols complex) from the real product P = X_d Y_d^T of the de-interleaved columns
+// (row 2c of X_d the real parts of column c of X, row 2c+1 the imaginary parts; Y_d alike):
+//   (X^H Y)_ij = P[2i][2j] + P[2i+1][2j+1] + i (P[2i][2j+1] - P[2i+1][2j])
+__global__ void k_complex_from_real(const float* __restrict__ P, long ldp, long sp, int rows, int cols,
+                                    float2* __restrict__ G, long ldg, long sG, int batch) {
+  const long total = (long)batch * rows * cols;
   for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-    const int j = idx % nb;
-    const long r = idx / nb;
-    const int i = r % nb;
-    const int b = r / nb;
+    const int j = idx % cols;
+    const long r = idx / cols;
+    const int i = r % rows;
+    const int b = r / rows;
     const float* p0 = P + (long)b * sp + (long)(2 * i) * ldp + 2 * j;
     const float* p1 = p0 + ldp;
     G[(long)b * sG + (long)i * ldg + j] = make_float2(p0[0] + p1[1], p0[1] - p1[0]);
   }
+}
+
+static int complex_from_real(const float* P, long ldp, long sp, int rows, int cols, float2* G, long ldg, long sG,
+                             int batch, cudaStream_t s) {
+  const long total = (long)batch * rows * cols;
+  if (total <= 0) return TSVD_OK;
+  k_complex_from_real<<<(unsigned)std::min<long>(cdiv(total, 256), 4096), 256, 0, s>>>(P, ldp, sp, rows, cols, G,
+                                                                                      ldg, sG, batch);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
 }
 
 static int orth_block_tc(int n1, int b, int m, int h, const OrthWs& w, int c, int nb, int block_id, uint64_t seed,
@@ -493,12 +503,21 @@ static int orth_block_tc(int n1, int b, int m, int h, const OrthWs& w, int c, in
   float2* Mi = (float2*)w.Minv;
   const long sQ = (long)n1 * m, sW = (long)n1 * b, sP = (long)m * b, sG = (long)b * b;
   const long sWT = (long)b * t.ldq2, sWr = (long)n1 * t.ldw2, sE = 2L * b * t.ldq2;
-  const size_t sk = 2 * w.splitk_elems;
   for (int pass = 0; pass < 3; ++pass) {
     if (c > 0) {
+      // the projection on tcgen05 against the cached split operands of Q's finished columns:
+      // Q^H W from the real product Q_d W_d^T (K = n1), then W -= Q (Q^H W) with Q's
+      // interleaved rows (K = 2c) against the expanded coefficients
       TSVD_STAGE("orth_cgs", s);
-      TSVD_TRY(cgemm<float2>(gemm('H', 'N', c, nb, n1, 1.0, Q, m, sQ, W, b, sW, 0.0, P, nb, sP, h), w.splitk, sk, s));
-      TSVD_TRY(cgemm<float2>(gemm('N', 'N', n1, nb, c, -1.0, Q, m, sQ, P, nb, sP, 1.0, W, b, sW, h), w.splitk, sk, s));
+      const long ldd = t.ldq2 / 2;
+      TSVD_TRY(split_deinterleave(W, n1, nb, b, sW, h, t.WThi, t.WTlo, ldd, sWT, s));
+      TSVD_TRY(tc_gemm_split(t.Qdhi, t.Qdlo, ldd, 2L * m * ldd, 2 * c, t.WThi, t.WTlo, ldd, sWT, 2 * nb, n1, t.Elo,
+                             2L * b, 4L * m * b, h, t.err, s));
+      TSVD_TRY(complex_from_real(t.Elo, 2L * b, 4L * m * b, c, nb, P, nb, sP, h, s));
+      const long sEq = 2L * b * t.ldqi;
+      TSVD_TRY(expand_thin_split(P, nb, sP, c, nb, t.Ehi, t.Elo, t.ldqi, sEq, h, 0, s));
+      TSVD_TRY(tc_gemm_split(t.Qhi, t.Qlo, t.ldqi, (long)n1 * t.ldqi, n1, t.Ehi, t.Elo, t.ldqi, sEq, 2 * nb, 2 * c,
+                             (float*)W, 2L * b, 2L * sW, h, t.err, s, -1.0f, 1.0f));
     }
     {
       // G = W^H W through the real Gram of W's de-interleaved columns (K = n1; 2 nb x 2 nb outputs,
@@ -509,10 +528,7 @@ static int orth_block_tc(int n1, int b, int m, int h, const OrthWs& w, int c, in
       TSVD_TRY(split_deinterleave(W, n1, nb, b, sW, h, t.WThi, t.WTlo, ldd, sWT, s));
       TSVD_TRY(tc_gemm_split(t.WThi, t.WTlo, ldd, sWT, 2 * nb, t.WThi, t.WTlo, ldd, sWT, 2 * nb, n1, Pr, 2L * b,
                              4L * b * b, h, t.err, s));
-      const long total = (long)h * nb * nb;
-      k_gram_from_real<<<(unsigned)std::min<long>(cdiv(total, 256), 4096), 256, 0, s>>>(Pr, 2L * b, 4L * b * b, nb,
-                                                                                       Gs, b, sG, h);
-      TSVD_LAUNCHED();
+      TSVD_TRY(complex_from_real(Pr, 2L * b, 4L * b * b, nb, nb, Gs, b, sG, h, s));
     }
     {
       TSVD_STAGE("orth_chol", s);
@@ -527,8 +543,17 @@ static int orth_block_tc(int n1, int b, int m, int h, const OrthWs& w, int c, in
                              pass < 2 ? 2L * b : 2L * m, pass < 2 ? 2L * sW : 2L * sQ, h, t.err, s));
     }
   }
-  TSVD_STAGE("orth_repair", s);
-  return repair_dead<float2>(Q, m, sQ, n1, c, nb, w.dead, h, seed, block_id, w.dead_count, w.k0, w.nyq, s);
+  {
+    TSVD_STAGE("orth_repair", s);
+    TSVD_TRY(repair_dead<float2>(Q, m, sQ, n1, c, nb, w.dead, h, seed, block_id, w.dead_count, w.k0, w.nyq, s));
+  }
+  // the finished columns' split operands for the projections of the later blocks
+  TSVD_STAGE("orth_cgs", s);
+  const long ldd = t.ldq2 / 2;
+  TSVD_TRY(split_block((const float*)(Q + c), 2L * m, t.Qhi + 2L * c, t.Qlo + 2L * c, t.ldqi, 2 * nb, (long)h * n1,
+                       s));
+  return split_deinterleave(Q + c, n1, nb, m, sQ, h, t.Qdhi + 2L * c * ldd, t.Qdlo + 2L * c * ldd, ldd,
+                            2L * m * ldd, s);
 }
 
 template <typename L>

@@ -124,7 +124,9 @@ struct OrthTc {
   float *WThi, *WTlo;  // W^T: b rows of 2 n1 floats (leading dim ldq2)
   float *Whi, *Wlo;    // W as real rows: n1 rows of 2 b floats (leading dim ldw2)
   float *Ehi, *Elo;    // expanded real forms of the thin factors: 2b rows (leading dim <= ldq2)
-  long ldq2, ldw2;
+  float *Qhi, *Qlo;    // finished basis columns as real rows: n1 rows of 2 m floats (leading dim ldqi)
+  float *Qdhi, *Qdlo;  // ... and de-interleaved: 2m rows of n1 floats (leading dim ldq2 / 2)
+  long ldq2, ldw2, ldqi;
   int* err;            // set by a tcgen05 pipeline wait that timed out
 };
 

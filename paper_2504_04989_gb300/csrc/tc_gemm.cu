@@ -223,12 +223,34 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
           : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (row < M) {
+        float* dst = crow + n0 + c0;
+        if (n0 + c0 + 16 <= N && ((uintptr_t)dst & 15) == 0) {
+          // the thread's 16 columns as four 16-byte accesses (the old values all loaded first)
+          float4 o[4];
+          if (beta != 0.0f) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = n0 + c0 + j;
-          if (col < N) {
-            const float v = alpha * __uint_as_float(r[j]);  // C = alpha A B^T + beta C
-            crow[col] = (beta != 0.0f) ? fmaf(beta, crow[col], v) : v;
+            for (int q = 0; q < 4; ++q) o[q] = reinterpret_cast<const float4*>(dst)[q];
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float4 v = make_float4(alpha * __uint_as_float(r[4 * q]), alpha * __uint_as_float(r[4 * q + 1]),
+                                   alpha * __uint_as_float(r[4 * q + 2]), alpha * __uint_as_float(r[4 * q + 3]));
+            if (beta != 0.0f) {
+              v.x = fmaf(beta, o[q].x, v.x);
+              v.y = fmaf(beta, o[q].y, v.y);
+              v.z = fmaf(beta, o[q].z, v.z);
+              v.w = fmaf(beta, o[q].w, v.w);
+            }
+            reinterpret_cast<float4*>(dst)[q] = v;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int col = n0 + c0 + j;
+            if (col < N) {
+              const float v = alpha * __uint_as_float(r[j]);  // C = alpha A B^T + beta C
+              crow[col] = (beta != 0.0f) ? fmaf(beta, crow[col], v) : v;
+            }
           }
         }
       }

@@ -188,6 +188,11 @@ static RbkWs<T> carve_rbk(void* base, const RbkDims& d) {
     t.Wlo = cv.take<float>(h * d.n1 * t.ldw2);
     t.Ehi = cv.take<float>(h * 2 * (size_t)d.b * t.ldq2);
     t.Elo = cv.take<float>(h * 2 * (size_t)d.b * t.ldq2);
+    t.ldqi = (2L * d.m + 7) / 8 * 8;
+    t.Qhi = cv.take<float>(h * d.n1 * t.ldqi);
+    t.Qlo = cv.take<float>(h * d.n1 * t.ldqi);
+    t.Qdhi = cv.take<float>(h * 2 * (size_t)d.m * (t.ldq2 / 2));
+    t.Qdlo = cv.take<float>(h * 2 * (size_t)d.m * (t.ldq2 / 2));
     t.err = w.tc_err;
   }
   w.splitk_elems = 8 * h * (size_t)d.m * std::max(d.b, 64);
