@@ -92,6 +92,11 @@ typedef struct {
    (absolute ~eps sigma_1) are returned, e.g. for the fast-decaying spectra of Sec. 5, Ex. 1.
    Other precisions return TSVD_ERR_UNSUPPORTED. */
 #define TSVD_FLAG_DEFLATE 16
+/* bit 5 (TSVD_FLAG_GRAM_INT, FP32 / mixed paths): take the exact Gram C C^H of the small SVD in
+   64-bit integer multiply-adds on the SIMT units instead of its base-64 digit form on the BF16
+   tensor cores (n2 <= 4096; larger n2 always use the integer form).  Both give the same G to
+   the bit; the flag exists to compare them. */
+#define TSVD_FLAG_GRAM_INT 32
 
 /* ---- device-side outcome, read back only when requested ---- */
 typedef struct {

@@ -16,6 +16,7 @@ TSVD_FLAG_ALG1 = 2
 TSVD_FLAG_SIMT = 4
 TSVD_FLAG_QTRUNC = 8
 TSVD_FLAG_DEFLATE = 16
+TSVD_FLAG_GRAM_INT = 32
 PRECISIONS = {"fp64": TSVD_FP64, "fp32": TSVD_FP32, "tf32": TSVD_MIXED_TF32, "bf16": TSVD_MIXED_BF16,
               "tf32x3": TSVD_SPLIT_TF32}
 

@@ -44,13 +44,14 @@ def _workspace(nbytes, device):
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
-def _flags(fp64_qr, alg1, q_trunc, deflate=False):
+def _flags(fp64_qr, alg1, q_trunc, deflate=False, gram_int=False):
     return ((_lib.TSVD_FLAG_FP64_QR if fp64_qr else 0) | (_lib.TSVD_FLAG_ALG1 if alg1 else 0) |
-            (_lib.TSVD_FLAG_QTRUNC if q_trunc else 0) | (_lib.TSVD_FLAG_DEFLATE if deflate else 0))
+            (_lib.TSVD_FLAG_QTRUNC if q_trunc else 0) | (_lib.TSVD_FLAG_DEFLATE if deflate else 0) |
+            (_lib.TSVD_FLAG_GRAM_INT if gram_int else 0))
 
 
 def rbk(A, R, P=10, q=2, seed=0, precision="fp32", omega=None, return_info=False, fp64_qr=False, alg1=False,
-        q_trunc=False, deflate=False):
+        q_trunc=False, deflate=False, gram_int=False):
     """Randomized block Krylov truncated T-SVD (Alg. 2): A ~ U * S * V^T.
 
     A: (n3, n1, n2) CUDA tensor.  Returns U (n3, n1, R), S (n3, R) singular
@@ -61,7 +62,9 @@ def rbk(A, R, P=10, q=2, seed=0, precision="fp32", omega=None, return_info=False
     (power iteration, basis of R+P columns) instead of Alg. 2; q_trunc=True
     projects on the leading R+P basis columns only (Ex. 1's truncated Q);
     deflate=True (FP64 only) resolves singular values below ~1e-8 sigma_1 by
-    deflated Rayleigh-Ritz passes in the small SVD.
+    deflated Rayleigh-Ritz passes in the small SVD.  gram_int=True (FP32 paths)
+    takes the exact Gram of the small SVD in integer arithmetic instead of its
+    digit form on the tensor cores (the same G to the bit).
     """
     lib = _lib.load()
     pr = _prec(precision)
@@ -69,7 +72,7 @@ def rbk(A, R, P=10, q=2, seed=0, precision="fp32", omega=None, return_info=False
     A = A.contiguous()
     _need_cuda(A, omega, dtype=dt)
     n3, n1, n2 = A.shape
-    flags = _flags(fp64_qr, alg1, q_trunc, deflate)
+    flags = _flags(fp64_qr, alg1, q_trunc, deflate, gram_int)
     p = _lib.TsvdParams(R=int(R), P=int(P), q=int(q), precision=pr, seed=int(seed), flags=flags)
     nbytes = C.c_size_t()
     _lib.check(lib.tsvd_rbk_workspace_size(n1, n2, n3, C.byref(p), C.byref(nbytes)), "tsvd_rbk_workspace_size")
@@ -99,10 +102,10 @@ class RbkPlan:
     (no allocation per call, so a loop of calls can be captured in a CUDA graph)."""
 
     def __init__(self, n1, n2, n3, R, P=10, q=2, seed=0, precision="fp32", device="cuda", fp64_qr=False,
-                 alg1=False, q_trunc=False, deflate=False):
+                 alg1=False, q_trunc=False, deflate=False, gram_int=False):
         self.lib = _lib.load()
         self.dt = _DT[precision]
-        flags = _flags(fp64_qr, alg1, q_trunc, deflate)
+        flags = _flags(fp64_qr, alg1, q_trunc, deflate, gram_int)
         self.p = _lib.TsvdParams(R=int(R), P=int(P), q=int(q), precision=_prec(precision), seed=int(seed),
                                  flags=flags)
         self.shape = (n1, n2, n3)

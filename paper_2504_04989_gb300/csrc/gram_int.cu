@@ -12,6 +12,8 @@
 // eps32 ||C||^2 on the small eigenvalues sigma_i^2 the method keeps; this form
 // keeps the error at the level of a perturbation of C itself, as the FP64 Gram
 // does, while running on the integer pipe instead of GB300's narrow FP64 unit.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -50,10 +52,90 @@ __global__ void __launch_bounds__(256) k_gram_quantize(const float2* __restrict_
   int e = 0;
   if (cm > 0.0f) frexpf(cm, &e);  // cm < 2^e
   if (ry == 0) colexp[(long)k * m + i] = e;
+  if (!Q) return;  // the exponents only (the sliced form quantizes as it writes its digits)
   int2* dst = Q + (long)k * n2 * m + i;
   for (int l = ry; l < n2; l += 8) {
     const float2 x = src[(long)l * ldc];
     dst[(long)l * m] = make_int2((int)rintf(ldexpf(x.x, B - e)), (int)rintf(ldexpf(x.y, B - e)));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The same exact Gram on the BF16 tensor cores.  Every integer q (|q| <= 2^B,
+// B <= 23) is split into four signed base-64 digits, q = sum_s d_s 64^(3-s),
+// |d_s| <= 63: exact in BF16, and a digit product summed over n2 <= 4096 terms
+// stays below 2^24, so the FP32 accumulation of the tensor cores adds exact
+// integers and is exact.  The digits of the real and imaginary parts of every
+// column i of C^H are rows s 2m + 2i (real) and s 2m + 2i + 1 (imaginary) of D
+// (8m x n2 per slice), P = D D^T holds all 16 digit pairs (s, t) of the
+// de-interleaved real products, and
+//   sum_l conj(q_li) q_lj = sum_(s,t) 64^(6-s-t) (P[2i][2j] + P[2i+1][2j+1]
+//                                  + i (P[2i][2j+1] - P[2i+1][2j]))   (block s, t)
+// is summed in 64-bit integers and rounded once, as above: G is bitwise the
+// integer kernel's.
+// ---------------------------------------------------------------------------
+constexpr int GS_DIGITS = 4, GS_DBITS = 6;
+
+// digits of the quantized C^H: 32 columns x 32 rows of C^H per block, transposed
+// through shared memory so that the rows of D are written along l
+__global__ void k_gram_digits(const float2* __restrict__ CH, long ldc, long sC, int n2, int m, int B,
+                              const int* __restrict__ colexp, __nv_bfloat16* __restrict__ D, long ldd, long sD) {
+  __shared__ int2 t[32][33];
+  const int b = blockIdx.z, i0 = blockIdx.x * 32, l0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int rr = ty; rr < 32; rr += blockDim.y) {
+    const int l = l0 + rr, i = i0 + tx;
+    int2 q = make_int2(0, 0);
+    if (l < n2 && i < m) {
+      const float2 x = CH[(long)b * sC + (long)l * ldc + i];
+      const int sh = B - colexp[(long)b * m + i];
+      q = make_int2((int)rintf(ldexpf(x.x, sh)), (int)rintf(ldexpf(x.y, sh)));
+    }
+    t[rr][tx] = q;
+  }
+  __syncthreads();
+  __nv_bfloat16* Db = D + (long)b * sD;
+  for (int cc = ty; cc < 32; cc += blockDim.y) {
+    const int i = i0 + cc, l = l0 + tx;
+    if (i >= m || l >= n2) continue;
+    const int2 q = t[tx][cc];
+#pragma unroll
+    for (int part = 0; part < 2; ++part) {
+      const int v = part ? q.y : q.x;
+      const int mag = v < 0 ? -v : v;
+#pragma unroll
+      for (int sd = 0; sd < GS_DIGITS; ++sd) {
+        const int d = (mag >> (GS_DBITS * (GS_DIGITS - 1 - sd))) & ((1 << GS_DBITS) - 1);
+        Db[(long)(sd * 2 * m + 2 * i + part) * ldd + l] = __int2bfloat16_rn(v < 0 ? -d : d);
+      }
+    }
+  }
+}
+
+// G_ij from the 16 digit-pair blocks of P (exact integers in FP32), summed in 64 bits
+__global__ void k_gram_combine(const float* __restrict__ P, long ldp, long sP, int m, int B,
+                               const int* __restrict__ colexp, double2* __restrict__ G, long ldg, long sG,
+                               int batch) {
+  const long total = (long)batch * m * m;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int j = idx % m;
+    const long r = idx / m;
+    const int i = r % m;
+    const int b = r / m;
+    const float* Pb = P + (long)b * sP;
+    long long re = 0, im = 0;
+#pragma unroll
+    for (int sd = 0; sd < GS_DIGITS; ++sd)
+#pragma unroll
+      for (int td = 0; td < GS_DIGITS; ++td) {
+        const float* p0 = Pb + (long)(sd * 2 * m + 2 * i) * ldp + td * 2 * m + 2 * j;
+        const float* p1 = p0 + ldp;
+        const long long w = 1LL << (GS_DBITS * (2 * GS_DIGITS - 2 - sd - td));
+        re += ((long long)p0[0] + (long long)p1[1]) * w;
+        im += ((long long)p0[1] - (long long)p1[0]) * w;
+      }
+    const int sc = colexp[(long)b * m + i] + colexp[(long)b * m + j] - 2 * B;
+    G[(long)b * sG + (long)i * ldg + j] = make_double2(ldexp((double)re, sc), ldexp((double)im, sc));
   }
 }
 
@@ -139,6 +221,35 @@ int gram_int_fp32(const float2* CH, long ldc, long sC, int n2, int m, int batch,
   TSVD_LAUNCHED();
   const int nt = cdiv(m, GI_TILE);
   k_gram_int<<<dim3(nt * (nt + 1) / 2, batch), 256, 0, s>>>(Q, colexp, n2, m, B, G, ldg, sG);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
+// the sliced form: for n2 <= 4096 (the digit products' sums stay below 2^24)
+bool gram_sliced_ok(int n2, int m) { return n2 >= 1 && n2 <= 4096 && m >= 1 && 8L * m <= 65535; }
+long gram_sliced_ldd(int n2) { return (n2 + 7) / 8 * 8; }
+size_t gram_sliced_bytes(int n2, int m, int batch) {
+  return (size_t)batch * 8 * m * gram_sliced_ldd(n2) * sizeof(__nv_bfloat16) +
+         (size_t)batch * 64 * m * m * sizeof(float) + 512;
+}
+
+int gram_sliced_fp32(const float2* CH, long ldc, long sC, int n2, int m, int batch, int* colexp, void* ws,
+                     double2* G, long ldg, long sG, int* err, cudaStream_t s) {
+  if (n2 <= 0 || m <= 0 || batch <= 0) return TSVD_OK;
+  if (batch > 65535 || !gram_sliced_ok(n2, m)) return TSVD_ERR_UNSUPPORTED;
+  const int B = gram_bits(n2);
+  const long ldd = gram_sliced_ldd(n2), sD = 8L * m * ldd, sP = 64L * m * m;
+  __nv_bfloat16* D = (__nv_bfloat16*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  float* P = (float*)(((uintptr_t)(D + (size_t)batch * sD) + 255) & ~(uintptr_t)255);
+  k_gram_quantize<<<dim3(cdiv(m, 32), batch), 256, 0, s>>>(CH, ldc, sC, n2, m, B, nullptr, colexp);
+  TSVD_LAUNCHED();
+  k_gram_digits<<<dim3(cdiv(m, 32), cdiv(n2, 32), batch), dim3(32, 8), 0, s>>>(CH, ldc, sC, n2, m, B, colexp, D,
+                                                                              ldd, sD);
+  TSVD_LAUNCHED();
+  TSVD_TRY(tc_gemm(D, ldd, sD, 8 * m, D, ldd, sD, 8 * m, n2, P, 8L * m, sP, batch, true, err, s));
+  const long total = (long)batch * m * m;
+  k_gram_combine<<<(unsigned)std::min<long>(cdiv(total, 256), 8192), 256, 0, s>>>(P, 8L * m, sP, m, B, colexp, G,
+                                                                                  ldg, sG, batch);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }

@@ -213,5 +213,11 @@ int deflate_merge(const double* lam_p, const double2* U_p, int mp, int R, int ba
 // (batch x m) are scratch.
 int gram_int_fp32(const float2* CH, long ldc, long sC, int n2, int m, int batch, int2* Q, int* colexp, double2* G,
                   long ldg, long sG, cudaStream_t s);
+// the same G, bitwise, from base-64 digits of the integers on the BF16 tensor cores (n2 <= 4096):
+// gram_sliced_bytes of scratch in ws, colexp (batch x m) as above; err as for tc_gemm
+bool gram_sliced_ok(int n2, int m);
+size_t gram_sliced_bytes(int n2, int m, int batch);
+int gram_sliced_fp32(const float2* CH, long ldc, long sC, int n2, int m, int batch, int* colexp, void* ws,
+                     double2* G, long ldg, long sG, int* err, cudaStream_t s);
 
 }  // namespace tsvd

@@ -41,6 +41,7 @@ struct RbkDims {
   int tco;   // FP32 block orthonormalisation with its Gram and W R^-1 on tcgen05 (split TF32)
   int tc3;   // FP32-accurate products on tcgen05 (split TF32): FP32 data unless TSVD_FLAG_SIMT
   int alg1;  // Alg. 1 (power iteration, last block only) instead of Alg. 2
+  int gsl;   // FP32 paths: the exact Gram in its digit form on the BF16 tensor cores
   int mp;    // basis columns used by the projection: m, or R+P with TSVD_FLAG_QTRUNC
   int deflate;  // deflated Rayleigh-Ritz passes for the small SVD (FP64 path)
 };
@@ -70,6 +71,7 @@ static int rbk_dims(int n1, int n2, int n3, const tsvd_params* p, RbkDims* d) {
   long m = (long)(d->alg1 ? 1 : p->q + 1) * d->b;
   m = std::min<long>(m, std::min(n1, n2));
   d->m = (int)m;
+  d->gsl = (d->tc3 && !(p->flags & TSVD_FLAG_GRAM_INT) && gram_sliced_ok(n2, d->m)) ? 1 : 0;
   d->mp = (p->flags & TSVD_FLAG_QTRUNC) ? std::min(d->b, d->m) : d->m;
   d->deflate = (p->flags & TSVD_FLAG_DEFLATE) ? 1 : 0;
   if (d->deflate && p->precision != TSVD_FP64) return TSVD_ERR_UNSUPPORTED;
@@ -92,7 +94,8 @@ struct RbkWs {
   void* Gl;    // block Gram matrix (b x b)
   C* CHt;
   double2* CH64;  // C^H in FP64 for the Gram (FP64 path: alias of CHt)
-  int2* Qint;     // C^H as scaled integers for the exact Gram (FP32 paths)
+  int2* Qint;     // C^H as scaled integers for the exact Gram (FP32 paths; integer form)
+  void* gsl;      // scratch of its digit form on the BF16 tensor cores
   int* colexp;    // their per-column exponents
   double2* Rs;
   uint32_t* dead;
@@ -148,7 +151,9 @@ static RbkWs<T> carve_rbk(void* base, const RbkDims& d) {
   w.Gl = cv.take<CL>(h * d.b * d.b);
   w.CHt = cv.take<C>(h * d.n2 * d.m);
   w.CH64 = dbl ? (double2*)w.CHt : nullptr;
-  w.Qint = dbl ? nullptr : cv.take<int2>(h * d.n2 * d.m);
+  const bool sliced = !dbl && d.gsl;
+  w.Qint = (dbl || sliced) ? nullptr : cv.take<int2>(h * d.n2 * d.m);
+  w.gsl = sliced ? (void*)cv.take<char>(gram_sliced_bytes(d.n2, d.m, h)) : nullptr;
   w.colexp = dbl ? nullptr : cv.take<int>(h * d.m);
   w.Rs = cv.take<double2>(h * d.b * d.b);
   w.dead = cv.take<uint32_t>(h * 4);
@@ -424,7 +429,11 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
                                       (long)mp * mp, h),
                                  w.splitk, w.splitk_elems, s));
   } else {
-    TSVD_TRY(gram_int_fp32((const float2*)w.CHt, m, sCH, n2, mp, h, w.Qint, w.colexp, w.G, mp, (long)mp * mp, s));
+    if (w.gsl)
+      TSVD_TRY(gram_sliced_fp32((const float2*)w.CHt, m, sCH, n2, mp, h, w.colexp, w.gsl, w.G, mp, (long)mp * mp,
+                                w.tc_err, s));
+    else
+      TSVD_TRY(gram_int_fp32((const float2*)w.CHt, m, sCH, n2, mp, h, w.Qint, w.colexp, w.G, mp, (long)mp * mp, s));
   }
   }
   TSVD_TRY(herm_eig_topR<C>(w.G, mp, (long)mp * mp, mp, R, h, w.lam, w.Uct, R, (long)mp * R, w.eig, w.counters, s));

@@ -165,6 +165,25 @@ def test_zero_tensor(api):
         assert np.all(S == 0)
 
 
+@pytest.mark.parametrize("n1,n2,n3,R,P,q,precision", [
+    (65, 129, 7, 6, 4, 3, "fp32"),       # ragged tiles
+    (300, 410, 10, 40, 10, 3, "tf32"),   # m = 200
+    (64, 4096, 2, 10, 5, 1, "fp32"),     # n2 = 4096: digit-product sums nearest 2^24
+    (1100, 700, 4, 100, 20, 3, "tf32"),  # m = 480, tensor-core orthonormalisation
+])
+def test_sliced_gram_bitwise_equals_integer_gram(api, n1, n2, n3, R, P, q, precision):
+    """The exact Gram in base-64 digits on the BF16 tensor cores gives the same G as
+    the 64-bit integer kernel, so the whole T-SVD is bitwise the same."""
+    X = wl.low_tubal_rank(n1, n2, n3, np.arange(1, min(n1, n2) + 1) ** -1.0, noise_std=1e-4, seed=n2 + n3)
+    om = wl.omega(n2, R + P, n3, seed=11).astype(np.float32)
+    Xd, od = dev(X, torch.float32), dev(om, torch.float32)
+    a = api.rbk(Xd, R, P, q, precision=precision, omega=od)
+    b = api.rbk(Xd, R, P, q, precision=precision, omega=od, gram_int=True)
+    torch.cuda.synchronize()
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
+
+
 def test_deterministic(api):
     X = wl.make_c1(1)
     a = run_gpu(api, X, 10, 5, 2, "fp64", seed=3)
