@@ -113,9 +113,11 @@ __global__ void k_gram_digits(const float2* __restrict__ CH, long ldc, long sC, 
 }
 
 // G_ij from the 16 digit-pair blocks of P (exact integers in FP32), summed in 64 bits
+// (P holds only the tiles of 128 rows x bn columns not wholly below its diagonal; an
+// element of a skipped tile is read at its transposed place, whose tile is always there)
 __global__ void k_gram_combine(const float* __restrict__ P, long ldp, long sP, int m, int B,
                                const int* __restrict__ colexp, double2* __restrict__ G, long ldg, long sG,
-                               int batch) {
+                               int batch, int bn) {
   const long total = (long)batch * m * m;
   for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
     const int j = idx % m;
@@ -128,11 +130,26 @@ __global__ void k_gram_combine(const float* __restrict__ P, long ldp, long sP, i
     for (int sd = 0; sd < GS_DIGITS; ++sd)
 #pragma unroll
       for (int td = 0; td < GS_DIGITS; ++td) {
-        const float* p0 = Pb + (long)(sd * 2 * m + 2 * i) * ldp + td * 2 * m + 2 * j;
-        const float* p1 = p0 + ldp;
+        const int a = sd * 2 * m + 2 * i, c = td * 2 * m + 2 * j;  // the even-aligned 2 x 2 block (a, c)
+        float q00, q01, q10, q11;
+        if ((c / bn + 1) * bn <= (a / 128) * 128) {  // its tile was skipped: P is symmetric
+          const float* t0 = Pb + (long)c * ldp + a;
+          const float* t1 = t0 + ldp;
+          q00 = t0[0];
+          q01 = t1[0];
+          q10 = t0[1];
+          q11 = t1[1];
+        } else {
+          const float* p0 = Pb + (long)a * ldp + c;
+          const float* p1 = p0 + ldp;
+          q00 = p0[0];
+          q01 = p0[1];
+          q10 = p1[0];
+          q11 = p1[1];
+        }
         const long long w = 1LL << (GS_DBITS * (2 * GS_DIGITS - 2 - sd - td));
-        re += ((long long)p0[0] + (long long)p1[1]) * w;
-        im += ((long long)p0[1] - (long long)p1[0]) * w;
+        re += ((long long)q00 + (long long)q11) * w;
+        im += ((long long)q01 - (long long)q10) * w;
       }
     const int sc = colexp[(long)b * m + i] + colexp[(long)b * m + j] - 2 * B;
     G[(long)b * sG + (long)i * ldg + j] = make_double2(ldexp((double)re, sc), ldexp((double)im, sc));
@@ -246,10 +263,11 @@ int gram_sliced_fp32(const float2* CH, long ldc, long sC, int n2, int m, int bat
   k_gram_digits<<<dim3(cdiv(m, 32), cdiv(n2, 32), batch), dim3(32, 8), 0, s>>>(CH, ldc, sC, n2, m, B, colexp, D,
                                                                               ldd, sD);
   TSVD_LAUNCHED();
-  TSVD_TRY(tc_gemm(D, ldd, sD, 8 * m, D, ldd, sD, 8 * m, n2, P, 8L * m, sP, batch, true, err, s));
+  TSVD_TRY(tc_gemm(D, ldd, sD, 8 * m, D, ldd, sD, 8 * m, n2, P, 8L * m, sP, batch, true, err, s, true));
+  const int bn = tc_gemm_tile_n(8 * m, true);
   const long total = (long)batch * m * m;
   k_gram_combine<<<(unsigned)std::min<long>(cdiv(total, 256), 8192), 256, 0, s>>>(P, 8L * m, sP, m, B, colexp, G,
-                                                                                  ldg, sG, batch);
+                                                                                  ldg, sG, batch, bn);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }

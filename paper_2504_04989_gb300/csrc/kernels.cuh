@@ -153,8 +153,11 @@ int orth_block_cols(int n1, int b, int m, int h, const OrthWs& w, int c, int nb,
 // 16-byte aligned bases, row strides and batch strides (tc_gemm_supported);
 // *err is set if a pipeline wait timed out.
 bool tc_gemm_supported(const void* A, long lda, long sA, const void* B, long ldb, long sB, int batch, bool bf16);
+// upper: a symmetric product (B = A, M = N): only the tiles not wholly below the diagonal are
+// written (tile rows of 128, tile columns of tc_gemm_tile_n(N, bf16))
 int tc_gemm(const void* A, long lda, long sA, int M, const void* B, long ldb, long sB, int N, int K, float* C, long ldc,
-            long sC, int batch, bool bf16, int* err, cudaStream_t s);
+            long sC, int batch, bool bf16, int* err, cudaStream_t s, bool upper = false);
+int tc_gemm_tile_n(int N, bool bf16);
 // expanded real form E (2N x 2K, leading dim lde) of a thin interleaved complex
 // Y (K x N): real(X) E^T = X Y (mode 0) or conj(X) Y (mode 1)
 int expand_thin(const float2* Y, long ldy, long sy, int K, int N, void* E, long lde, long se, int batch, int mode,

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
                                                     const __grid_constant__ CUtensorMap tmA2,
                                                     const __grid_constant__ CUtensorMap tmB2, float* __restrict__ C,
                                                     long ldc, long sC, int M, int N, int nk, int* __restrict__ err,
-                                                    float alpha, float beta) {
+                                                    float alpha, float beta, int upper) {
   constexpr bool BF16 = MODE == 1, SPLIT = MODE == 2;
   constexpr int STAGES = tc_stages<MODE, BN>(), SB = tc_stage_bytes<MODE, BN>();
   static_assert(tc_smem<MODE, BN>() <= 227 * 1024, "the stages must fit the opt-in shared memory of a CTA");
@@ -139,6 +139,8 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * TC_BM, bz = blockIdx.z;
+  // upper: a symmetric product (B = A) needs only the tiles not wholly below the diagonal
+  if (upper && n0 + BN <= m0) return;
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
   constexpr int KE = BF16 ? 64 : 32;  // elements per 128 bytes of K
 
@@ -317,7 +319,7 @@ bool tc_gemm_supported(const void* A, long lda, long sA, const void* B, long ldb
 template <int MODE, int BN>
 static int tc_launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& ta2, const CUtensorMap& tb2,
                      float* C, long ldc, long sC, int M, int N, int nk, int batch, int* err, cudaStream_t s,
-                     float alpha = 1.0f, float beta = 0.0f) {
+                     float alpha = 1.0f, float beta = 0.0f, int upper = 0) {
   dim3 grid(cdiv(N, BN), cdiv(M, TC_BM), batch);
   if (cudaFuncSetAttribute(k_tc_gemm<MODE, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<MODE, BN>()) !=
       cudaSuccess) {
@@ -325,15 +327,16 @@ static int tc_launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtenso
     return TSVD_ERR_CUDA;
   }
   k_tc_gemm<MODE, BN><<<grid, 128, tc_smem<MODE, BN>(), s>>>(ta, tb, ta2, tb2, C, ldc, sC, M, N, nk, err, alpha,
-                                                               beta);
+                                                               beta, upper);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }
 // tile width: 256 columns when N > 128 (one tile row covers the whole of N <= 256)
 static int tc_bn(int N) { return N > 128 ? 256 : 128; }
+int tc_gemm_tile_n(int N, bool bf16) { (void)bf16; return tc_bn(N); }
 
 int tc_gemm(const void* A, long lda, long sA, int M, const void* B, long ldb, long sB, int N, int K, float* C, long ldc,
-            long sC, int batch, bool bf16, int* err, cudaStream_t s) {
+            long sC, int batch, bool bf16, int* err, cudaStream_t s, bool upper) {
   if (M <= 0 || N <= 0 || batch <= 0) return TSVD_OK;
   if (!tc_gemm_supported(A, lda, sA, B, ldb, sB, batch, bf16)) return TSVD_ERR_UNSUPPORTED;
   CUtensorMap ta, tb;
@@ -342,11 +345,12 @@ int tc_gemm(const void* A, long lda, long sA, int M, const void* B, long ldb, lo
   TSVD_TRY(make_map(&tb, B, N, K, ldb, sB, batch, bf16, bn));
   const int kelem = bf16 ? 64 : 32;
   const int nk = (K + kelem - 1) / kelem;
+  const int up = upper ? 1 : 0;
   if (bf16)
-    return bn == 256 ? tc_launch<1, 256>(ta, tb, ta, tb, C, ldc, sC, M, N, nk, batch, err, s)
-                     : tc_launch<1, 128>(ta, tb, ta, tb, C, ldc, sC, M, N, nk, batch, err, s);
-  return bn == 256 ? tc_launch<0, 256>(ta, tb, ta, tb, C, ldc, sC, M, N, nk, batch, err, s)
-                   : tc_launch<0, 128>(ta, tb, ta, tb, C, ldc, sC, M, N, nk, batch, err, s);
+    return bn == 256 ? tc_launch<1, 256>(ta, tb, ta, tb, C, ldc, sC, M, N, nk, batch, err, s, 1.f, 0.f, up)
+                     : tc_launch<1, 128>(ta, tb, ta, tb, C, ldc, sC, M, N, nk, batch, err, s, 1.f, 0.f, up);
+  return bn == 256 ? tc_launch<0, 256>(ta, tb, ta, tb, C, ldc, sC, M, N, nk, batch, err, s, 1.f, 0.f, up)
+                   : tc_launch<0, 128>(ta, tb, ta, tb, C, ldc, sC, M, N, nk, batch, err, s, 1.f, 0.f, up);
 }
 
 int tc_gemm_split(const float* Ahi, const float* Alo, long lda, long sA, int M, const float* Bhi, const float* Blo,
