@@ -445,10 +445,37 @@ static int rbk_run(const T* A, const RbkDims& d, const tsvd_params& p, const T* 
   TSVD_TRY(sigma_from_lambda<T>(w.lam, R, h, sig, w.Sh, s, w.counters));
 
   // Uhat = Q U_c,  Vhat = C^H U_c S^{-1}
-  TSVD_TRY(cgemm<C>(gemm('N', 'N', n1, R, mp, 1.0, w.Qt, m, sQ, w.Uct, R, (long)mp * R, 0.0, w.Uh, R, (long)n1 * R, h),
-                    w.splitk, w.splitk_elems * 2, s));
-  TSVD_TRY(cgemm<C>(gemm('N', 'N', n2, R, mp, 1.0, w.CHt, m, sCH, w.Uct, R, (long)mp * R, 0.0, w.Vh, R, (long)n2 * R, h),
-                    w.splitk, w.splitk_elems * 2, s));
+  bool done = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (d.tco) {
+      // split TF32 on tcgen05: Q's interleaved rows from the orthonormalisation's cache (K = 2 mp),
+      // then C^H split into the same buffers (Q's are no longer needed), against E(U_c)
+      const OrthTc& t = w.otc;
+      const long sE = 2L * R * t.ldqi, sQi = (long)n1 * t.ldqi;
+      TSVD_TRY(expand_thin_split(w.Uct, R, (long)mp * R, mp, R, t.Ehi, t.Elo, t.ldqi, sE, h, 0, s));
+      TSVD_TRY(tc_gemm_split(t.Qhi, t.Qlo, t.ldqi, sQi, n1, t.Ehi, t.Elo, t.ldqi, sE, 2 * R, 2 * mp, (float*)w.Uh,
+                             2L * R, 2L * n1 * R, h, w.tc_err, s));
+      if (n2 <= n1) {
+        TSVD_TRY(split_rows((const float*)w.CHt, 2L * m, t.Qhi, t.Qlo, t.ldqi, 2 * mp, (long)h * n2, s));
+        TSVD_TRY(tc_gemm_split(t.Qhi, t.Qlo, t.ldqi, (long)n2 * t.ldqi, n2, t.Ehi, t.Elo, t.ldqi, sE, 2 * R, 2 * mp,
+                               (float*)w.Vh, 2L * R, 2L * n2 * R, h, w.tc_err, s));
+        done = true;
+      } else {
+        TSVD_TRY(cgemm<C>(gemm('N', 'N', n2, R, mp, 1.0, w.CHt, m, sCH, w.Uct, R, (long)mp * R, 0.0, w.Vh, R,
+                               (long)n2 * R, h),
+                          w.splitk, w.splitk_elems * 2, s));
+        done = true;
+      }
+    }
+  }
+  if (!done) {
+    TSVD_TRY(cgemm<C>(gemm('N', 'N', n1, R, mp, 1.0, w.Qt, m, sQ, w.Uct, R, (long)mp * R, 0.0, w.Uh, R,
+                           (long)n1 * R, h),
+                      w.splitk, w.splitk_elems * 2, s));
+    TSVD_TRY(cgemm<C>(gemm('N', 'N', n2, R, mp, 1.0, w.CHt, m, sCH, w.Uct, R, (long)mp * R, 0.0, w.Vh, R,
+                           (long)n2 * R, h),
+                      w.splitk, w.splitk_elems * 2, s));
+  }
   TSVD_TRY(scale_columns_inv<T>(w.Vh, R, (long)n2 * R, n2, R, w.lam, h, s));
   }
   if (!d.fourier) {
