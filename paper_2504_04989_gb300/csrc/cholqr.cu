@@ -503,29 +503,43 @@ static int orth_block_tc(int n1, int b, int m, int h, const OrthWs& w, int c, in
   float2* Mi = (float2*)w.Minv;
   const long sQ = (long)n1 * m, sW = (long)n1 * b, sP = (long)m * b, sG = (long)b * b;
   const long sWT = (long)b * t.ldq2, sWr = (long)n1 * t.ldw2, sE = 2L * b * t.ldq2;
+  const long ldd = t.ldq2 / 2;  // de-interleaved rows: >= n1, a multiple of 4 (16-byte rows)
+  // which split copies of the current W exist: wd its de-interleaved rows (WThi / WTlo), wr its
+  // rows (Whi / Wlo), written by the epilogue of the GEMM that produced W
+  bool wd = false, wr = false;
+  TcSplitOut both;
+  both.Rhi = t.Whi;
+  both.Rlo = t.Wlo;
+  both.ldr = t.ldw2;
+  both.sr = sWr;
+  both.Thi = t.WThi;
+  both.Tlo = t.WTlo;
+  both.ldt = ldd;
+  both.st = sWT;
+  TcSplitOut cols_only = both;  // W R^-1 reads Whi / Wlo as its operand: it writes only the other copy
+  cols_only.Rhi = cols_only.Rlo = nullptr;
   for (int pass = 0; pass < 3; ++pass) {
     if (c > 0) {
       // the projection on tcgen05 against the cached split operands of Q's finished columns:
       // Q^H W from the real product Q_d W_d^T (K = n1), then W -= Q (Q^H W) with Q's
       // interleaved rows (K = 2c) against the expanded coefficients
       TSVD_STAGE("orth_cgs", s);
-      const long ldd = t.ldq2 / 2;
-      TSVD_TRY(split_deinterleave(W, n1, nb, b, sW, h, t.WThi, t.WTlo, ldd, sWT, s));
+      if (!wd) TSVD_TRY(split_deinterleave(W, n1, nb, b, sW, h, t.WThi, t.WTlo, ldd, sWT, s));
       TSVD_TRY(tc_gemm_split(t.Qdhi, t.Qdlo, ldd, 2L * m * ldd, 2 * c, t.WThi, t.WTlo, ldd, sWT, 2 * nb, n1, t.Elo,
                              2L * b, 4L * m * b, h, t.err, s));
       TSVD_TRY(complex_from_real(t.Elo, 2L * b, 4L * m * b, c, nb, P, nb, sP, h, s));
       const long sEq = 2L * b * t.ldqi;
       TSVD_TRY(expand_thin_split(P, nb, sP, c, nb, t.Ehi, t.Elo, t.ldqi, sEq, h, 0, s));
       TSVD_TRY(tc_gemm_split(t.Qhi, t.Qlo, t.ldqi, (long)n1 * t.ldqi, n1, t.Ehi, t.Elo, t.ldqi, sEq, 2 * nb, 2 * c,
-                             (float*)W, 2L * b, 2L * sW, h, t.err, s, -1.0f, 1.0f));
+                             (float*)W, 2L * b, 2L * sW, h, t.err, s, -1.0f, 1.0f, &both));
+      wd = wr = true;
     }
     {
       // G = W^H W through the real Gram of W's de-interleaved columns (K = n1; 2 nb x 2 nb outputs,
       // kept in Elo until the Cholesky has read G)
       TSVD_STAGE("orth_gram", s);
-      const long ldd = t.ldq2 / 2;  // >= n1, a multiple of 4 (16-byte rows)
       float* Pr = t.Elo;
-      TSVD_TRY(split_deinterleave(W, n1, nb, b, sW, h, t.WThi, t.WTlo, ldd, sWT, s));
+      if (!wd) TSVD_TRY(split_deinterleave(W, n1, nb, b, sW, h, t.WThi, t.WTlo, ldd, sWT, s));
       TSVD_TRY(tc_gemm_split(t.WThi, t.WTlo, ldd, sWT, 2 * nb, t.WThi, t.WTlo, ldd, sWT, 2 * nb, n1, Pr, 2L * b,
                              4L * b * b, h, t.err, s));
       TSVD_TRY(complex_from_real(Pr, 2L * b, 4L * b * b, nb, nb, Gs, b, sG, h, s));
@@ -536,11 +550,14 @@ static int orth_block_tc(int n1, int b, int m, int h, const OrthWs& w, int c, in
     }
     {
       TSVD_STAGE("orth_trsm", s);  // W R^-1, the last pass straight into its columns of Q
-      TSVD_TRY(split_rows((const float*)W, 2L * b, t.Whi, t.Wlo, t.ldw2, 2 * nb, (long)h * n1, s));
+      if (!wr) TSVD_TRY(split_rows((const float*)W, 2L * b, t.Whi, t.Wlo, t.ldw2, 2 * nb, (long)h * n1, s));
       TSVD_TRY(expand_thin_split(Mi, b, sG, nb, nb, t.Ehi, t.Elo, t.ldw2, sE, h, 0, s));
       float* out = (pass < 2) ? (float*)W : (float*)(Q + c);
       TSVD_TRY(tc_gemm_split(t.Whi, t.Wlo, t.ldw2, sWr, n1, t.Ehi, t.Elo, t.ldw2, sE, 2 * nb, 2 * nb, out,
-                             pass < 2 ? 2L * b : 2L * m, pass < 2 ? 2L * sW : 2L * sQ, h, t.err, s));
+                             pass < 2 ? 2L * b : 2L * m, pass < 2 ? 2L * sW : 2L * sQ, h, t.err, s, 1.0f, 0.0f,
+                             pass < 2 ? &cols_only : nullptr));
+      wd = pass < 2;
+      wr = false;
     }
   }
   {
@@ -549,7 +566,6 @@ static int orth_block_tc(int n1, int b, int m, int h, const OrthWs& w, int c, in
   }
   // the finished columns' split operands for the projections of the later blocks
   TSVD_STAGE("orth_cgs", s);
-  const long ldd = t.ldq2 / 2;
   TSVD_TRY(split_block((const float*)(Q + c), 2L * m, t.Qhi + 2L * c, t.Qlo + 2L * c, t.ldqi, 2 * nb, (long)h * n1,
                        s));
   return split_deinterleave(Q + c, n1, nb, m, sQ, h, t.Qdhi + 2L * c * ldd, t.Qdlo + 2L * c * ldd, ldd,

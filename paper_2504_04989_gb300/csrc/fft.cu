@@ -260,10 +260,17 @@ constexpr size_t fft_smem_c(int n, int tt) {
   return sizeof(cx_t<T>) * ((size_t)n + (size_t)FFT_WARPS * 2 * fft_seqs(n) * n + (size_t)(n / 2 + 1) * (tt + 1)) +
          sizeof(T) * (size_t)n * (tt + 1);
 }
-// tubes per CTA: the widest tile that fits (the choice fft_setup makes at run time)
+// tubes per CTA (the choice fft_setup makes at run time): the widest tile that leaves room for
+// three CTAs per SM (measured: n = 128 in FP32 went from 64 tubes, two CTAs per SM, to 32),
+// else the widest within 110 KB
+constexpr size_t FFT_SMEM_3 = 72 * 1024, FFT_SMEM_MAX = 110 * 1024;
+constexpr int fft_pick_tt(size_t s64, size_t s32, size_t s16) {
+  return s64 <= FFT_SMEM_3 ? 64 : s32 <= FFT_SMEM_3 ? 32 : s16 <= FFT_SMEM_3 ? 16 :
+         s64 <= FFT_SMEM_MAX ? 64 : s32 <= FFT_SMEM_MAX ? 32 : s16 <= FFT_SMEM_MAX ? 16 : 0;
+}
 template <typename T>
 constexpr int fft_tt(int n) {
-  return fft_smem_c<T>(n, 64) <= 110 * 1024 ? 64 : (fft_smem_c<T>(n, 32) <= 110 * 1024 ? 32 : 16);
+  return fft_pick_tt(fft_smem_c<T>(n, 64), fft_smem_c<T>(n, 32), fft_smem_c<T>(n, 16));
 }
 
 template <typename T, int NC>  // NC: compile-time length (0: the plan's)
@@ -447,15 +454,11 @@ static size_t fft_smem(int n, int tt, int seqs) {
 template <typename T>
 static bool fft_setup(int n, FftPlan* P, size_t* smem) {
   if (!make_plan(n, P)) return false;
-  for (int tt = 64; tt >= 16; tt >>= 1) {
-    const size_t b = fft_smem<T>(n, tt, P->seqs);
-    if (b <= 110 * 1024) {
-      P->tubes = tt;
-      *smem = b;
-      return true;
-    }
-  }
-  return false;
+  const int tt = fft_pick_tt(fft_smem<T>(n, 64, P->seqs), fft_smem<T>(n, 32, P->seqs), fft_smem<T>(n, 16, P->seqs));
+  if (tt == 0) return false;
+  P->tubes = tt;
+  *smem = fft_smem<T>(n, tt, P->seqs);
+  return true;
 }
 
 template <typename T>

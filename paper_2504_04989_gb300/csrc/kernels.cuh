@@ -166,9 +166,18 @@ int expand_thin(const float2* Y, long ldy, long sy, int K, int N, void* E, long 
 int copy_rows(const float* x, long ldx, void* y, long ldy, int cols, long rows, bool bf16, cudaStream_t s);
 // split TF32: C = alpha A B^T + beta C with A = Ahi + Alo, B = Bhi + Blo (hi*hi + hi*lo + lo*hi),
 // FP32-level accuracy
+// Optional split copies of the result written by the epilogue (null pointers: none):
+//   rows (Rhi / Rlo): hi / lo of C in C's own layout (leading dim ldr, batch stride sr);
+//   cols (Thi / Tlo): hi / lo of C^T (row f of T is column f of C; leading dim ldt, batch stride st).
+struct TcSplitOut {
+  float *Rhi = nullptr, *Rlo = nullptr;
+  long ldr = 0, sr = 0;
+  float *Thi = nullptr, *Tlo = nullptr;
+  long ldt = 0, st = 0;
+};
 int tc_gemm_split(const float* Ahi, const float* Alo, long lda, long sA, int M, const float* Bhi, const float* Blo,
                   long ldb, long sB, int N, int K, float* C, long ldc, long sC, int batch, int* err, cudaStream_t s,
-                  float alpha = 1.0f, float beta = 0.0f);
+                  float alpha = 1.0f, float beta = 0.0f, const TcSplitOut* out2 = nullptr);
 // FP32 rows -> hi (nearest TF32) / lo rows of leading dim ldy, padding zeroed
 int split_rows(const float* x, long ldx, float* hi, float* lo, long ldy, int cols, long rows, cudaStream_t s);
 // columns [0, cols) of FP32 rows -> hi / lo rows (leading dim ldy); other columns untouched

@@ -46,6 +46,13 @@ constexpr int tc_smem() { return tc_stages<MODE, BN>() * tc_stage_bytes<MODE, BN
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// hi = x rounded to the nearest TF32 (lo = x - hi is exact in FP32)
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
@@ -123,7 +130,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
                                                     const __grid_constant__ CUtensorMap tmA2,
                                                     const __grid_constant__ CUtensorMap tmB2, float* __restrict__ C,
                                                     long ldc, long sC, int M, int N, int nk, int* __restrict__ err,
-                                                    float alpha, float beta, int upper) {
+                                                    float alpha, float beta, int upper, TcSplitOut o2) {
   constexpr bool BF16 = MODE == 1, SPLIT = MODE == 2;
   constexpr int STAGES = tc_stages<MODE, BN>(), SB = tc_stage_bytes<MODE, BN>();
   static_assert(tc_smem<MODE, BN>() <= 227 * 1024, "the stages must fit the opt-in shared memory of a CTA");
@@ -226,32 +233,77 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (row < M) {
         float* dst = crow + n0 + c0;
-        if (n0 + c0 + 16 <= N && ((uintptr_t)dst & 15) == 0) {
+        const bool full = n0 + c0 + 16 <= N;
+        float o[16];  // the chunk's final values (C = alpha A B^T + beta C)
+        if (full && ((uintptr_t)dst & 15) == 0) {
           // the thread's 16 columns as four 16-byte accesses (the old values all loaded first)
-          float4 o[4];
+          float4 old4[4];
           if (beta != 0.0f) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) o[q] = reinterpret_cast<const float4*>(dst)[q];
+            for (int q = 0; q < 4; ++q) old4[q] = reinterpret_cast<const float4*>(dst)[q];
           }
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             float4 v = make_float4(alpha * __uint_as_float(r[4 * q]), alpha * __uint_as_float(r[4 * q + 1]),
                                    alpha * __uint_as_float(r[4 * q + 2]), alpha * __uint_as_float(r[4 * q + 3]));
             if (beta != 0.0f) {
-              v.x = fmaf(beta, o[q].x, v.x);
-              v.y = fmaf(beta, o[q].y, v.y);
-              v.z = fmaf(beta, o[q].z, v.z);
-              v.w = fmaf(beta, o[q].w, v.w);
+              v.x = fmaf(beta, old4[q].x, v.x);
+              v.y = fmaf(beta, old4[q].y, v.y);
+              v.z = fmaf(beta, old4[q].z, v.z);
+              v.w = fmaf(beta, old4[q].w, v.w);
             }
             reinterpret_cast<float4*>(dst)[q] = v;
+            o[4 * q] = v.x;
+            o[4 * q + 1] = v.y;
+            o[4 * q + 2] = v.z;
+            o[4 * q + 3] = v.w;
           }
         } else {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int col = n0 + c0 + j;
+            o[j] = 0.0f;
             if (col < N) {
-              const float v = alpha * __uint_as_float(r[j]);  // C = alpha A B^T + beta C
-              crow[col] = (beta != 0.0f) ? fmaf(beta, crow[col], v) : v;
+              const float v = alpha * __uint_as_float(r[j]);
+              o[j] = (beta != 0.0f) ? fmaf(beta, crow[col], v) : v;
+              crow[col] = o[j];
+            }
+          }
+        }
+        if (o2.Rhi) {  // split copy in C's layout
+          float* rh = o2.Rhi + (long)bz * o2.sr + (long)row * o2.ldr + n0 + c0;
+          float* rl = o2.Rlo + (long)bz * o2.sr + (long)row * o2.ldr + n0 + c0;
+          if (full && (((uintptr_t)rh | (uintptr_t)rl) & 15) == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              float h4[4], l4[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                h4[u] = tf32_hi(o[4 * q + u]);
+                l4[u] = o[4 * q + u] - h4[u];
+              }
+              reinterpret_cast<float4*>(rh)[q] = make_float4(h4[0], h4[1], h4[2], h4[3]);
+              reinterpret_cast<float4*>(rl)[q] = make_float4(l4[0], l4[1], l4[2], l4[3]);
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (n0 + c0 + j < N) {
+                const float hv = tf32_hi(o[j]);
+                rh[j] = hv;
+                rl[j] = o[j] - hv;
+              }
+          }
+        }
+        if (o2.Thi) {  // split copy of C^T: lanes are consecutive rows, so each store is coalesced
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int col = n0 + c0 + j;
+            if (col < N) {
+              const long off = (long)bz * o2.st + (long)col * o2.ldt + row;
+              const float hv = tf32_hi(o[j]);
+              o2.Thi[off] = hv;
+              o2.Tlo[off] = o[j] - hv;
             }
           }
         }
@@ -319,7 +371,7 @@ bool tc_gemm_supported(const void* A, long lda, long sA, const void* B, long ldb
 template <int MODE, int BN>
 static int tc_launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& ta2, const CUtensorMap& tb2,
                      float* C, long ldc, long sC, int M, int N, int nk, int batch, int* err, cudaStream_t s,
-                     float alpha = 1.0f, float beta = 0.0f, int upper = 0) {
+                     float alpha = 1.0f, float beta = 0.0f, int upper = 0, const TcSplitOut& o2 = TcSplitOut()) {
   dim3 grid(cdiv(N, BN), cdiv(M, TC_BM), batch);
   if (cudaFuncSetAttribute(k_tc_gemm<MODE, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<MODE, BN>()) !=
       cudaSuccess) {
@@ -327,7 +379,7 @@ static int tc_launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtenso
     return TSVD_ERR_CUDA;
   }
   k_tc_gemm<MODE, BN><<<grid, 128, tc_smem<MODE, BN>(), s>>>(ta, tb, ta2, tb2, C, ldc, sC, M, N, nk, err, alpha,
-                                                               beta, upper);
+                                                               beta, upper, o2);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }
@@ -355,7 +407,7 @@ int tc_gemm(const void* A, long lda, long sA, int M, const void* B, long ldb, lo
 
 int tc_gemm_split(const float* Ahi, const float* Alo, long lda, long sA, int M, const float* Bhi, const float* Blo,
                   long ldb, long sB, int N, int K, float* C, long ldc, long sC, int batch, int* err, cudaStream_t s,
-                  float alpha, float beta) {
+                  float alpha, float beta, const TcSplitOut* out2) {
   if (M <= 0 || N <= 0 || batch <= 0) return TSVD_OK;
   if (!tc_gemm_supported(Ahi, lda, sA, Bhi, ldb, sB, batch, false) ||
       !tc_gemm_supported(Alo, lda, sA, Blo, ldb, sB, batch, false))
@@ -367,7 +419,8 @@ int tc_gemm_split(const float* Ahi, const float* Alo, long lda, long sA, int M, 
   TSVD_TRY(make_map(&tb, Bhi, N, K, ldb, sB, batch, false));
   TSVD_TRY(make_map(&ta2, Alo, M, K, lda, sA, batch, false));
   TSVD_TRY(make_map(&tb2, Blo, N, K, ldb, sB, batch, false));
-  return tc_launch<2, 128>(ta, tb, ta2, tb2, C, ldc, sC, M, N, (K + 31) / 32, batch, err, s, alpha, beta);
+  return tc_launch<2, 128>(ta, tb, ta2, tb2, C, ldc, sC, M, N, (K + 31) / 32, batch, err, s, alpha, beta, 0,
+                           out2 ? *out2 : TcSplitOut());
 }
 
 // ---------------------------------------------------------------------------
@@ -462,11 +515,6 @@ int copy_rows(const float* x, long ldx, void* y, long ldy, int cols, long rows, 
 // Split operands for the split-TF32 mode: hi = x rounded to the nearest TF32
 // (cvt.rna.tf32.f32), lo = x - hi (exact in FP32).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float tf32_hi(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
 
 // rows x cols FP32 (leading dim ldx) to hi / lo rows of leading dim ldy (padding zeroed)
 __global__ void k_split_rows(const float* __restrict__ x, long ldx, float* __restrict__ hi, float* __restrict__ lo,
