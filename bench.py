@@ -408,9 +408,14 @@ def main():
                 peak, src = alu["double_float"], "measured FP32 GEMM rate / 15 instructions per double-float FMA x 2"
             elif stage == "krylov_gemm_tc":
                 peak, src = alu["tf32"], "measured here: cuBLAS TF32 GEMM"
-            elif stage in ("orth_gram", "orth_trsm") and d["n1"] >= 1024:
+            elif stage in ("orth_gram", "orth_trsm", "orth_cgs") and d["n1"] >= 1024:
                 # tcgen05 in split TF32 from n1 = 1024 on: three TF32 products per FP32-accurate one
                 peak, src = alu["tf32"] and alu["tf32"] / 3, "measured here: cuBLAS TF32 GEMM / 3 (split TF32)"
+            elif stage == "gram_c" and d["n2"] <= 4096:
+                # the exact Gram in base-64 digits on the BF16 tensor cores: of the 16 digit-pair
+                # products about 8 are computed (the symmetric half skipped)
+                peak = pk.get("bf16_tflops")
+                peak, src = peak and peak / 8, "MEASURED_PEAKS.json bf16_tflops / 8 (digit-pair products)"
             else:
                 peak, src = alu["fp32"], "measured here: cuBLAS FP32 GEMM (no TF32)"
             a = work["flops"] / t / 1e12
