@@ -516,8 +516,8 @@ static int orth_block_tc(int n1, int b, int m, int h, const OrthWs& w, int c, in
   both.Tlo = t.WTlo;
   both.ldt = ldd;
   both.st = sWT;
-  TcSplitOut cols_only = both;  // W R^-1 reads Whi / Wlo as its operand: it writes only the other copy
-  cols_only.Rhi = cols_only.Rlo = nullptr;
+  TcSplitOut rows_only = both;  // measured: the transposed copy costs the epilogue more than a
+  rows_only.Thi = rows_only.Tlo = nullptr;  // separate de-interleaving pass
   for (int pass = 0; pass < 3; ++pass) {
     if (c > 0) {
       // the projection on tcgen05 against the cached split operands of Q's finished columns:
@@ -531,8 +531,9 @@ static int orth_block_tc(int n1, int b, int m, int h, const OrthWs& w, int c, in
       const long sEq = 2L * b * t.ldqi;
       TSVD_TRY(expand_thin_split(P, nb, sP, c, nb, t.Ehi, t.Elo, t.ldqi, sEq, h, 0, s));
       TSVD_TRY(tc_gemm_split(t.Qhi, t.Qlo, t.ldqi, (long)n1 * t.ldqi, n1, t.Ehi, t.Elo, t.ldqi, sEq, 2 * nb, 2 * c,
-                             (float*)W, 2L * b, 2L * sW, h, t.err, s, -1.0f, 1.0f, &both));
-      wd = wr = true;
+                             (float*)W, 2L * b, 2L * sW, h, t.err, s, -1.0f, 1.0f, &rows_only));
+      wd = false;
+      wr = true;
     }
     {
       // G = W^H W through the real Gram of W's de-interleaved columns (K = n1; 2 nb x 2 nb outputs,
@@ -554,10 +555,8 @@ static int orth_block_tc(int n1, int b, int m, int h, const OrthWs& w, int c, in
       TSVD_TRY(expand_thin_split(Mi, b, sG, nb, nb, t.Ehi, t.Elo, t.ldw2, sE, h, 0, s));
       float* out = (pass < 2) ? (float*)W : (float*)(Q + c);
       TSVD_TRY(tc_gemm_split(t.Whi, t.Wlo, t.ldw2, sWr, n1, t.Ehi, t.Elo, t.ldw2, sE, 2 * nb, 2 * nb, out,
-                             pass < 2 ? 2L * b : 2L * m, pass < 2 ? 2L * sW : 2L * sQ, h, t.err, s, 1.0f, 0.0f,
-                             pass < 2 ? &cols_only : nullptr));
-      wd = pass < 2;
-      wr = false;
+                             pass < 2 ? 2L * b : 2L * m, pass < 2 ? 2L * sW : 2L * sQ, h, t.err, s));
+      wd = wr = false;
     }
   }
   {
