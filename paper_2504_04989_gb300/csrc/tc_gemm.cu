@@ -10,8 +10,12 @@
 // buffers guarded by mbarriers; one thread issues tcgen05.mma (4 per stage,
 // 32 bytes of K each) into a BN-column TMEM accumulator and commits each
 // stage back to the producer; all four warps then read the accumulator with
-// tcgen05.ld and store it.  Every wait is bounded: on a timeout the kernel
-// records an error flag instead of hanging.
+// tcgen05.ld and store it (thread = row, 16 columns at a time as four 16-byte
+// accesses where aligned; C = alpha A B^T + beta C, the old values loaded
+// before any store).  Every wait is bounded: on a timeout the kernel records
+// an error flag instead of hanging.  Options: `upper` skips the tiles wholly
+// below the diagonal of a symmetric product (B = A); the split-TF32 epilogue
+// can also write hi / lo copies of C and of C^T for a following product.
 //
 // A third mode keeps FP32 accuracy on the TF32 units ("split TF32"): each
 // operand is split as x = hi + lo with hi = x rounded to TF32 and lo = x - hi
@@ -22,7 +26,9 @@
 // Complex products use it without moving the big operand: an interleaved
 // complex matrix X (rows x cols) is the real matrix [Re Im Re Im ...] of
 // rows x 2cols, so X * Y = real(X) * E(Y)^T with a small expanded real form
-// E(Y) of the thin factor (see expand_* below).
+// E(Y) of the thin factor (see expand_* below).  X^H Y with both factors tall
+// takes their de-interleaved columns instead (split_deinterleave): one real
+// product of the rows Re x_c, Im x_c against those of Y, combined 2 x 2.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
