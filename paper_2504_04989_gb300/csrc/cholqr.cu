@@ -460,12 +460,13 @@ template int repair_dead<float2>(float2*, long, long, int, int, int, const uint3
 // succeed for any W; the next two passes restore orthogonality to rounding
 // level), each pass preceded by a classical Gram-Schmidt projection against
 // Q_{<i}; dependent columns are then replaced.
-// The FP32 block step with its block Gram and its W R^-1 on tcgen05 (split
-// TF32: FP32-level accuracy): each complex product X Y is real(X) E(Y)^T with
-// the expanded real form E of the thin factor (tc_gemm.cu).  The Gram-Schmidt
-// projections stay on the SIMT GEMM: as long-K products with two 128-column
-// output tiles they stream their split operands twice, measured slower than
-// the SIMT kernel (which runs them at about half of the FP32 peak).
+// The FP32 block step with every product on tcgen05 in split TF32 (FP32-level
+// accuracy, tc_gemm.cu): the block Gram W^H W and the coefficients Q^H W as
+// real products of de-interleaved columns (K = n1), the update W -= Q (Q^H W)
+// and W R^-1 as real(X) E(Y)^T with the small expanded real form E of the
+// thin factor.  Q's finished columns are split once per block (hi / lo
+// interleaved and de-interleaved rows) and reused by all later projections;
+// the update's epilogue writes W's split rows for W R^-1.
 // X^H Y (rows x cols complex) from the real product P = X_d Y_d^T of the de-interleaved columns
 // (row 2c of X_d the real parts of column c of X, row 2c+1 the imaginary parts; Y_d alike):
 //   (X^H Y)_ij = P[2i][2j] + P[2i+1][2j+1] + i (P[2i][2j+1] - P[2i+1][2j])
